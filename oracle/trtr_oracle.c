@@ -1,0 +1,478 @@
+/*
+ * trtr_oracle.c -- plain FP64 CPU oracle of the TRT-R lattice Boltzmann step for the
+ * convection-diffusion equation with variable coefficients (Yu, Qin, Yuan, Shu,
+ * arXiv 2312.10316).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or load this
+ * file: only the tests, the smoke check and the CPU-baseline leg of the benchmark use
+ * it.  It shares no code, header, table or helper with the CUDA library.
+ *
+ * Structure: the evolution equation is written out literally, in the paper's notation
+ * and PHYSICAL units (e_i = c*ehat_i, c_s^2 = c^2/3, u in length/time, kappa in
+ * length^2/time), with explicit Hermite tensors and explicit tensor contractions:
+ *
+ *   g_i(x + e_i dt, t + dt) = g_i^eq + (1 - 1/tau1) w_i H_ia B_a^neq / cs^2
+ *                           + (1 - 1/tau2) w_i H_iab B_ab^neq / (2 cs^4)
+ *                           + dt G_i + dt F_i + dt^2/2 d_t F_i              Eq. (14) [eq_ev]
+ *
+ * and streaming is done by PUSHING the post-collision value to x + e_i dt, the form the
+ * left-hand side of Eq. (14) states.  The stored state is the pre-collision population
+ * g_i(x, t_n).
+ *
+ * Equation numbers count the paper's displayed equations in order; the LaTeX label is
+ * given in brackets.  Readings of points the paper leaves open:
+ *  - d_beta u_alpha in G_i (Eq. (16) [eq_aux_new]) is a second-order central difference of
+ *    the nodal u field; mode 1 uses the one-sided two-point difference on the first and
+ *    last column/row instead of wrapping (both are exact for a linear u).
+ *  - dt^2/2 d_t F_i is (dt^2/2)(F_i^n - F_i^{n-1})/dt, with F^{-1} := F^0 at the first step
+ *    after initialisation (u is time-independent within a step, Sec. 2.3).
+ *  - phi = sum_i g_i of the pre-collision populations (B_0^neq = 0, Sec. 2.2).
+ *  - tau1 from kappa = (tau1 - 1/2) c_s^2 dt (Sec. 2.4), per node from D(x); tau2 from the
+ *    magic parameter Lambda = (tau1 - 1/2)(tau2 - 1/2) (Eq. (28)) or given.
+ *
+ * Build: cc -O2 -ffp-contract=off -fPIC -shared [-fopenmp] trtr_oracle.c -lm
+ * (-ffp-contract=off: every product and sum rounds as written).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define Q 9
+#define PI 3.14159265358979323846
+
+/* D2Q9 (Sec. 2.2): e_0 = (0,0), (+-c,0), (0,+-c), (+-c,+-c); w_0 = 4/9, w_1..4 = 1/9,
+ * w_5..8 = 1/36.  Index order (shared convention of this project, not the paper's):
+ * 0:(0,0) 1:(1,0) 2:(-1,0) 3:(0,1) 4:(0,-1) 5:(1,1) 6:(-1,-1) 7:(1,-1) 8:(-1,1). */
+static const int EHAT[Q][2] = {{0, 0}, {1, 0}, {-1, 0}, {0, 1}, {0, -1},
+                               {1, 1}, {-1, -1}, {1, -1}, {-1, 1}};
+static const double WEIGHT[Q] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
+                                 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+
+typedef struct {
+    int nx, ny;
+    double x0, y0, dx, dt;
+    int tau2_mode;      /* 0: magic parameter, 1: fixed tau2 */
+    double magic, tau2; /* Lambda (Eq. (28)); fixed tau2 */
+    double tau1_const;  /* > 0: tau1 given directly, D ignored */
+    int grad_mode;      /* 0: periodic central differences, 1: one-sided at the edges */
+    int src_mode;       /* 0: S = 0, 1: given field, 2: manufactured pulse source */
+    double omega, xc, yc, sigma0, D0, D_amp; /* pulse parameters (src_mode 2) */
+} oracle_params;
+
+/* Lattice constants and Hermite tensors in physical units (Sec. 2.2, text after Eq. (10)):
+ * H0 = 1, H_a = e_a, H_ab = e_a e_b - cs^2 d_ab,
+ * H_abg = e_a e_b e_g - cs^2 (e_a d_bg + e_b d_ga + e_g d_ab). */
+typedef struct {
+    double c, cs2;
+    double e[Q][2];
+    double H1[Q][2];
+    double H2[Q][2][2];
+    double H3[Q][2][2][2];
+} oracle_lattice;
+
+static double kron(int a, int b) { return a == b ? 1.0 : 0.0; }
+
+static void lattice_init(oracle_lattice* L, double dx, double dt) {
+    L->c = dx / dt;
+    L->cs2 = L->c * L->c / 3.0;
+    for (int i = 0; i < Q; ++i) {
+        for (int a = 0; a < 2; ++a) L->e[i][a] = L->c * (double)EHAT[i][a];
+        for (int a = 0; a < 2; ++a) {
+            L->H1[i][a] = L->e[i][a];
+            for (int b = 0; b < 2; ++b) {
+                L->H2[i][a][b] = L->e[i][a] * L->e[i][b] - L->cs2 * kron(a, b);
+                for (int g = 0; g < 2; ++g)
+                    L->H3[i][a][b][g] = L->e[i][a] * L->e[i][b] * L->e[i][g] -
+                                        L->cs2 * (L->e[i][a] * kron(b, g) + L->e[i][b] * kron(g, a) +
+                                                  L->e[i][g] * kron(a, b));
+            }
+        }
+    }
+}
+
+/* Third-order Hermite equilibrium, Eq. (6):
+ * g_i^eq = w_i phi { H0 + H_a u_a / cs^2 + H_ab u_a u_b / (2 cs^4) + H_abg u_a u_b u_g / (6 cs^6) } */
+static void equilibrium(const oracle_lattice* L, double phi, const double u[2], double geq[Q]) {
+    const double cs2 = L->cs2, cs4 = cs2 * cs2, cs6 = cs4 * cs2;
+    for (int i = 0; i < Q; ++i) {
+        double t1 = 0.0, t2 = 0.0, t3 = 0.0;
+        for (int a = 0; a < 2; ++a) {
+            t1 += L->H1[i][a] * u[a];
+            for (int b = 0; b < 2; ++b) {
+                t2 += L->H2[i][a][b] * u[a] * u[b];
+                for (int g = 0; g < 2; ++g) t3 += L->H3[i][a][b][g] * u[a] * u[b] * u[g];
+            }
+        }
+        geq[i] = WEIGHT[i] * phi * (1.0 + t1 / cs2 + t2 / (2.0 * cs4) + t3 / (6.0 * cs6));
+    }
+}
+
+/* TRT-R collision operator, Eq. (12) [eq11], with
+ *   g_i^neq = g_i - g_i^eq                     Eq. (5)
+ *   B_a^neq  = sum_i H_ia  g_i^neq            Eq. (8)
+ *   B_ab^neq = sum_i H_iab (g_i - g_i^eq)     Eq. (13)
+ *   phi = sum_i g_i                            (B_0^neq = 0, text after Eq. (10)) */
+static void collide_trtr(const oracle_lattice* L, const double g[Q], const double u[2], double tau1,
+                         double tau2, double out[Q], double* phi_out) {
+    const double cs2 = L->cs2, cs4 = cs2 * cs2;
+    double phi = 0.0;
+    for (int i = 0; i < Q; ++i) phi += g[i];
+    double geq[Q], gneq[Q];
+    equilibrium(L, phi, u, geq);
+    for (int i = 0; i < Q; ++i) gneq[i] = g[i] - geq[i];
+    double B1[2] = {0.0, 0.0};
+    double B2[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+    for (int i = 0; i < Q; ++i)
+        for (int a = 0; a < 2; ++a) {
+            B1[a] += L->H1[i][a] * gneq[i];
+            for (int b = 0; b < 2; ++b) B2[a][b] += L->H2[i][a][b] * gneq[i];
+        }
+    for (int i = 0; i < Q; ++i) {
+        double r1 = 0.0, r2 = 0.0;
+        for (int a = 0; a < 2; ++a) {
+            r1 += L->H1[i][a] * B1[a];
+            for (int b = 0; b < 2; ++b) r2 += L->H2[i][a][b] * B2[a][b];
+        }
+        out[i] = geq[i] + (1.0 - 1.0 / tau1) * WEIGHT[i] * r1 / cs2 +
+                 (1.0 - 1.0 / tau2) * WEIGHT[i] * r2 / (2.0 * cs4);
+    }
+    if (phi_out) *phi_out = phi;
+}
+
+/* New space-derivative auxiliary term, Eq. (16) [eq_aux_new]:
+ *   G_i = w_i e_ia / cs^2 (1 - 1/(2 tau1)) phi u_b d_b u_a,   du[a][b] = d_b u_a */
+static void aux_G(const oracle_lattice* L, double phi, const double u[2], const double du[2][2],
+                  double tau1, double G[Q]) {
+    double adv[2];
+    for (int a = 0; a < 2; ++a) {
+        adv[a] = 0.0;
+        for (int b = 0; b < 2; ++b) adv[a] += u[b] * du[a][b];
+    }
+    for (int i = 0; i < Q; ++i) {
+        double ea = 0.0;
+        for (int a = 0; a < 2; ++a) ea += L->e[i][a] * adv[a];
+        G[i] = WEIGHT[i] * ea / L->cs2 * (1.0 - 1.0 / (2.0 * tau1)) * phi;
+    }
+}
+
+/* First-order discrete-velocity source term, Eq. (3) [eq_Fi]:
+ *   F_i = w_i S + (1 - 1/(2 tau1)) w_i e_ia u_a S / cs^2 */
+static void source_F(const oracle_lattice* L, double S, const double u[2], double tau1, double F[Q]) {
+    for (int i = 0; i < Q; ++i) {
+        double eu = 0.0;
+        for (int a = 0; a < 2; ++a) eu += L->e[i][a] * u[a];
+        F[i] = WEIGHT[i] * S + (1.0 - 1.0 / (2.0 * tau1)) * WEIGHT[i] * eu * S / L->cs2;
+    }
+}
+
+/* kappa = (tau1 - 1/2) cs^2 dt (Sec. 2.4, after Eq. (27)) solved for tau1. */
+static double tau1_from_kappa(const oracle_lattice* L, double kappa, double dt) {
+    return 0.5 + kappa / (L->cs2 * dt);
+}
+
+/* Lambda = (tau1 - 1/2)(tau2 - 1/2), Eq. (28), solved for tau2. */
+static double tau2_from_magic(double tau1, double magic) { return 0.5 + magic / (tau1 - 0.5); }
+
+/* ------------------------------------------------------------------------------------ */
+/* Single-node entry points (used by the pins on their own).                            */
+
+void oracle_equilibrium(double dx, double dt, double phi, double ux, double uy, double* geq) {
+    oracle_lattice L;
+    lattice_init(&L, dx, dt);
+    const double u[2] = {ux, uy};
+    equilibrium(&L, phi, u, geq);
+}
+
+void oracle_collide(double dx, double dt, const double* g, double ux, double uy, double tau1, double tau2,
+                    double* out) {
+    oracle_lattice L;
+    lattice_init(&L, dx, dt);
+    const double u[2] = {ux, uy};
+    collide_trtr(&L, g, u, tau1, tau2, out, NULL);
+}
+
+/* du = {d_x u_x, d_y u_x, d_x u_y, d_y u_y} */
+void oracle_aux_G(double dx, double dt, double phi, double ux, double uy, const double* du, double tau1,
+                  double* G) {
+    oracle_lattice L;
+    lattice_init(&L, dx, dt);
+    const double u[2] = {ux, uy};
+    const double d[2][2] = {{du[0], du[1]}, {du[2], du[3]}};
+    aux_G(&L, phi, u, d, tau1, G);
+}
+
+void oracle_source_F(double dx, double dt, double S, double ux, double uy, double tau1, double* F) {
+    oracle_lattice L;
+    lattice_init(&L, dx, dt);
+    const double u[2] = {ux, uy};
+    source_F(&L, S, u, tau1, F);
+}
+
+double oracle_tau1(double D, double dx, double dt) {
+    oracle_lattice L;
+    lattice_init(&L, dx, dt);
+    return tau1_from_kappa(&L, D, dt);
+}
+
+double oracle_tau2_magic(double tau1, double magic) { return tau2_from_magic(tau1, magic); }
+
+void oracle_d2q9(int* ex, int* ey, double* w) {
+    for (int i = 0; i < Q; ++i) {
+        ex[i] = EHAT[i][0];
+        ey[i] = EHAT[i][1];
+        w[i] = WEIGHT[i];
+    }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Grid simulation.                                                                     */
+
+typedef struct {
+    oracle_params p;
+    oracle_lattice L;
+    size_t n;                  /* nx * ny */
+    double *g, *gnext;         /* [Q][ny][nx] pre-collision populations g_i(x, t_n) */
+    double *ux, *uy, *D;       /* physical fields */
+    double *S_cur, *S_prev;    /* src_mode 1: S used at this step and at the previous one */
+    int S_prev_valid;          /* 0 right after init: F^{-1} := F^0 */
+    long step;
+} oracle_sim;
+
+#define AT(s, q, j, i) ((size_t)(q) * (s)->n + (size_t)(j) * (size_t)(s)->p.nx + (size_t)(i))
+
+oracle_sim* oracle_create(const oracle_params* p) {
+    if (p->nx < 1 || p->ny < 1 || !(p->dx > 0.0) || !(p->dt > 0.0)) return NULL;
+    oracle_sim* s = (oracle_sim*)calloc(1, sizeof(oracle_sim));
+    if (!s) return NULL;
+    s->p = *p;
+    lattice_init(&s->L, p->dx, p->dt);
+    s->n = (size_t)p->nx * (size_t)p->ny;
+    s->g = (double*)calloc(Q * s->n, sizeof(double));
+    s->gnext = (double*)calloc(Q * s->n, sizeof(double));
+    s->ux = (double*)calloc(s->n, sizeof(double));
+    s->uy = (double*)calloc(s->n, sizeof(double));
+    s->D = (double*)calloc(s->n, sizeof(double));
+    s->S_cur = (double*)calloc(s->n, sizeof(double));
+    s->S_prev = (double*)calloc(s->n, sizeof(double));
+    if (!s->g || !s->gnext || !s->ux || !s->uy || !s->D || !s->S_cur || !s->S_prev) {
+        free(s->g); free(s->gnext); free(s->ux); free(s->uy); free(s->D); free(s->S_cur); free(s->S_prev);
+        free(s);
+        return NULL;
+    }
+    return s;
+}
+
+void oracle_destroy(oracle_sim* s) {
+    if (!s) return;
+    free(s->g); free(s->gnext); free(s->ux); free(s->uy); free(s->D); free(s->S_cur); free(s->S_prev);
+    free(s);
+}
+
+/* Physical fields u_x, u_y, D (= kappa) on the nodes, row-major [ny][nx]. */
+void oracle_set_fields(oracle_sim* s, const double* ux, const double* uy, const double* D) {
+    memcpy(s->ux, ux, s->n * sizeof(double));
+    memcpy(s->uy, uy, s->n * sizeof(double));
+    memcpy(s->D, D, s->n * sizeof(double));
+}
+
+/* src_mode 1: S for the next step.  The previous step's S stays as S^{n-1}. */
+void oracle_set_source(oracle_sim* s, const double* S) { memcpy(s->S_cur, S, s->n * sizeof(double)); }
+
+static double node_x(const oracle_sim* s, int i) { return s->p.x0 + (double)i * s->p.dx; }
+static double node_y(const oracle_sim* s, int j) { return s->p.y0 + (double)j * s->p.dx; }
+
+/* Manufactured source of the rotating, spreading Gaussian pulse with
+ * D(x) = D0 (1 + D_amp sin(pi x) sin(pi y)):  phi_a = (s0^2/s^2) exp(-|x - c(t)|^2 / (2 s^2)),
+ * s^2 = s0^2 + 2 D0 t, c(t) = R(omega t)(xc, yc), solves the constant-D0 equation (1) with
+ * u = omega(-y, x); S = -div((D - D0) grad phi_a) makes it solve the variable-D one. */
+static double pulse_source(const oracle_sim* s, double x, double y, double t) {
+    const oracle_params* p = &s->p;
+    const double cx = p->xc * cos(p->omega * t) - p->yc * sin(p->omega * t);
+    const double cy = p->xc * sin(p->omega * t) + p->yc * cos(p->omega * t);
+    const double s2 = p->sigma0 * p->sigma0 + 2.0 * p->D0 * t;
+    const double rx = x - cx, ry = y - cy, r2 = rx * rx + ry * ry;
+    const double phia = p->sigma0 * p->sigma0 / s2 * exp(-r2 / (2.0 * s2));
+    const double gx = -rx / s2 * phia, gy = -ry / s2 * phia;       /* grad phi_a */
+    const double lap = (r2 / (s2 * s2) - 2.0 / s2) * phia;          /* laplacian phi_a */
+    const double dD = p->D0 * p->D_amp * sin(PI * x) * sin(PI * y); /* D - D0 */
+    const double dDx = p->D0 * p->D_amp * PI * cos(PI * x) * sin(PI * y);
+    const double dDy = p->D0 * p->D_amp * PI * sin(PI * x) * cos(PI * y);
+    return -(dDx * gx + dDy * gy + dD * lap);
+}
+
+void oracle_pulse_source(const oracle_sim* s, double t, double* out) {
+    for (int j = 0; j < s->p.ny; ++j)
+        for (int i = 0; i < s->p.nx; ++i)
+            out[(size_t)j * s->p.nx + i] = pulse_source(s, node_x(s, i), node_y(s, j), t);
+}
+
+/* Initial condition g_i = g_i^eq(phi_0, u) (Sec. 3). */
+void oracle_init_equilibrium(oracle_sim* s, const double* phi0) {
+    for (int j = 0; j < s->p.ny; ++j)
+        for (int i = 0; i < s->p.nx; ++i) {
+            const size_t k = (size_t)j * s->p.nx + i;
+            const double u[2] = {s->ux[k], s->uy[k]};
+            double geq[Q];
+            equilibrium(&s->L, phi0[k], u, geq);
+            for (int q = 0; q < Q; ++q) s->g[AT(s, q, j, i)] = geq[q];
+        }
+    s->step = 0;
+    s->S_prev_valid = 0;
+}
+
+/* d_b u_a at node (i, j): du[a][b]. */
+static void grad_u(const oracle_sim* s, int i, int j, double du[2][2]) {
+    const int nx = s->p.nx, ny = s->p.ny;
+    const double* f[2] = {s->ux, s->uy};
+    for (int a = 0; a < 2; ++a) {
+        const double* u = f[a];
+        /* x derivative */
+        if (nx == 1) {
+            du[a][0] = 0.0;
+        } else if (s->p.grad_mode == 1 && i == 0) {
+            du[a][0] = (u[(size_t)j * nx + 1] - u[(size_t)j * nx]) / s->p.dx;
+        } else if (s->p.grad_mode == 1 && i == nx - 1) {
+            du[a][0] = (u[(size_t)j * nx + i] - u[(size_t)j * nx + i - 1]) / s->p.dx;
+        } else {
+            const int ip = (i + 1) % nx, im = (i - 1 + nx) % nx;
+            du[a][0] = (u[(size_t)j * nx + ip] - u[(size_t)j * nx + im]) / (2.0 * s->p.dx);
+        }
+        /* y derivative */
+        if (ny == 1) {
+            du[a][1] = 0.0;
+        } else if (s->p.grad_mode == 1 && j == 0) {
+            du[a][1] = (u[(size_t)nx + i] - u[i]) / s->p.dx;
+        } else if (s->p.grad_mode == 1 && j == ny - 1) {
+            du[a][1] = (u[(size_t)j * nx + i] - u[(size_t)(j - 1) * nx + i]) / s->p.dx;
+        } else {
+            const int jp = (j + 1) % ny, jm = (j - 1 + ny) % ny;
+            du[a][1] = (u[(size_t)jp * nx + i] - u[(size_t)jm * nx + i]) / (2.0 * s->p.dx);
+        }
+    }
+}
+
+static void node_taus(const oracle_sim* s, size_t k, double* tau1, double* tau2) {
+    *tau1 = s->p.tau1_const > 0.0 ? s->p.tau1_const : tau1_from_kappa(&s->L, s->D[k], s->p.dt);
+    *tau2 = s->p.tau2_mode == 1 ? s->p.tau2 : tau2_from_magic(*tau1, s->p.magic);
+}
+
+/* One time step over rows [j0, j1): collide each node, then push the post-collision value
+ * to x + e_i dt (periodic), Eq. (14). */
+static void step_rows(oracle_sim* s, int j0, int j1, double t_n, double t_nm1) {
+    const int nx = s->p.nx, ny = s->p.ny;
+    const double dt = s->p.dt;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (int j = j0; j < j1; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            const size_t k = (size_t)j * nx + i;
+            double g[Q], post[Q], G[Q], Fn[Q], Fnm1[Q];
+            for (int q = 0; q < Q; ++q) g[q] = s->g[AT(s, q, j, i)];
+            const double u[2] = {s->ux[k], s->uy[k]};
+            double tau1, tau2, phi;
+            node_taus(s, k, &tau1, &tau2);
+            collide_trtr(&s->L, g, u, tau1, tau2, post, &phi);
+
+            double du[2][2];
+            grad_u(s, i, j, du);
+            aux_G(&s->L, phi, u, du, tau1, G);
+
+            double Sn = 0.0, Snm1 = 0.0;
+            if (s->p.src_mode == 1) {
+                Sn = s->S_cur[k];
+                Snm1 = s->S_prev_valid ? s->S_prev[k] : Sn;
+            } else if (s->p.src_mode == 2) {
+                const double x = node_x(s, i), y = node_y(s, j);
+                Sn = pulse_source(s, x, y, t_n);
+                Snm1 = s->step > 0 ? pulse_source(s, x, y, t_nm1) : Sn;
+            }
+            source_F(&s->L, Sn, u, tau1, Fn);
+            source_F(&s->L, Snm1, u, tau1, Fnm1);
+
+            for (int q = 0; q < Q; ++q) {
+                const double dtF = (dt * dt / 2.0) * (Fn[q] - Fnm1[q]) / dt; /* dt^2/2 d_t F_i */
+                post[q] = post[q] + dt * G[q] + dt * Fn[q] + dtF;
+                const int it = ((i + EHAT[q][0]) % nx + nx) % nx;
+                const int jt = ((j + EHAT[q][1]) % ny + ny) % ny;
+                s->gnext[AT(s, q, jt, it)] = post[q];
+            }
+        }
+    }
+}
+
+void oracle_step(oracle_sim* s, long nsteps) {
+    for (long n = 0; n < nsteps; ++n) {
+        const double t_n = (double)s->step * s->p.dt;
+        const double t_nm1 = (double)(s->step - 1) * s->p.dt;
+        step_rows(s, 0, s->p.ny, t_n, t_nm1);
+        double* tmp = s->g;
+        s->g = s->gnext;
+        s->gnext = tmp;
+        if (s->p.src_mode == 1) {
+            memcpy(s->S_prev, s->S_cur, s->n * sizeof(double));
+            s->S_prev_valid = 1;
+        }
+        s->step += 1;
+    }
+}
+
+/* Timing sample: the collide-and-push work of one step restricted to rows [j0, j1), written
+ * into the scratch array only (the state does not advance).  Used by the CPU baseline. */
+void oracle_step_rows_sample(oracle_sim* s, int j0, int j1) {
+    const double t_n = (double)s->step * s->p.dt;
+    step_rows(s, j0, j1, t_n, t_n - s->p.dt);
+}
+
+long oracle_step_count(const oracle_sim* s) { return s->step; }
+
+/* phi(x, t_n) = sum_i g_i(x, t_n). */
+void oracle_phi(const oracle_sim* s, double* out) {
+    for (size_t k = 0; k < s->n; ++k) {
+        double phi = 0.0;
+        for (int q = 0; q < Q; ++q) phi += s->g[(size_t)q * s->n + k];
+        out[k] = phi;
+    }
+}
+
+void oracle_get_g(const oracle_sim* s, double* out) { memcpy(out, s->g, Q * s->n * sizeof(double)); }
+
+/* Sets the pre-collision state g_i(x, t_n) and the step counter n. */
+void oracle_set_g(oracle_sim* s, const double* g, long step) {
+    memcpy(s->g, g, Q * s->n * sizeof(double));
+    s->step = step;
+    s->S_prev_valid = 0;
+}
+
+double oracle_mass(const oracle_sim* s) {
+    double m = 0.0;
+    for (size_t k = 0; k < s->n; ++k)
+        for (int q = 0; q < Q; ++q) m += s->g[(size_t)q * s->n + k];
+    return m;
+}
+
+/* RMS error, Eq. (33) [eq19]: E_r = sqrt(sum |phi - phi_ref|^2 / (Nx Ny)), and the relative
+ * L2 error ||phi - phi_ref|| / ||phi_ref||. */
+void oracle_error(const oracle_sim* s, const double* phi_ref, double* rms, double* rel_l2) {
+    double num = 0.0, den = 0.0;
+    for (size_t k = 0; k < s->n; ++k) {
+        double phi = 0.0;
+        for (int q = 0; q < Q; ++q) phi += s->g[(size_t)q * s->n + k];
+        const double d = phi - phi_ref[k];
+        num += d * d;
+        den += phi_ref[k] * phi_ref[k];
+    }
+    *rms = sqrt(num / (double)s->n);
+    *rel_l2 = den > 0.0 ? sqrt(num / den) : sqrt(num);
+}
+
+int oracle_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,439 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by the mathematics.
+
+Every pin is a plain function ``pin_*(lib)`` that raises AssertionError on failure, so the
+same set runs against the real oracle (tests/test_oracle_pins.py) and against copies of
+it with planted mistakes (tests/test_oracle_mutants.py), each of which must fail at least
+one pin.  None of them re-types the oracle's population-space formulas: they use the
+moment-space statement in ``_moments.py``, quadrature identities, closed-form solutions,
+finite-difference residuals and brute force on tiny grids.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+import oracle
+from paper_2312_10316_gb300 import workloads as W
+
+from . import _moments as MS
+
+EX, EY = MS.EX, MS.EY
+
+
+def _rng(seed):
+    return np.random.default_rng(seed)
+
+
+# ---------------------------------------------------------------------------- node level
+
+
+def pin_lattice(lib):
+    """D2Q9 weights and velocities (Sec. 2.2): sum w = 1, sum w e_a e_b = cs^2 d_ab,
+    fourth-order isotropy sum w e_x^2 e_y^2 = cs^4, sum w e_x^4 = 3 cs^4."""
+    ex, ey, w = oracle.d2q9(lib)
+    assert np.allclose(w.sum(), 1.0, atol=1e-15)
+    assert np.allclose([np.sum(w * ex * ex), np.sum(w * ey * ey), np.sum(w * ex * ey)], [1 / 3, 1 / 3, 0], atol=1e-15)
+    assert abs(np.sum(w * ex**2 * ey**2) - 1 / 9) < 1e-15
+    assert abs(np.sum(w * ex**4) - 3 / 9) < 1e-15
+    assert np.array_equal(ex, EX) and np.array_equal(ey, EY)
+
+
+def pin_equilibrium_moments(lib):
+    """Hermite moments of g^eq (Eq. (6)) are phi, phi u, phi u u and the D2Q9-supported
+    third-order ones (D2Q9 quadrature exactness), in physical units for several c."""
+    rng = _rng(1)
+    for dx, dt in ((1.0, 1.0), (0.1, 0.02), (2.0 / 64, 1.4e-3)):
+        c = dx / dt
+        cs2 = c * c / 3
+        e = np.stack([c * EX, c * EY])
+        for _ in range(5):
+            phi = rng.uniform(0.1, 2.0)
+            u = c * rng.uniform(-0.4, 0.4, size=2)
+            g = oracle.equilibrium(dx, dt, phi, u[0], u[1], lib)
+            assert abs(g.sum() - phi) < 1e-13 * phi
+            assert np.allclose(e @ g, phi * u, atol=1e-13 * c * phi)
+            H2 = np.einsum("ai,bi->abi", e, e) - cs2 * np.eye(2)[:, :, None]
+            assert np.allclose(np.einsum("abi,i->ab", H2, g), phi * np.outer(u, u), atol=1e-12 * c * c * phi)
+            hxxy = e[0] ** 2 * e[1] - cs2 * e[1]
+            hxyy = e[0] * e[1] ** 2 - cs2 * e[0]
+            assert abs(hxxy @ g - phi * u[0] ** 2 * u[1]) < 1e-12 * c**3 * phi
+            assert abs(hxyy @ g - phi * u[0] * u[1] ** 2) < 1e-12 * c**3 * phi
+
+
+def pin_collision_moment_space(lib):
+    """TRT-R collision (Eq. (12)) equals the moment-space relaxation: first-order
+    non-equilibrium by (1 - 1/tau1), second-order by (1 - 1/tau2), higher orders projected
+    onto the equilibrium; unit-independent once u is scaled by c."""
+    rng = _rng(2)
+    for dx, dt in ((1.0, 1.0), (0.1, 0.02)):
+        c = dx / dt
+        for _ in range(20):
+            g = rng.uniform(0.0, 0.3, size=9)
+            uh = rng.uniform(-0.3, 0.3, size=2)
+            tau1 = rng.uniform(0.51, 2.0)
+            tau2 = rng.uniform(0.51, 2.0)
+            out = oracle.collide(dx, dt, g, c * uh[0], c * uh[1], tau1, tau2, lib)
+            ref = MS.collision_matrix(uh[0], uh[1], tau1, tau2) @ g
+            assert np.allclose(out, ref, rtol=0, atol=1e-14), (out - ref)
+
+
+def pin_aux_term_moments(lib):
+    """G (Eq. (16)): zero mass, first moment (1 - 1/(2 tau1)) phi (u.grad)u, no second moment."""
+    rng = _rng(3)
+    for dx, dt in ((1.0, 1.0), (0.05, 0.01)):
+        c = dx / dt
+        e = np.stack([c * EX, c * EY])
+        for _ in range(10):
+            phi = rng.uniform(0.1, 2.0)
+            u = c * rng.uniform(-0.3, 0.3, size=2)
+            du = rng.uniform(-3.0, 3.0, size=4)  # d_x u_x, d_y u_x, d_x u_y, d_y u_y
+            tau1 = rng.uniform(0.51, 2.0)
+            G = oracle.aux_G(dx, dt, phi, u[0], u[1], du, tau1, lib)
+            adv = np.array([u[0] * du[0] + u[1] * du[1], u[0] * du[2] + u[1] * du[3]])
+            k = 1.0 - 1.0 / (2.0 * tau1)
+            scale = max(1.0, np.abs(k * phi * adv).max())
+            assert abs(G.sum()) < 1e-13 * scale
+            assert np.allclose(e @ G, k * phi * adv, rtol=1e-12, atol=1e-13 * scale)
+            assert np.allclose(e[0] * e[1] @ G, 0.0, atol=1e-12 * c * scale)
+            assert np.allclose((e[0] ** 2 - e[1] ** 2) @ G, 0.0, atol=1e-12 * c * scale)
+
+
+def pin_source_moments(lib):
+    """F (Eq. (3)): zeroth moment S, first moment (1 - 1/(2 tau1)) u S, no second moment."""
+    rng = _rng(4)
+    for dx, dt in ((1.0, 1.0), (0.05, 0.01)):
+        c = dx / dt
+        e = np.stack([c * EX, c * EY])
+        for _ in range(10):
+            S = rng.uniform(-2.0, 2.0)
+            u = c * rng.uniform(-0.3, 0.3, size=2)
+            tau1 = rng.uniform(0.51, 2.0)
+            F = oracle.source_F(dx, dt, S, u[0], u[1], tau1, lib)
+            k = 1.0 - 1.0 / (2.0 * tau1)
+            assert abs(F.sum() - S) < 1e-14 * max(1, abs(S))
+            assert np.allclose(e @ F, k * u * S, rtol=1e-12, atol=1e-13 * c)
+            assert abs(e[0] * e[1] @ F) < 1e-12 * c * c
+
+
+def pin_relaxation_times(lib):
+    """tau1 from kappa = (tau1 - 1/2) cs^2 dt (Sec. 2.4) and Lambda = (tau1-1/2)(tau2-1/2)
+    (Eq. (28)); the Fourier-decay pin checks the former against the dynamics."""
+    for D, dx, dt in ((1e-3, 2 / 64, 1.4e-3), (0.05, 0.1, 0.01)):
+        t1 = oracle.tau1(D, dx, dt, lib)
+        cs2 = (dx / dt) ** 2 / 3
+        assert abs((t1 - 0.5) * cs2 * dt - D) < 1e-15 * max(1, D) + 1e-12 * D
+        t2 = oracle.tau2_magic(t1, 1 / 12, lib)
+        assert abs((t1 - 0.5) * (t2 - 0.5) - 1 / 12) < 1e-14
+
+
+# ---------------------------------------------------------------------------- grid level
+
+
+def _tiny_setup(nx, ny, seed, src_mode=0):
+    dx, dt = 0.5, 0.1
+    c = dx / dt
+    omega = 0.3 * c / max(nx, ny)  # |u| / c <= ~0.3 on the grid
+    x0 = -dx * (nx // 2)
+    y0 = -dx * (ny // 2)
+    x = x0 + dx * np.arange(nx)
+    y = y0 + dx * np.arange(ny)
+    X, Y = np.meshgrid(x, y, indexing="xy")
+    ux, uy = -omega * Y, omega * X
+    rng = _rng(seed)
+    D = rng.uniform(0.3, 1.5, size=(ny, nx)) * (dx * dx / dt) / 3.0 * 0.5  # tau1 in (0.65, 1.25)
+    p = oracle.SimParams(nx=nx, ny=ny, dx=dx, dt=dt, x0=x0, y0=y0, grad_mode=1, src_mode=src_mode)
+    return p, X, Y, ux, uy, D, omega
+
+
+def _expected_step_matrix(p, X, Y, ux, uy, D, omega):
+    """Brute-force statement of one step: node-local moment-space map, then a push by e_i."""
+    nx, ny, dx, dt = p.nx, p.ny, p.dx, p.dt
+    c = dx / dt
+    n = nx * ny
+    A = np.zeros((9 * n, 9 * n))
+    for j in range(ny):
+        for i in range(nx):
+            k = j * nx + i
+            tau1 = 0.5 + 3.0 * D[j, i] * dt / (dx * dx)
+            tau2 = 0.5 + (1 / 12) / (tau1 - 0.5)
+            uh = (ux[j, i] / c, uy[j, i] / c)
+            # (u.grad)u for the rigid rotation is -omega^2 (x, y); lattice units: * dt^2 / dx
+            a = (-omega**2 * X[j, i] * dt * dt / dx, -omega**2 * Y[j, i] * dt * dt / dx)
+            C = MS.collision_matrix(uh[0], uh[1], tau1, tau2, a[0], a[1], dt_g=1.0)
+            for q in range(9):
+                it = (i + int(EX[q])) % nx
+                jt = (j + int(EY[q])) % ny
+                row = q * n + jt * nx + it
+                for qq in range(9):
+                    A[row, qq * n + k] = C[q, qq]
+    return A
+
+
+def _oracle_step_matrix(lib, p, ux, uy, D):
+    sim = oracle.Sim(p, lib)
+    sim.set_fields(ux, uy, D)
+    n = p.nx * p.ny
+    A = np.zeros((9 * n, 9 * n))
+    e = np.zeros(9 * n)
+    for col in range(9 * n):
+        e[:] = 0.0
+        e[col] = 1.0
+        sim.set_g(e.reshape(9, p.ny, p.nx), step=0)
+        sim.step(1)
+        A[:, col] = sim.get_g().ravel()
+    sim.close()
+    return A
+
+
+def pin_tiny_grid_matrix(lib):
+    """The step is affine in g; on 4x4 and 5x3 periodic grids its matrix, built by applying
+    the oracle to unit vectors, equals the brute-force moment-space-plus-push statement
+    (rotation u, variable D, magic tau2, auxiliary term on)."""
+    for nx, ny, seed in ((4, 4, 10), (5, 3, 11)):
+        p, X, Y, ux, uy, D, omega = _tiny_setup(nx, ny, seed)
+        A = _oracle_step_matrix(lib, p, ux, uy, D)
+        B = _expected_step_matrix(p, X, Y, ux, uy, D, omega)
+        assert np.allclose(A, B, rtol=0, atol=1e-13), np.abs(A - B).max()
+
+
+def pin_tiny_grid_source(lib):
+    """Affine part with a source field (Eq. (14)): from g = 0 the first step leaves
+    dt F^n pushed by e_i (F^{-1} := F^n); the second adds dt F^n + (dt/2)(F^n - F^{n-1})
+    on top of the linear part."""
+    p, X, Y, ux, uy, D, omega = _tiny_setup(5, 3, 12, src_mode=1)
+    rng = _rng(13)
+    S1 = rng.uniform(-1.0, 1.0, size=(p.ny, p.nx))
+    S2 = rng.uniform(-1.0, 1.0, size=(p.ny, p.nx))
+    sim = oracle.Sim(p, lib)
+    sim.set_fields(ux, uy, D)
+    sim.set_source(S1)
+    sim.init_equilibrium(np.zeros((p.ny, p.nx)))
+    sim.step(1)
+    g1 = sim.get_g()
+    sim.set_source(S2)
+    sim.step(1)
+    g2 = sim.get_g().ravel()
+    sim.close()
+    A = _expected_step_matrix(p, X, Y, ux, uy, D, omega)
+    n = p.nx * p.ny
+    c = p.dx / p.dt
+
+    def pushed(S_eff):
+        b = np.zeros(9 * n)
+        for j in range(p.ny):
+            for i in range(p.nx):
+                tau1 = 0.5 + 3.0 * D[j, i] * p.dt / (p.dx * p.dx)
+                f = MS.source_populations(p.dt * S_eff[j, i], ux[j, i] / c, uy[j, i] / c, tau1)
+                for q in range(9):
+                    it = (i + int(EX[q])) % p.nx
+                    jt = (j + int(EY[q])) % p.ny
+                    b[q * n + jt * p.nx + it] = f[q]
+        return b
+
+    assert np.allclose(g1.ravel(), pushed(S1), atol=1e-14)
+    exp2 = A @ g1.ravel() + pushed(1.5 * S2 - 0.5 * S1)
+    assert np.allclose(g2, exp2, atol=1e-13)
+
+
+def pin_periodic_gradient(lib):
+    """Periodic central difference of a sheared u_x = U cos(k y) (grad_mode 0) has the closed
+    form d_y u_x = -U sin(k y) sin(k dx) / dx; checked through the step's affine matrix on a
+    single column of nodes where only the first moment sees it."""
+    nx, ny = 1, 8
+    dx, dt = 0.25, 0.05
+    c = dx / dt
+    U = 0.2 * c
+    k = 2 * math.pi / (ny * dx)
+    y = dx * np.arange(ny)
+    ux = (U * np.cos(k * y)).reshape(ny, 1)
+    uy = (0.1 * c * np.ones(ny)).reshape(ny, 1)
+    D = np.full((ny, 1), 0.25 * (dx * dx / dt) / 3.0)
+    p = oracle.SimParams(nx=nx, ny=ny, dx=dx, dt=dt, x0=0.0, y0=0.0, grad_mode=0)
+    A = _oracle_step_matrix(lib, p, ux, uy, D)
+    n = ny
+    for j in range(ny):
+        tau1 = 0.5 + 3.0 * D[j, 0] * dt / (dx * dx)
+        tau2 = 0.5 + (1 / 12) / (tau1 - 0.5)
+        dyux = -U * math.sin(k * y[j]) * math.sin(k * dx) / dx
+        a = (uy[j, 0] * dyux * dt * dt / dx, 0.0)
+        C = MS.collision_matrix(ux[j, 0] / c, uy[j, 0] / c, tau1, tau2, a[0], a[1], dt_g=1.0)
+        for q in range(9):
+            jt = (j + int(EY[q])) % ny
+            for qq in range(9):
+                assert abs(A[q * n + jt, qq * n + j] - C[q, qq]) < 1e-13
+
+
+def pin_fixed_point_and_mass(lib):
+    """Uniform phi with u = 0 and S = 0 is a fixed point (g^eq, B^neq = 0) up to rounding of
+    sum_i w_i phi (a few ulps, no drift over many steps);
+    with S = 0 the total sum phi is conserved (B_0^neq = 0) for a rotating, variable-D run."""
+    p = oracle.SimParams(nx=7, ny=5, dx=0.1, dt=0.01, grad_mode=1)
+    sim = oracle.Sim(p, lib)
+    z = np.zeros((5, 7))
+    sim.set_fields(z, z, np.full((5, 7), 0.2))
+    sim.init_equilibrium(np.full((5, 7), 0.75))
+    g0 = sim.get_g()
+    sim.step(100)
+    assert np.abs(sim.get_g() - g0).max() < 4e-16
+    sim.close()
+
+    pulse = W.Pulse(n=48, D_amp=0.5, courant=0.5)
+    f = W.fields(pulse)
+    p = oracle.SimParams(nx=48, ny=48, dx=pulse.dx, dt=pulse.dt, grad_mode=1)
+    sim = oracle.Sim(p, lib)
+    sim.set_fields(f["ux"], f["uy"], f["D"])
+    sim.init_equilibrium(f["phi0"])
+    m0 = sim.mass()
+    sim.step(200)
+    assert abs(sim.mass() - m0) < 1e-13 * abs(m0)
+    sim.close()
+
+
+def pin_fourier_decay(lib):
+    """u = 0, constant kappa, phi = 1 + eps cos(k x): the mode decays at kappa k^2 with
+    kappa = (tau1 - 1/2) cs^2 dt (Sec. 2.4); the lattice deviation shrinks as (k dx)^2."""
+    devs = []
+    for nx in (32, 64):
+        dx, dt = 1.0 / nx, 1.0 / nx**2  # diffusive scaling
+        kappa = 0.05
+        ny = 2
+        k = 2 * math.pi  # one wavelength over the unit box
+        x = dx * np.arange(nx)
+        phi0 = np.tile(1.0 + 0.01 * np.cos(k * x), (ny, 1))
+        p = oracle.SimParams(nx=nx, ny=ny, dx=dx, dt=dt, x0=0.0, y0=0.0, grad_mode=0)
+        sim = oracle.Sim(p, lib)
+        z = np.zeros((ny, nx))
+        sim.set_fields(z, z, np.full((ny, nx), kappa))
+        sim.init_equilibrium(phi0)
+        amps = []
+        n1 = nx * nx // 10
+        for _ in range(2):
+            sim.step(n1)
+            a = np.abs(np.fft.rfft(sim.phi()[0])[1]) * 2 / nx
+            amps.append(a)
+        rate = -math.log(amps[1] / amps[0]) / (n1 * dt)
+        devs.append(abs(rate / (kappa * k * k) - 1.0))
+        sim.close()
+    assert devs[1] < 2e-3, devs
+    assert devs[1] < devs[0] / 3.0, devs
+
+
+def _pde_residual_source(pulse, X, Y, t, h=1e-3):
+    """S = d_t phi + div(phi u) - div(D grad phi) for phi = phi_a, by fourth-order central
+    differences (independent of any closed form of S)."""
+
+    def phi(x, y, tt):
+        return W.phi_analytic(pulse, tt, x, y)
+
+    def D(x, y):
+        return pulse.D0 * (1 + pulse.D_amp * np.sin(np.pi * x) * np.sin(np.pi * y))
+
+    def d1(f, hh):
+        return (-f(2 * hh) + 8 * f(hh) - 8 * f(-hh) + f(-2 * hh)) / (12 * hh)
+
+    dphidt = d1(lambda s: phi(X, Y, t + s), h)
+    ux, uy = -pulse.omega * Y, pulse.omega * X
+
+    def flux_x(x, y):  # phi u_x - D d_x phi
+        return phi(x, y, t) * (-pulse.omega * y) - D(x, y) * d1(lambda s: phi(x + s, y, t), h)
+
+    def flux_y(x, y):
+        return phi(x, y, t) * (pulse.omega * x) - D(x, y) * d1(lambda s: phi(x, y + s, t), h)
+
+    div = d1(lambda s: flux_x(X + s, Y), h) + d1(lambda s: flux_y(X, Y + s), h)
+    return dphidt + div
+
+
+def pin_manufactured_source(lib):
+    """The oracle's built-in pulse source and the input generator's both equal the PDE
+    residual of phi_a for the variable-D equation (1); with D_amp = 0 phi_a is exact (S = 0)."""
+    for damp in (0.0, 0.5):
+        pulse = W.Pulse(n=16, D_amp=damp, D0=5e-3, sigma0=0.15)
+        X, Y = W.coords(pulse)
+        p = oracle.SimParams(nx=16, ny=16, dx=pulse.dx, dt=pulse.dt, src_mode=2, omega=pulse.omega,
+                             xc=pulse.xc, yc=pulse.yc, sigma0=pulse.sigma0, D0=pulse.D0, D_amp=pulse.D_amp)
+        sim = oracle.Sim(p, lib)
+        for t in (0.0, 0.37):
+            ref = _pde_residual_source(pulse, X, Y, t)
+            scale = max(1e-6, np.abs(ref).max()) if damp else 1.0
+            tol = 1e-6 * (pulse.D0 / pulse.sigma0**2)
+            assert np.abs(sim.pulse_source(t) - ref).max() < tol * max(1.0, scale), np.abs(sim.pulse_source(t) - ref).max()
+            assert np.abs(W.source(pulse, t) - ref).max() < tol * max(1.0, scale)
+        sim.close()
+
+
+def pin_pulse_source_time_levels(lib):
+    """src_mode 2 (built-in source) takes S^n = S(t_n) and S^{n-1} = S(t_{n-1}) (S^{-1} := S^0):
+    it equals src_mode 1 fed with the generator's S(t_n) every step."""
+    pulse = W.Pulse(n=24, D_amp=0.5, D0=5e-3, courant=0.5)
+    f = W.fields(pulse)
+    common = dict(nx=24, ny=24, dx=pulse.dx, dt=pulse.dt, grad_mode=1, omega=pulse.omega, xc=pulse.xc,
+                  yc=pulse.yc, sigma0=pulse.sigma0, D0=pulse.D0, D_amp=pulse.D_amp)
+    a = oracle.Sim(oracle.SimParams(src_mode=2, **common), lib)
+    b = oracle.Sim(oracle.SimParams(src_mode=1, **common), lib)
+    for s in (a, b):
+        s.set_fields(f["ux"], f["uy"], f["D"])
+    b.set_source(W.source(pulse, 0.0))
+    for s in (a, b):
+        s.init_equilibrium(f["phi0"])
+    for n in range(6):
+        a.step(1)
+        b.step(1)
+        b.set_source(W.source(pulse, (n + 1) * pulse.dt))
+    assert np.allclose(a.get_g(), b.get_g(), rtol=0, atol=1e-14)
+    a.close()
+    b.close()
+
+
+def convergence_orders(lib, cases=((0.0, 0.0, 0), (math.pi, 0.0, 0), (math.pi, 0.5, 2)), sizes=(64, 128, 256)):
+    """RMS error (Eq. (33)) against the closed-form pulse under diffusive scaling (tau1 fixed,
+    as in Sec. 3.2), at t = 0.05."""
+    T = 0.05
+    out = {}
+    for omega, damp, src in cases:
+        errs = []
+        for n in sizes:
+            pulse = W.Pulse(n=n, sigma0=0.1, D0=1e-2, D_amp=damp, omega=omega)
+            dx = pulse.dx
+            dt = 0.3 * dx * dx / (3 * pulse.D0)  # tau1 = 0.8
+            steps = int(round(T / dt))
+            dt = T / steps
+            f = W.fields(pulse)
+            p = oracle.SimParams(nx=n, ny=n, dx=dx, dt=dt, src_mode=src, grad_mode=1, omega=omega,
+                                 xc=pulse.xc, yc=pulse.yc, sigma0=pulse.sigma0, D0=pulse.D0, D_amp=damp)
+            sim = oracle.Sim(p, lib)
+            sim.set_fields(f["ux"], f["uy"], f["D"])
+            sim.init_equilibrium(f["phi0"])
+            sim.step(steps)
+            pa = W.phi_analytic(pulse, steps * dt)
+            errs.append(math.sqrt(np.mean((sim.phi() - pa) ** 2)))
+            sim.close()
+        out[(omega, damp)] = (errs, [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)])
+    return out
+
+
+def pin_second_order_convergence(lib, sizes=(64, 128, 256)):
+    """Second-order convergence to the closed-form pulse: diffusion, rotation, and variable D
+    with the manufactured source."""
+    for key, (errs, orders) in convergence_orders(lib, sizes=sizes).items():
+        assert min(orders) > 1.85, (key, errs, orders)
+        assert errs[-1] < 1e-4, (key, errs)
+
+
+ALL_PINS = [
+    pin_lattice,
+    pin_equilibrium_moments,
+    pin_collision_moment_space,
+    pin_aux_term_moments,
+    pin_source_moments,
+    pin_relaxation_times,
+    pin_tiny_grid_matrix,
+    pin_tiny_grid_source,
+    pin_periodic_gradient,
+    pin_fixed_point_and_mass,
+    pin_fourier_decay,
+    pin_manufactured_source,
+    pin_pulse_source_time_levels,
+    pin_second_order_convergence,
+]
