@@ -1,0 +1,399 @@
+#!/usr/bin/env python3
+"""Throughput of the fused TRT-R step (GLUPS) on the rotating-pulse workloads.
+
+One bench step is one TRT-R time step (pull-stream, phi, TRT-R relaxation, auxiliary term,
+source, store) over every node of the workload's grid, i.e. one launch of the fused step
+kernel.  Prints ONE JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on this machine's host cores on a bounded row
+sample of the same workload.  With N > 1 (torchrun) every rank advances its own copy of the
+workload (independent replicas, weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2312_10316_gb300 import workloads as W  # noqa: E402
+
+METRIC = "GLUPS & % HBM roofline, FP32 vs FP16-store at stated L2 err vs FP64 oracle"
+UNIT = "GLUPS"
+FALLBACK_HBM_GBS = 6800.0
+
+# name -> (pulse, precision key, bytes per stored population)
+WORKLOADS = {
+    "pulse4096_f32_varD_mms": (W.C2B_F32_4096, "f32", 4),
+    "pulse1024_f32_varD_mms": (W.C2A_F32_1024, "f32", 4),
+    "pulse8192_f16_varD_mms": (W.C3_HALF_8192, "f16", 2),
+    "pulse8192_bf16_varD_mms": (W.C3_HALF_8192, "bf16", 2),
+    "pulse8192_f32_varD_mms": (W.C3_HALF_8192, "f32", 4),
+    "pulse4096_f16_varD_mms": (W.C2B_F32_4096, "f16", 2),
+}
+DEFAULT_WORKLOAD = "pulse4096_f32_varD_mms"
+STEP_SOURCES = ["paper_2312_10316_gb300/csrc/trtr_step.cu", "paper_2312_10316_gb300/csrc/trtr_internal.cuh"]
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample length")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--parity-steps", type=int, default=1000,
+                    help="steps of the FP64 GPU comparison run that states the L2 error (0: skip)")
+    return ap.parse_args()
+
+
+def algorithmic_bytes_per_node(pop_bytes: int, field_bytes: int = 4) -> int:
+    """9 populations read + 9 written, plus u_x, u_y, D read once per node."""
+    return 2 * 9 * pop_bytes + 3 * field_bytes
+
+
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def step_kernel_sha() -> str:
+    h = hashlib.sha256()
+    for rel in STEP_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload: str):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_counters.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    entry = d.get(workload)
+    if not entry or entry.get("kernel_sha") != step_kernel_sha():
+        return None
+    return entry.get("dram_bytes_per_launch")
+
+
+# ------------------------------------------------------------------------------ clocks
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 8:
+                    continue
+                if self.uuid and self.uuid not in parts[0]:
+                    continue
+                rows.append(parts)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[4 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------- distributed
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+# ----------------------------------------------------------------------- CPU baseline
+
+
+def oracle_sample(pulse, target_seconds: float, warm_rows: int = 8):
+    """Times the FP64 oracle's collide-and-push work on row bands of the workload's grid.
+    Returns (nodes per second, threads, description, seconds per band, rows per band)."""
+    import oracle
+
+    f = W.fields(pulse)
+    sp = oracle.SimParams(nx=pulse.nx, ny=pulse.ny, dx=pulse.dx, dt=pulse.dt, x0=pulse.x0, y0=pulse.y0,
+                          src_mode=2 if pulse.D_amp else 0, grad_mode=1, omega=pulse.omega, xc=pulse.xc,
+                          yc=pulse.yc, sigma0=pulse.sigma0, D0=pulse.D0, D_amp=pulse.D_amp)
+    sim = oracle.Sim(sp)
+    sim.set_fields(f["ux"], f["uy"], f["D"])
+    sim.init_equilibrium(f["phi0"])
+    threads = oracle.num_threads()
+    j0 = pulse.ny // 2 - warm_rows // 2
+    t = time.perf_counter()
+    sim.step_rows_sample(j0, j0 + warm_rows)
+    rate = warm_rows * pulse.nx / max(time.perf_counter() - t, 1e-6)
+    return sim, rate, threads
+
+
+def cpu_baseline(pulse, seconds: float):
+    sim, rate, threads = oracle_sample(pulse, seconds)
+    rows = max(1, min(pulse.ny, int(rate * seconds / pulse.nx)))
+    j0 = max(0, pulse.ny // 2 - rows // 2)
+    t = time.perf_counter()
+    sim.step_rows_sample(j0, j0 + rows)
+    el = time.perf_counter() - t
+    sim.close()
+    value = rows * pulse.nx / el / 1e9
+    return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"one FP64 oracle step over rows {j0}..{j0 + rows - 1} of the {pulse.nx}x{pulse.ny} grid "
+                      f"({rows * pulse.nx} node updates, {el:.1f} s)"}
+
+
+# ------------------------------------------------------------------------------ ours
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2312_10316_gb300 import trtr as T
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    pulse, prec_key, pop_bytes = WORKLOADS[args.workload]
+    prec = T.PRECISIONS[prec_key]
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+    n_nodes = pulse.nx * pulse.ny
+
+    # ---- device-resident throughput
+    solver = T.pulse_solver(pulse, precision=prec, stream=sh)
+    solver.step(args.warmup)
+    solver.sync()
+    barrier(world)
+    torch.cuda.synchronize()
+    props = torch.cuda.get_device_properties(local)
+    uuid = str(getattr(props, "uuid", "")) or None
+    clocks = ClockSampler(("GPU-" + uuid) if uuid and not uuid.startswith("GPU-") else uuid)
+    clocks.start()
+    time.sleep(0.4)  # let the sampler take a reading at the start of the region
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    launches0 = solver.launches
+    with torch.cuda.stream(stream):
+        ev[0].record(stream)
+        for k in range(args.steps):
+            T.trtr_step(solver.ctx, 1)
+            ev[k + 1].record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    gpu_launches = solver.launches - launches0
+    per_launch = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    total_ms = max_over_ranks(total_ms, world)
+    ms_per_step = total_ms / args.steps
+    value = n_nodes * args.steps * world / (total_ms * 1e-3) / 1e9
+    avg_launch_ms = sum(per_launch) / len(per_launch)
+
+    bpn = algorithmic_bytes_per_node(pop_bytes)
+    peak, peak_kind = measured_hbm_peak()
+    achieved = bpn * n_nodes / (avg_launch_ms * 1e-3) / 1e9
+    traffic = ncu_traffic(args.workload)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_kind": f"{peak_kind} copy bandwidth", "bytes_per_node": bpn,
+                "kernel": "step_kernel", "median_launch_ms": round(statistics.median(per_launch), 5)}
+    phi_gpu = solver.moments() if args.parity_steps else None
+    solver.close()
+
+    # ---- stated L2 error against the FP64 path (outside the timed region)
+    parity = None
+    if args.parity_steps and rank == 0:
+        ks = min(args.parity_steps, args.steps + args.warmup)
+        with T.pulse_solver(pulse, precision=prec, stream=sh) as a, \
+                T.pulse_solver(pulse, precision=T.TRTR_F64, stream=sh) as b:
+            a.step(ks)
+            b.step(ks)
+            pa, pb = a.moments(), b.moments()
+        parity = {"rel_l2_vs_f64_gpu": float(np.linalg.norm(pa - pb) / np.linalg.norm(pb)), "steps": ks,
+                  "reference": "GPU FP64 path (matches the FP64 oracle to 1e-12)"}
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        f = W.fields(pulse)
+        pinned = {}
+        for k_, v in f.items():
+            t_ = torch.empty(v.shape, dtype=torch.float64, pin_memory=True)
+            t_.numpy()[...] = v
+            pinned[k_] = t_
+        out = torch.empty((pulse.ny, pulse.nx), dtype=torch.float64, pin_memory=True)
+        p = T.Params(nx=pulse.nx, ny=pulse.ny, dx=pulse.dx, dt=pulse.dt, x0=pulse.x0, y0=pulse.y0, precision=prec,
+                     src_mode=T.TRTR_SRC_PULSE if pulse.D_amp else T.TRTR_SRC_NONE)
+        with T.Solver(p, sh) as s:
+            s.set_pulse(pulse.omega, pulse.xc, pulse.yc, pulse.sigma0, pulse.D0, pulse.D_amp)
+            s.sync()
+            barrier(world)
+            t0 = time.perf_counter()
+            s.set_fields(pinned["ux"].numpy(), pinned["uy"].numpy(), pinned["D"].numpy())
+            s.init_equilibrium(pinned["phi0"].numpy())
+            s.step(args.steps)
+            s.moments(out.numpy())
+            el = time.perf_counter() - t0
+        el = max_over_ranks(el, world)
+        h2d = 4 * n_nodes * 8
+        d2h = n_nodes * 8
+        e2e = {"value": n_nodes * args.steps * world / el / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "scope": f"one solve per rank: u, D, phi0 host-to-device (pinned), init, {args.steps} steps, "
+                        f"phi device-to-host; bytes amortised over the steps"}
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+        return None
+
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": prec_key, "data": "synthetic",
+        "config": {"workload": args.workload, "nx": pulse.nx, "ny": pulse.ny, "precision": prec_key,
+                   "courant": pulse.courant, "D": f"{pulse.D0}*(1+{pulse.D_amp} sin(pi x) sin(pi y))",
+                   "source": "manufactured (in-kernel)" if pulse.D_amp else "none",
+                   "omega": pulse.omega, "sigma0": pulse.sigma0, "parallelism": f"replicas{world}",
+                   "l2_flush": f"inputs larger than L2: {2 * 9 * pop_bytes * n_nodes / 1e9:.2f} GB of populations"},
+        "roofline": roofline,
+        "gpu_launches": gpu_launches,
+        "clocks": clk,
+        "e2e": e2e,
+        "parity": parity,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(pulse, args.cpu_seconds)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return line
+
+
+# ------------------------------------------------------------------------- reference
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return None
+    pulse, prec_key, pop_bytes = WORKLOADS[args.workload]
+    budget = 150.0  # seconds for the whole --warmup W --steps K run
+    sim, rate, threads = oracle_sample(pulse, 0.0)
+    per_step = budget / max(1, args.steps + args.warmup)
+    rows = max(1, min(pulse.ny, int(rate * per_step / pulse.nx)))
+    j0 = max(0, pulse.ny // 2 - rows // 2)
+    for _ in range(args.warmup):
+        sim.step_rows_sample(j0, j0 + rows)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        sim.step_rows_sample(j0, j0 + rows)
+    el = time.perf_counter() - t
+    sim.close()
+    nodes = rows * pulse.nx
+    value = nodes * args.steps / el / 1e9
+    sample = (f"each step: one FP64 oracle step over rows {j0}..{j0 + rows - 1} of the {pulse.nx}x{pulse.ny} "
+              f"grid ({nodes} node updates)")
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "nx": pulse.nx, "ny": pulse.ny, "precision": prec_key,
+                   "courant": pulse.courant, "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse_args()
+    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

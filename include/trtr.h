@@ -1,0 +1,194 @@
+/*
+ * trtr.h -- C ABI of the GB300 (sm_103a) TRT-R lattice Boltzmann library for the
+ * convection-diffusion equation with variable coefficients
+ *
+ *     d_t phi + d_a(phi u_a) = d_a(kappa d_a phi) + S                    Eq. (1)
+ *
+ * (Yu, Qin, Yuan, Shu, arXiv 2312.10316).  One call of trtr_step advances every node of an
+ * nx x ny periodic D2Q9 grid by the evolution equation of Sec. 2.2,
+ *
+ *   g_i(x + e_i dt, t + dt) = g_i^eq + (1 - 1/tau1) w_i H_ia B_a^neq / cs^2
+ *                           + (1 - 1/tau2) w_i H_iab B_ab^neq / (2 cs^4)
+ *                           + dt G_i + dt F_i + dt^2/2 d_t F_i               Eq. (14)
+ *
+ * with the third-order Hermite equilibrium (Eq. (6)), the first-order discrete-velocity
+ * source F_i (Eq. (3)) and the space-derivative auxiliary term
+ * G_i = w_i e_ia/cs^2 (1 - 1/(2 tau1)) phi u_b d_b u_a (Eq. (16)).  kappa = D(x) sets
+ * tau1 = 1/2 + kappa / (cs^2 dt) (Sec. 2.4); tau2 is free, set either by the magic
+ * parameter Lambda = (tau1 - 1/2)(tau2 - 1/2) (Eq. (28)) or given directly.
+ *
+ * Equation numbers count the paper's displayed equations in order.
+ *
+ * Conventions shared by every call:
+ *  - Fields are row-major [ny][nx] doubles, x fastest; node (i, j) sits at
+ *    (x0 + i dx, y0 + j dx).  Populations are [9][ny][nx] doubles in the D2Q9 order
+ *    0:(0,0) 1:(1,0) 2:(-1,0) 3:(0,1) 4:(0,-1) 5:(1,1) 6:(-1,-1) 7:(1,-1) 8:(-1,1).
+ *  - Physical units: u in length/time, D (= kappa) in length^2/time, S in 1/time.
+ *  - `on_device` = 1: the pointer is CUDA device memory of the context's device, read
+ *    (or written) on the context's stream during the call only; 0: host memory.  Caller
+ *    memory is never retained.  All device buffers of a context are owned by the library.
+ *  - Every call returns a trtr_status; nothing throws across the ABI.  TRTR_EINVAL: bad
+ *    argument (nothing was changed); TRTR_ESTATE: call out of order (e.g. step before
+ *    init); TRTR_ECUDA: a CUDA call failed (trtr_last_error has the text; the context
+ *    should be destroyed); TRTR_EUNSTABLE: non-finite populations found by the stability
+ *    check.
+ *  - trtr_step only enqueues work on the context's stream: an asynchronous device fault
+ *    surfaces as TRTR_ECUDA from the next call that synchronises (moments, mass, error,
+ *    sample, get, save, sync).
+ *  - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef TRTR_H
+#define TRTR_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TRTR_OK = 0,
+    TRTR_EINVAL = 1,
+    TRTR_ENOMEM = 2,
+    TRTR_ECUDA = 3,
+    TRTR_EUNSTABLE = 4,
+    TRTR_ETIMEOUT = 5,
+    TRTR_ESTATE = 6
+} trtr_status;
+
+/* Storage / arithmetic of the populations.  F64: stored and computed in double.  F32:
+ * stored and computed in float.  F16_OFS / BF16_OFS: stored as the half-precision offset
+ * g_i - w_i phi_ref (round to nearest even), computed in float. */
+typedef enum { TRTR_F64 = 0, TRTR_F32 = 1, TRTR_F16_OFS = 2, TRTR_BF16_OFS = 3 } trtr_precision;
+
+typedef enum { TRTR_TAU2_MAGIC = 0, TRTR_TAU2_FIXED = 1 } trtr_tau2_mode;
+
+/* d_b u_a in G_i: second-order central differences; at the first and last column/row
+ * either wrapped periodically or one-sided (two-point), which is exact for a linear u
+ * such as a rigid rotation that jumps across the periodic seam. */
+typedef enum { TRTR_GRAD_PERIODIC = 0, TRTR_GRAD_ONESIDED_EDGE = 1 } trtr_grad_mode;
+
+/* Source S: none; a field set with trtr_set_source (S^n, the previous step's field kept as
+ * S^{n-1}); or the built-in manufactured source of the rotating pulse (trtr_set_pulse).
+ * d_t F_i is (F^n - F^{n-1}) / dt with F^{-1} := F^0 at the first step after init. */
+typedef enum { TRTR_SRC_NONE = 0, TRTR_SRC_FIELD = 1, TRTR_SRC_PULSE = 2 } trtr_src_mode;
+
+typedef struct {
+    int nx, ny;         /* nodes, >= 1 each; ny * round_up(nx, 32) < 2^31              */
+    double x0, y0;      /* coordinates of node (0, 0)                                  */
+    double dx, dt;      /* lattice spacing and time step (> 0); c = dx / dt             */
+    int precision;      /* trtr_precision                                               */
+    double phi_ref;     /* offset level for the *_OFS storage (ignored otherwise)       */
+    int tau2_mode;      /* trtr_tau2_mode                                               */
+    double magic;       /* Lambda for TRTR_TAU2_MAGIC (the paper uses 1/12)             */
+    double tau2;        /* tau2 for TRTR_TAU2_FIXED (> 1/2)                             */
+    double tau1_const;  /* > 0: tau1 everywhere, the D field is ignored; 0: from D(x)   */
+    int grad_mode;      /* trtr_grad_mode                                               */
+    int src_mode;       /* trtr_src_mode                                                */
+    int check_every;    /* > 0: trtr_step checks every k steps that all populations are
+                           finite and returns TRTR_EUNSTABLE if not (synchronises)      */
+} trtr_params;
+
+typedef struct trtr_ctx trtr_ctx; /* opaque, library-owned */
+
+/* Creates a context on the current CUDA device and allocates its device buffers (two
+ * population arrays, the coefficient fields, source buffers, reduction scratch).
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream) that every later call of this
+ * context enqueues on.  Validates the parameters (Sec. 2.2 lattice, Sec. 2.4 tau rules).
+ * *out receives the context, or NULL on error. */
+trtr_status trtr_create(const trtr_params* p, void* cuda_stream, trtr_ctx** out);
+
+/* Frees every device and host buffer of the context after synchronising its stream.
+ * NULL is accepted. */
+trtr_status trtr_destroy(trtr_ctx* ctx);
+
+/* Copies in the coefficient fields u_x, u_y and D (= kappa(x), Eq. (1)); D may be NULL when
+ * tau1_const > 0.  S (may be NULL) sets the source field for TRTR_SRC_FIELD as by
+ * trtr_set_source.  tau1 = 1/2 + 3 D dt / dx^2 must exceed 1/2 at every node (checked on
+ * host input only).  Fields persist until set again. */
+trtr_status trtr_set_fields(trtr_ctx* ctx, const double* ux, const double* uy, const double* D,
+                            const double* S, int on_device);
+
+/* TRTR_SRC_FIELD: sets S^n, the source of the next step (Eq. (3)); the source used by the
+ * previous step becomes S^{n-1}.  Before the first step after init, S^{n-1} := S^n. */
+trtr_status trtr_set_source(trtr_ctx* ctx, const double* S, int on_device);
+
+/* Rotating, spreading Gaussian pulse (the benchmark family of Sec. 3 on this periodic box):
+ * u = omega (-y, x); D = D0 (1 + D_amp sin(pi x) sin(pi y)); phi_a(x, t) =
+ * (s0^2/s^2) exp(-|x - c(t)|^2 / (2 s^2)), s^2 = s0^2 + 2 D0 t, c(t) = R(omega t)(xc, yc).
+ * Fills u and D on the device, and makes the manufactured source
+ * S = -div((D - D0) grad phi_a) (TRTR_SRC_PULSE), trtr_init_equilibrium(ctx, NULL, 0) and
+ * trtr_error_vs_pulse refer to this pulse.  sigma0 > 0, D0 >= 0. */
+trtr_status trtr_set_pulse(trtr_ctx* ctx, double omega, double xc, double yc, double sigma0, double D0,
+                           double D_amp);
+
+/* Initial condition g_i = g_i^eq(phi_0, u) (Sec. 3) and step counter n = 0.  phi0: [ny][nx];
+ * NULL = the pulse's phi_a(x, 0) (needs trtr_set_pulse).  Needs the fields. */
+trtr_status trtr_init_equilibrium(trtr_ctx* ctx, const double* phi0, int on_device);
+
+/* Advances n >= 0 time steps of Eq. (14): one fused pull-stream + collide kernel per step on
+ * the context's stream, ping-pong buffers, no host synchronisation (unless check_every). */
+trtr_status trtr_step(trtr_ctx* ctx, long n);
+
+/* phi(x, t_n) = sum_i g_i(x, t_n) of the pre-collision populations (B_0^neq = 0, Sec. 2.2),
+ * written as doubles [ny][nx].  Synchronises. */
+trtr_status trtr_moments(trtr_ctx* ctx, double* phi_out, int on_device);
+
+/* FP64 sum over nodes of phi(x, t_n) (conserved when S = 0).  Synchronises. */
+trtr_status trtr_mass(trtr_ctx* ctx, double* sum_phi);
+
+/* RMS error E_r = sqrt(sum (phi - phi_a)^2 / (nx ny)) (Eq. (33)) and relative L2 error
+ * ||phi - phi_a|| / ||phi_a|| against the pulse's closed form at t_n = n dt, accumulated in
+ * FP64.  Needs trtr_set_pulse.  Synchronises. */
+trtr_status trtr_error_vs_pulse(trtr_ctx* ctx, double* rms, double* rel_l2);
+
+/* As trtr_error_vs_pulse against a given field phi_ref [ny][nx] (rel_l2 falls back to the
+ * absolute L2 norm when phi_ref is all zero). */
+trtr_status trtr_error_vs(trtr_ctx* ctx, const double* phi_ref, int on_device, double* rms, double* rel_l2);
+
+/* Pre-collision populations g_i(x, t_n) as doubles [9][ny][nx].  Synchronises. */
+trtr_status trtr_get_populations(trtr_ctx* ctx, double* g_out, int on_device);
+
+/* Sets the pre-collision populations g_i(x, t_n) from doubles [9][ny][nx] (rounded to the
+ * storage precision) and the step counter n = step >= 0; S^{n-1} := S^n for the next step. */
+trtr_status trtr_set_populations(trtr_ctx* ctx, const double* g, int on_device, long step);
+
+/* g_i(x, t_n) at `count` node indices k = j * nx + i (host array), written to host
+ * out[count][9].  Synchronises. */
+trtr_status trtr_sample_populations(trtr_ctx* ctx, const long* nodes, int count, double* out);
+
+/* Step counter n and time t_n = n dt. */
+trtr_status trtr_time(const trtr_ctx* ctx, long* step, double* t);
+
+/* Checkpoint of the state (populations in storage precision, step counter, source
+ * buffers).  host_buf == NULL: *bytes receives the size needed.  Otherwise *bytes is the
+ * buffer size on input and the bytes written on output.  Synchronises. */
+trtr_status trtr_save(trtr_ctx* ctx, void* host_buf, size_t* bytes);
+
+/* Restores a checkpoint written by trtr_save from a context with the same nx, ny and
+ * precision; fields and pulse are not part of it. */
+trtr_status trtr_load(trtr_ctx* ctx, const void* host_buf, size_t bytes);
+
+/* Waits for the context's stream and reports any pending CUDA error. */
+trtr_status trtr_sync(trtr_ctx* ctx);
+
+/* Number of kernels the library enqueued on this context since creation (launch count). */
+trtr_status trtr_launch_count(const trtr_ctx* ctx, long* launches);
+
+/* Static text of a status code. */
+const char* trtr_status_str(trtr_status s);
+
+/* Last error message of the context ("" if none); valid until the next call on it. */
+const char* trtr_last_error(const trtr_ctx* ctx);
+
+/* The library's D2Q9 table: ex[9], ey[9] (integers) and w[9]. */
+void trtr_d2q9(int* ex, int* ey, double* w);
+
+/* ABI version (incremented on incompatible change). */
+int trtr_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TRTR_H */

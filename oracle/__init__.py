@@ -89,6 +89,9 @@ def load(path: str | None = None):
         "oracle_mass": (ctypes.c_double, [vp]),
         "oracle_error": (None, [vp, _dbl_p, _dbl_p, _dbl_p]),
         "oracle_num_threads": (ctypes.c_int, []),
+        "oracle_node_post": (None, [ctypes.POINTER(Params), _dbl_p, ctypes.c_double, ctypes.c_double, _dbl_p,
+                                    ctypes.c_double, ctypes.c_double, ctypes.c_double, _dbl_p]),
+        "oracle_pulse_source_at": (ctypes.c_double, [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -140,6 +143,18 @@ def source_F(dx, dt, S, ux, uy, tau1, lib=None) -> np.ndarray:
     lib = lib or load()
     out = np.zeros(Q)
     lib.oracle_source_F(dx, dt, S, ux, uy, tau1, _ptr(out))
+    return out
+
+
+def node_post(p: "SimParams", g, ux, uy, du, D, Sn=0.0, Snm1=0.0, lib=None) -> np.ndarray:
+    """Right-hand side of the evolution equation at one node (collision + dt G + dt F + dt^2/2 d_t F).
+    du = [d_x u_x, d_y u_x, d_x u_y, d_y u_y] in physical units."""
+    lib = lib or load()
+    cp = p.to_c()
+    g = _f64(g)
+    du = _f64(du)
+    out = np.zeros(Q)
+    lib.oracle_node_post(ctypes.byref(cp), _ptr(g), ux, uy, _ptr(du), D, Sn, Snm1, _ptr(out))
     return out
 
 
@@ -230,6 +245,9 @@ class Sim:
         out = np.zeros(self.shape)
         self.lib.oracle_pulse_source(self.h, float(t), _ptr(out))
         return out
+
+    def pulse_source_at(self, x, y, t) -> float:
+        return float(self.lib.oracle_pulse_source_at(self.h, float(x), float(y), float(t)))
 
     def init_equilibrium(self, phi0):
         phi0 = self._field(phi0)

@@ -359,27 +359,38 @@ static void node_taus(const oracle_sim* s, size_t k, double* tau1, double* tau2)
     *tau2 = s->p.tau2_mode == 1 ? s->p.tau2 : tau2_from_magic(*tau1, s->p.magic);
 }
 
+/* Right-hand side of Eq. (14) at one node: TRT-R collision, + dt G_i + dt F_i
+ * + dt^2/2 d_t F_i, with d_t F_i = (F_i^n - F_i^{n-1}) / dt. */
+static void node_post(const oracle_lattice* L, double dt, const double g[Q], const double u[2],
+                      const double du[2][2], double tau1, double tau2, double Sn, double Snm1, double post[Q]) {
+    double G[Q], Fn[Q], Fnm1[Q], phi;
+    collide_trtr(L, g, u, tau1, tau2, post, &phi);
+    aux_G(L, phi, u, du, tau1, G);
+    source_F(L, Sn, u, tau1, Fn);
+    source_F(L, Snm1, u, tau1, Fnm1);
+    for (int q = 0; q < Q; ++q) {
+        const double dtF = (dt * dt / 2.0) * (Fn[q] - Fnm1[q]) / dt; /* dt^2/2 d_t F_i */
+        post[q] = post[q] + dt * G[q] + dt * Fn[q] + dtF;
+    }
+}
+
 /* One time step over rows [j0, j1): collide each node, then push the post-collision value
  * to x + e_i dt (periodic), Eq. (14). */
 static void step_rows(oracle_sim* s, int j0, int j1, double t_n, double t_nm1) {
     const int nx = s->p.nx, ny = s->p.ny;
-    const double dt = s->p.dt;
 #ifdef _OPENMP
 #pragma omp parallel for schedule(static)
 #endif
     for (int j = j0; j < j1; ++j) {
         for (int i = 0; i < nx; ++i) {
             const size_t k = (size_t)j * nx + i;
-            double g[Q], post[Q], G[Q], Fn[Q], Fnm1[Q];
+            double g[Q], post[Q];
             for (int q = 0; q < Q; ++q) g[q] = s->g[AT(s, q, j, i)];
             const double u[2] = {s->ux[k], s->uy[k]};
-            double tau1, tau2, phi;
+            double tau1, tau2;
             node_taus(s, k, &tau1, &tau2);
-            collide_trtr(&s->L, g, u, tau1, tau2, post, &phi);
-
             double du[2][2];
             grad_u(s, i, j, du);
-            aux_G(&s->L, phi, u, du, tau1, G);
 
             double Sn = 0.0, Snm1 = 0.0;
             if (s->p.src_mode == 1) {
@@ -390,12 +401,8 @@ static void step_rows(oracle_sim* s, int j0, int j1, double t_n, double t_nm1) {
                 Sn = pulse_source(s, x, y, t_n);
                 Snm1 = s->step > 0 ? pulse_source(s, x, y, t_nm1) : Sn;
             }
-            source_F(&s->L, Sn, u, tau1, Fn);
-            source_F(&s->L, Snm1, u, tau1, Fnm1);
-
+            node_post(&s->L, s->p.dt, g, u, du, tau1, tau2, Sn, Snm1, post);
             for (int q = 0; q < Q; ++q) {
-                const double dtF = (dt * dt / 2.0) * (Fn[q] - Fnm1[q]) / dt; /* dt^2/2 d_t F_i */
-                post[q] = post[q] + dt * G[q] + dt * Fn[q] + dtF;
                 const int it = ((i + EHAT[q][0]) % nx + nx) % nx;
                 const int jt = ((j + EHAT[q][1]) % ny + ny) % ny;
                 s->gnext[AT(s, q, jt, it)] = post[q];
@@ -403,6 +410,22 @@ static void step_rows(oracle_sim* s, int j0, int j1, double t_n, double t_nm1) {
         }
     }
 }
+
+/* Single-node right-hand side of Eq. (14) for sampled checks: g (pre-collision), physical u,
+ * du = {d_x u_x, d_y u_x, d_x u_y, d_y u_y}, kappa = D, S^n, S^{n-1}; tau rules from p. */
+void oracle_node_post(const oracle_params* p, const double* g, double ux, double uy, const double* du, double D,
+                      double Sn, double Snm1, double* post) {
+    oracle_lattice L;
+    lattice_init(&L, p->dx, p->dt);
+    const double u[2] = {ux, uy};
+    const double d[2][2] = {{du[0], du[1]}, {du[2], du[3]}};
+    const double tau1 = p->tau1_const > 0.0 ? p->tau1_const : tau1_from_kappa(&L, D, p->dt);
+    const double tau2 = p->tau2_mode == 1 ? p->tau2 : tau2_from_magic(tau1, p->magic);
+    node_post(&L, p->dt, g, u, d, tau1, tau2, Sn, Snm1, post);
+}
+
+/* Manufactured pulse source at one point (src_mode 2 closed form). */
+double oracle_pulse_source_at(const oracle_sim* s, double x, double y, double t) { return pulse_source(s, x, y, t); }
 
 void oracle_step(oracle_sim* s, long nsteps) {
     for (long n = 0; n < nsteps; ++n) {

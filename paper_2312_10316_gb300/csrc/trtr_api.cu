@@ -1,0 +1,579 @@
+// trtr_api.cu -- the C ABI declared in include/trtr.h: validation, device memory of a
+// context, ping-pong bookkeeping and the host side of every call.  All compute runs in the
+// kernels of trtr_step.cu and trtr_aux.cu.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "trtr_internal.cuh"
+
+namespace {
+
+constexpr int kAbiVersion = 1;
+constexpr uint64_t kSaveMagic = 0x3152545254ULL;  // "TRTR1"
+
+struct SaveHeader {
+    uint64_t magic;
+    int32_t nx, ny, precision, src_mode;
+    int64_t step;
+    int32_t S_cur, S_prev;
+    uint64_t pop_bytes, src_bytes;
+};
+
+trtr_status fail(trtr_ctx* ctx, trtr_status s, const char* fmt, ...) {
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+        va_end(ap);
+    }
+    return s;
+}
+
+trtr_status cuda_fail(trtr_ctx* ctx, cudaError_t e, const char* where) {
+    return fail(ctx, TRTR_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define TRTR_CUDA(ctx, call, where)                     \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+    } while (0)
+
+size_t storage_size(int precision) {
+    switch (precision) {
+        case TRTR_F64: return 8;
+        case TRTR_F32: return 4;
+        case TRTR_F16_OFS:
+        case TRTR_BF16_OFS: return 2;
+        default: return 0;
+    }
+}
+
+size_t n_nodes(const trtr_ctx* ctx) { return (size_t)ctx->p.nx * (size_t)ctx->p.ny; }
+
+// Device staging buffer of at least `doubles` doubles.
+trtr_status ensure_tmp(trtr_ctx* ctx, size_t doubles) {
+    if (ctx->dtmp_len >= doubles) return TRTR_OK;
+    if (ctx->dtmp) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ctx->dtmp);
+        ctx->dtmp = nullptr;
+        ctx->dtmp_len = 0;
+    }
+    if (cudaMalloc(&ctx->dtmp, doubles * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, TRTR_ENOMEM, "cannot allocate %zu bytes of staging memory", doubles * sizeof(double));
+    }
+    ctx->dtmp_len = doubles;
+    return TRTR_OK;
+}
+
+// Stages `count` doubles of caller input on the device; returns the device pointer to read.
+trtr_status stage_in(trtr_ctx* ctx, const double* src, size_t count, int on_device, size_t slot,
+                     const double** dev) {
+    if (on_device) {
+        *dev = src;
+        return TRTR_OK;
+    }
+    trtr_status s = ensure_tmp(ctx, (slot + 1) * count);
+    if (s != TRTR_OK) return s;
+    double* d = ctx->dtmp + slot * count;
+    TRTR_CUDA(ctx, cudaMemcpyAsync(d, src, count * sizeof(double), cudaMemcpyHostToDevice, ctx->stream),
+              "host-to-device copy");
+    *dev = d;
+    return TRTR_OK;
+}
+
+trtr_status check_launch(trtr_ctx* ctx, cudaError_t e, const char* what) {
+    if (e != cudaSuccess) return cuda_fail(ctx, e, what);
+    return TRTR_OK;
+}
+
+trtr_status reduce(trtr_ctx* ctx, int kind, const double* ref_dev, double out[2]) {
+    trtr_status s = check_launch(ctx, trtr::launch_reduce(ctx, kind, ref_dev), "reduction launch");
+    if (s != TRTR_OK) return s;
+    TRTR_CUDA(ctx, cudaMemcpyAsync(ctx->hres, ctx->dres, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
+              "reduction result copy");
+    TRTR_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "reduction");
+    out[0] = ctx->hres[0];
+    out[1] = ctx->hres[1];
+    return TRTR_OK;
+}
+
+bool ready(trtr_ctx* ctx, trtr_status* s) {
+    if (!ctx->initialized) {
+        *s = fail(ctx, TRTR_ESTATE, "populations not initialised (call trtr_init_equilibrium or trtr_set_populations)");
+        return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int trtr_abi_version(void) { return kAbiVersion; }
+
+const char* trtr_status_str(trtr_status s) {
+    switch (s) {
+        case TRTR_OK: return "ok";
+        case TRTR_EINVAL: return "invalid argument";
+        case TRTR_ENOMEM: return "out of device memory";
+        case TRTR_ECUDA: return "CUDA error";
+        case TRTR_EUNSTABLE: return "non-finite populations (unstable run)";
+        case TRTR_ETIMEOUT: return "timed out";
+        case TRTR_ESTATE: return "call out of order";
+        default: return "unknown status";
+    }
+}
+
+const char* trtr_last_error(const trtr_ctx* ctx) { return ctx ? ctx->err : "null context"; }
+
+void trtr_d2q9(int* ex, int* ey, double* w) {
+    static const int EX[9] = {0, 1, -1, 0, 0, 1, -1, 1, -1};
+    static const int EY[9] = {0, 0, 0, 1, -1, 1, -1, -1, 1};
+    static const double W[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
+                                1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+    for (int i = 0; i < 9; ++i) {
+        if (ex) ex[i] = EX[i];
+        if (ey) ey[i] = EY[i];
+        if (w) w[i] = W[i];
+    }
+}
+
+trtr_status trtr_create(const trtr_params* p, void* cuda_stream, trtr_ctx** out) {
+    if (!out) return TRTR_EINVAL;
+    *out = nullptr;
+    if (!p) return TRTR_EINVAL;
+    if (p->nx < 1 || p->ny < 1) return TRTR_EINVAL;
+    if (!(p->dx > 0.0) || !(p->dt > 0.0) || !isfinite(p->dx) || !isfinite(p->dt)) return TRTR_EINVAL;
+    if (!isfinite(p->x0) || !isfinite(p->y0)) return TRTR_EINVAL;
+    const size_t es = storage_size(p->precision);
+    if (es == 0) return TRTR_EINVAL;
+    if (p->tau2_mode != TRTR_TAU2_MAGIC && p->tau2_mode != TRTR_TAU2_FIXED) return TRTR_EINVAL;
+    if (p->tau2_mode == TRTR_TAU2_MAGIC && !(p->magic > 0.0 && isfinite(p->magic))) return TRTR_EINVAL;
+    if (p->tau2_mode == TRTR_TAU2_FIXED && !(p->tau2 > 0.5 && isfinite(p->tau2))) return TRTR_EINVAL;
+    if (p->tau1_const != 0.0 && !(p->tau1_const > 0.5 && isfinite(p->tau1_const))) return TRTR_EINVAL;
+    if (p->grad_mode != TRTR_GRAD_PERIODIC && p->grad_mode != TRTR_GRAD_ONESIDED_EDGE) return TRTR_EINVAL;
+    if (p->src_mode < TRTR_SRC_NONE || p->src_mode > TRTR_SRC_PULSE) return TRTR_EINVAL;
+    if (p->check_every < 0 || !isfinite(p->phi_ref)) return TRTR_EINVAL;
+    const long long pitch = ((long long)p->nx + 31) / 32 * 32;
+    if (pitch * (long long)p->ny >= (1LL << 31)) return TRTR_EINVAL;
+
+    trtr_ctx* ctx = new (std::nothrow) trtr_ctx();
+    if (!ctx) return TRTR_ENOMEM;
+    memset(ctx, 0, sizeof(*ctx));
+    ctx->p = *p;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    ctx->esize = (int)es;
+    ctx->csize = p->precision == TRTR_F64 ? 8 : 4;
+    ctx->pitch = (int)pitch;
+    ctx->plane = (size_t)pitch * (size_t)p->ny;
+    ctx->S_cur = ctx->S_prev = -1;
+
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return TRTR_ECUDA;
+    }
+    ctx->red_blocks = ctx->num_sms * 4;
+
+    const size_t pop_bytes = trtr::kQ * ctx->plane * es;
+    const size_t fld_bytes = ctx->plane * ctx->csize;
+    struct {
+        void** ptr;
+        size_t bytes;
+    } allocs[] = {
+        {&ctx->pop[0], pop_bytes},
+        {&ctx->pop[1], pop_bytes},
+        {&ctx->ux, fld_bytes},
+        {&ctx->uy, fld_bytes},
+        {&ctx->Dh, fld_bytes},
+        {&ctx->S[0], p->src_mode == TRTR_SRC_FIELD ? fld_bytes : 0},
+        {&ctx->S[1], p->src_mode == TRTR_SRC_FIELD ? fld_bytes : 0},
+        {&ctx->tab_x, 2 * (size_t)pitch * ctx->csize},
+        {&ctx->tab_y, 2 * (size_t)p->ny * ctx->csize},
+        {(void**)&ctx->scratch, 2 * (size_t)ctx->red_blocks * sizeof(double)},
+        {(void**)&ctx->dres, 4 * sizeof(double)},
+    };
+    for (auto& a : allocs) {
+        if (a.bytes == 0) continue;
+        if (cudaMalloc(a.ptr, a.bytes) != cudaSuccess) {
+            cudaGetLastError();
+            trtr_destroy(ctx);
+            return TRTR_ENOMEM;
+        }
+    }
+    if (cudaMallocHost((void**)&ctx->hres, 4 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        trtr_destroy(ctx);
+        return TRTR_ENOMEM;
+    }
+    // Zero the padded population planes so that the pitch columns never hold garbage.
+    for (int b = 0; b < 2; ++b) {
+        if (cudaMemsetAsync(ctx->pop[b], 0, pop_bytes, ctx->stream) != cudaSuccess) {
+            cudaGetLastError();
+            trtr_destroy(ctx);
+            return TRTR_ECUDA;
+        }
+    }
+    *out = ctx;
+    return TRTR_OK;
+}
+
+trtr_status trtr_destroy(trtr_ctx* ctx) {
+    if (!ctx) return TRTR_OK;
+    cudaStreamSynchronize(ctx->stream);
+    cudaGetLastError();
+    void* ptrs[] = {ctx->pop[0], ctx->pop[1], ctx->ux, ctx->uy, ctx->Dh, ctx->S[0], ctx->S[1],
+                    ctx->tab_x, ctx->tab_y, ctx->scratch, ctx->dres, ctx->dtmp};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    if (ctx->hres) cudaFreeHost(ctx->hres);
+    cudaGetLastError();
+    delete ctx;
+    return TRTR_OK;
+}
+
+static trtr_status set_source_impl(trtr_ctx* ctx, const double* S, int on_device) {
+    const size_t n = n_nodes(ctx);
+    // The buffer that will hold S^n: not the one kept as S^{n-1}.
+    int dst;
+    if (ctx->S_cur < 0) dst = 0;
+    else if (ctx->S_prev == ctx->S_cur || ctx->S_prev < 0) dst = ctx->S_cur ^ 1;
+    else dst = ctx->S_cur;
+    const double* dev = nullptr;
+    trtr_status s = stage_in(ctx, S, n, on_device, 0, &dev);
+    if (s != TRTR_OK) return s;
+    s = check_launch(ctx, trtr::launch_convert_source(ctx, dev, ctx->S[dst]), "source conversion");
+    if (s != TRTR_OK) return s;
+    ctx->S_cur = dst;
+    return TRTR_OK;
+}
+
+trtr_status trtr_set_fields(trtr_ctx* ctx, const double* ux, const double* uy, const double* D, const double* S,
+                            int on_device) {
+    if (!ctx) return TRTR_EINVAL;
+    if (!ux || !uy) return fail(ctx, TRTR_EINVAL, "ux and uy are required");
+    if (!D && !(ctx->p.tau1_const > 0.0)) return fail(ctx, TRTR_EINVAL, "D is required unless tau1_const > 0");
+    if (S && ctx->p.src_mode != TRTR_SRC_FIELD) return fail(ctx, TRTR_EINVAL, "S given but src_mode is not FIELD");
+    const size_t n = n_nodes(ctx);
+    if (!on_device && D && !(ctx->p.tau1_const > 0.0)) {
+        for (size_t k = 0; k < n; ++k)
+            if (!(D[k] > 0.0) || !isfinite(D[k]))
+                return fail(ctx, TRTR_EINVAL, "D must be > 0 and finite at every node (node %zu: %g)", k, D[k]);
+    }
+    const double *dux, *duy, *dD = nullptr;
+    trtr_status s = stage_in(ctx, ux, n, on_device, 0, &dux);
+    if (s == TRTR_OK) s = stage_in(ctx, uy, n, on_device, 1, &duy);
+    if (s == TRTR_OK && D) s = stage_in(ctx, D, n, on_device, 2, &dD);
+    if (s != TRTR_OK) return s;
+    s = check_launch(ctx, trtr::launch_convert_fields(ctx, dux, duy, dD), "field conversion");
+    if (s != TRTR_OK) return s;
+    ctx->fields_set = true;
+    if (S) {
+        ctx->S_cur = ctx->S_prev = -1;
+        // staging slot 0 is reused: wait for the conversion above to have read it
+        if (!on_device) TRTR_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "field conversion");
+        s = set_source_impl(ctx, S, on_device);
+        if (s != TRTR_OK) return s;
+    }
+    return TRTR_OK;
+}
+
+trtr_status trtr_set_source(trtr_ctx* ctx, const double* S, int on_device) {
+    if (!ctx) return TRTR_EINVAL;
+    if (!S) return fail(ctx, TRTR_EINVAL, "S is NULL");
+    if (ctx->p.src_mode != TRTR_SRC_FIELD) return fail(ctx, TRTR_ESTATE, "src_mode is not TRTR_SRC_FIELD");
+    return set_source_impl(ctx, S, on_device);
+}
+
+trtr_status trtr_set_pulse(trtr_ctx* ctx, double omega, double xc, double yc, double sigma0, double D0,
+                           double D_amp) {
+    if (!ctx) return TRTR_EINVAL;
+    if (!(sigma0 > 0.0) || !(D0 >= 0.0) || !isfinite(omega) || !isfinite(xc) || !isfinite(yc) || !isfinite(D0) ||
+        !isfinite(D_amp) || !isfinite(sigma0))
+        return fail(ctx, TRTR_EINVAL, "bad pulse parameters");
+    if (!(ctx->p.tau1_const > 0.0) && !(D0 * (1.0 - fabs(D_amp)) > 0.0))
+        return fail(ctx, TRTR_EINVAL, "D0 (1 - |D_amp|) must be > 0 when tau1 comes from D");
+    ctx->pulse = trtr::Pulse{omega, xc, yc, sigma0, D0, D_amp};
+    trtr_status s = check_launch(ctx, trtr::launch_pulse_fields(ctx), "pulse fields");
+    if (s != TRTR_OK) return s;
+    ctx->pulse_set = true;
+    ctx->fields_set = true;
+    return TRTR_OK;
+}
+
+trtr_status trtr_init_equilibrium(trtr_ctx* ctx, const double* phi0, int on_device) {
+    if (!ctx) return TRTR_EINVAL;
+    if (!ctx->fields_set) return fail(ctx, TRTR_ESTATE, "fields not set");
+    if (!phi0 && !ctx->pulse_set) return fail(ctx, TRTR_ESTATE, "phi0 is NULL and no pulse is set");
+    if (ctx->p.src_mode == TRTR_SRC_PULSE && !ctx->pulse_set)
+        return fail(ctx, TRTR_ESTATE, "src_mode PULSE needs trtr_set_pulse");
+    const double* dev = nullptr;
+    if (phi0) {
+        if (!on_device) TRTR_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "staging");
+        trtr_status s = stage_in(ctx, phi0, n_nodes(ctx), on_device, 0, &dev);
+        if (s != TRTR_OK) return s;
+    }
+    trtr_status s = check_launch(ctx, trtr::launch_init_equilibrium(ctx, dev), "init");
+    if (s != TRTR_OK) return s;
+    ctx->step = 0;
+    ctx->initialized = true;
+    ctx->S_prev = -1;
+    return TRTR_OK;
+}
+
+trtr_status trtr_step(trtr_ctx* ctx, long n) {
+    if (!ctx) return TRTR_EINVAL;
+    if (n < 0) return fail(ctx, TRTR_EINVAL, "negative step count");
+    trtr_status s;
+    if (!ready(ctx, &s)) return s;
+    if (ctx->p.src_mode == TRTR_SRC_FIELD && ctx->S_cur < 0)
+        return fail(ctx, TRTR_ESTATE, "src_mode FIELD needs a source (trtr_set_source)");
+    if (ctx->p.src_mode == TRTR_SRC_PULSE && !ctx->pulse_set)
+        return fail(ctx, TRTR_ESTATE, "src_mode PULSE needs trtr_set_pulse");
+    for (long k = 0; k < n; ++k) {
+        cudaError_t e = trtr::launch_step(ctx);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "step launch");
+        ctx->launches += 1;
+        ctx->cur ^= 1;
+        ctx->step += 1;
+        if (ctx->p.src_mode == TRTR_SRC_FIELD) ctx->S_prev = ctx->S_cur;
+        if (ctx->p.check_every > 0 && (ctx->step % ctx->p.check_every) == 0) {
+            double r[2];
+            s = reduce(ctx, trtr::kReduceNonFinite, nullptr, r);
+            if (s != TRTR_OK) return s;
+            if (r[0] != 0.0)
+                return fail(ctx, TRTR_EUNSTABLE, "%.0f non-finite populations after step %ld", r[0], ctx->step);
+        }
+    }
+    return TRTR_OK;
+}
+
+trtr_status trtr_moments(trtr_ctx* ctx, double* phi_out, int on_device) {
+    if (!ctx) return TRTR_EINVAL;
+    if (!phi_out) return fail(ctx, TRTR_EINVAL, "phi_out is NULL");
+    trtr_status s;
+    if (!ready(ctx, &s)) return s;
+    const size_t n = n_nodes(ctx);
+    double* dev = phi_out;
+    if (!on_device) {
+        s = ensure_tmp(ctx, n);
+        if (s != TRTR_OK) return s;
+        dev = ctx->dtmp;
+    }
+    s = check_launch(ctx, trtr::launch_moments(ctx, dev), "moments");
+    if (s != TRTR_OK) return s;
+    if (!on_device)
+        TRTR_CUDA(ctx, cudaMemcpyAsync(phi_out, dev, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
+                  "device-to-host copy");
+    TRTR_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "moments");
+    return TRTR_OK;
+}
+
+trtr_status trtr_mass(trtr_ctx* ctx, double* sum_phi) {
+    if (!ctx) return TRTR_EINVAL;
+    if (!sum_phi) return fail(ctx, TRTR_EINVAL, "sum_phi is NULL");
+    trtr_status s;
+    if (!ready(ctx, &s)) return s;
+    double r[2];
+    s = reduce(ctx, trtr::kReduceMass, nullptr, r);
+    if (s == TRTR_OK) *sum_phi = r[0];
+    return s;
+}
+
+static void finish_error(const trtr_ctx* ctx, const double r[2], double* rms, double* rel) {
+    if (rms) *rms = sqrt(r[0] / (double)n_nodes(ctx));
+    if (rel) *rel = r[1] > 0.0 ? sqrt(r[0] / r[1]) : sqrt(r[0]);
+}
+
+trtr_status trtr_error_vs_pulse(trtr_ctx* ctx, double* rms, double* rel_l2) {
+    if (!ctx) return TRTR_EINVAL;
+    trtr_status s;
+    if (!ready(ctx, &s)) return s;
+    if (!ctx->pulse_set) return fail(ctx, TRTR_ESTATE, "no pulse set");
+    double r[2];
+    s = reduce(ctx, trtr::kReducePulse, nullptr, r);
+    if (s == TRTR_OK) finish_error(ctx, r, rms, rel_l2);
+    return s;
+}
+
+trtr_status trtr_error_vs(trtr_ctx* ctx, const double* phi_ref, int on_device, double* rms, double* rel_l2) {
+    if (!ctx) return TRTR_EINVAL;
+    if (!phi_ref) return fail(ctx, TRTR_EINVAL, "phi_ref is NULL");
+    trtr_status s;
+    if (!ready(ctx, &s)) return s;
+    const double* dev = nullptr;
+    if (!on_device) TRTR_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "staging");
+    s = stage_in(ctx, phi_ref, n_nodes(ctx), on_device, 0, &dev);
+    if (s != TRTR_OK) return s;
+    double r[2];
+    s = reduce(ctx, trtr::kReduceField, dev, r);
+    if (s == TRTR_OK) finish_error(ctx, r, rms, rel_l2);
+    return s;
+}
+
+trtr_status trtr_get_populations(trtr_ctx* ctx, double* g_out, int on_device) {
+    if (!ctx) return TRTR_EINVAL;
+    if (!g_out) return fail(ctx, TRTR_EINVAL, "g_out is NULL");
+    trtr_status s;
+    if (!ready(ctx, &s)) return s;
+    const size_t n = trtr::kQ * n_nodes(ctx);
+    double* dev = g_out;
+    if (!on_device) {
+        s = ensure_tmp(ctx, n);
+        if (s != TRTR_OK) return s;
+        dev = ctx->dtmp;
+    }
+    s = check_launch(ctx, trtr::launch_get_populations(ctx, dev), "get populations");
+    if (s != TRTR_OK) return s;
+    if (!on_device)
+        TRTR_CUDA(ctx, cudaMemcpyAsync(g_out, dev, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
+                  "device-to-host copy");
+    TRTR_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "get populations");
+    return TRTR_OK;
+}
+
+trtr_status trtr_set_populations(trtr_ctx* ctx, const double* g, int on_device, long step) {
+    if (!ctx) return TRTR_EINVAL;
+    if (!g || step < 0) return fail(ctx, TRTR_EINVAL, "g is NULL or step < 0");
+    if (!ctx->fields_set) return fail(ctx, TRTR_ESTATE, "fields not set");
+    const double* dev = nullptr;
+    if (!on_device) TRTR_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "staging");
+    trtr_status s = stage_in(ctx, g, trtr::kQ * n_nodes(ctx), on_device, 0, &dev);
+    if (s != TRTR_OK) return s;
+    s = check_launch(ctx, trtr::launch_set_populations(ctx, dev), "set populations");
+    if (s != TRTR_OK) return s;
+    ctx->step = step;
+    ctx->initialized = true;
+    ctx->S_prev = -1;
+    return TRTR_OK;
+}
+
+trtr_status trtr_sample_populations(trtr_ctx* ctx, const long* nodes, int count, double* out) {
+    if (!ctx) return TRTR_EINVAL;
+    if (count < 0 || (count > 0 && (!nodes || !out))) return fail(ctx, TRTR_EINVAL, "bad sample arguments");
+    trtr_status s;
+    if (!ready(ctx, &s)) return s;
+    if (count == 0) return TRTR_OK;
+    const long n = (long)n_nodes(ctx);
+    for (int k = 0; k < count; ++k)
+        if (nodes[k] < 0 || nodes[k] >= n) return fail(ctx, TRTR_EINVAL, "node index %ld out of range", nodes[k]);
+    // staging: count longs (rounded up to doubles) followed by 9 * count doubles
+    const size_t idx_d = ((size_t)count * sizeof(long) + sizeof(double) - 1) / sizeof(double);
+    TRTR_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "staging");
+    s = ensure_tmp(ctx, idx_d + (size_t)count * trtr::kQ);
+    if (s != TRTR_OK) return s;
+    long* dnodes = (long*)ctx->dtmp;
+    double* dout = ctx->dtmp + idx_d;
+    TRTR_CUDA(ctx, cudaMemcpyAsync(dnodes, nodes, count * sizeof(long), cudaMemcpyHostToDevice, ctx->stream),
+              "host-to-device copy");
+    s = check_launch(ctx, trtr::launch_sample(ctx, dnodes, count, dout), "sample");
+    if (s != TRTR_OK) return s;
+    TRTR_CUDA(ctx, cudaMemcpyAsync(out, dout, (size_t)count * trtr::kQ * sizeof(double), cudaMemcpyDeviceToHost,
+                                   ctx->stream),
+              "device-to-host copy");
+    TRTR_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "sample");
+    return TRTR_OK;
+}
+
+trtr_status trtr_time(const trtr_ctx* ctx, long* step, double* t) {
+    if (!ctx) return TRTR_EINVAL;
+    if (step) *step = ctx->step;
+    if (t) *t = (double)ctx->step * ctx->p.dt;
+    return TRTR_OK;
+}
+
+trtr_status trtr_save(trtr_ctx* ctx, void* host_buf, size_t* bytes) {
+    if (!ctx || !bytes) return TRTR_EINVAL;
+    trtr_status s;
+    if (!ready(ctx, &s)) return s;
+    const size_t pop_bytes = trtr::kQ * ctx->plane * ctx->esize;
+    const size_t src_bytes = ctx->p.src_mode == TRTR_SRC_FIELD ? 2 * ctx->plane * ctx->csize : 0;
+    const size_t need = sizeof(SaveHeader) + pop_bytes + src_bytes;
+    if (!host_buf) {
+        *bytes = need;
+        return TRTR_OK;
+    }
+    if (*bytes < need) return fail(ctx, TRTR_EINVAL, "buffer too small (%zu < %zu)", *bytes, need);
+    SaveHeader h;
+    memset(&h, 0, sizeof(h));
+    h.magic = kSaveMagic;
+    h.nx = ctx->p.nx;
+    h.ny = ctx->p.ny;
+    h.precision = ctx->p.precision;
+    h.src_mode = ctx->p.src_mode;
+    h.step = ctx->step;
+    h.S_cur = ctx->S_cur;
+    h.S_prev = ctx->S_prev;
+    h.pop_bytes = pop_bytes;
+    h.src_bytes = src_bytes;
+    char* b = (char*)host_buf;
+    memcpy(b, &h, sizeof(h));
+    TRTR_CUDA(ctx, cudaMemcpyAsync(b + sizeof(h), ctx->pop[ctx->cur], pop_bytes, cudaMemcpyDeviceToHost, ctx->stream),
+              "save copy");
+    if (src_bytes) {
+        const size_t half = src_bytes / 2;
+        TRTR_CUDA(ctx, cudaMemcpyAsync(b + sizeof(h) + pop_bytes, ctx->S[0], half, cudaMemcpyDeviceToHost, ctx->stream),
+                  "save copy");
+        TRTR_CUDA(ctx, cudaMemcpyAsync(b + sizeof(h) + pop_bytes + half, ctx->S[1], half, cudaMemcpyDeviceToHost,
+                                       ctx->stream),
+                  "save copy");
+    }
+    TRTR_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "save");
+    *bytes = need;
+    return TRTR_OK;
+}
+
+trtr_status trtr_load(trtr_ctx* ctx, const void* host_buf, size_t bytes) {
+    if (!ctx || !host_buf) return TRTR_EINVAL;
+    if (bytes < sizeof(SaveHeader)) return fail(ctx, TRTR_EINVAL, "checkpoint too small");
+    SaveHeader h;
+    memcpy(&h, host_buf, sizeof(h));
+    const size_t pop_bytes = trtr::kQ * ctx->plane * ctx->esize;
+    const size_t src_bytes = ctx->p.src_mode == TRTR_SRC_FIELD ? 2 * ctx->plane * ctx->csize : 0;
+    if (h.magic != kSaveMagic || h.nx != ctx->p.nx || h.ny != ctx->p.ny || h.precision != ctx->p.precision ||
+        h.src_mode != ctx->p.src_mode || h.pop_bytes != pop_bytes || h.src_bytes != src_bytes ||
+        bytes < sizeof(h) + pop_bytes + src_bytes || h.step < 0)
+        return fail(ctx, TRTR_EINVAL, "checkpoint does not match this context");
+    const char* b = (const char*)host_buf;
+    TRTR_CUDA(ctx, cudaMemcpyAsync(ctx->pop[ctx->cur], b + sizeof(h), pop_bytes, cudaMemcpyHostToDevice, ctx->stream),
+              "load copy");
+    if (src_bytes) {
+        const size_t half = src_bytes / 2;
+        TRTR_CUDA(ctx, cudaMemcpyAsync(ctx->S[0], b + sizeof(h) + pop_bytes, half, cudaMemcpyHostToDevice, ctx->stream),
+                  "load copy");
+        TRTR_CUDA(ctx, cudaMemcpyAsync(ctx->S[1], b + sizeof(h) + pop_bytes + half, half, cudaMemcpyHostToDevice,
+                                       ctx->stream),
+                  "load copy");
+        ctx->S_cur = h.S_cur;
+        ctx->S_prev = h.S_prev;
+    }
+    TRTR_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "load");
+    ctx->step = h.step;
+    ctx->initialized = true;
+    return TRTR_OK;
+}
+
+trtr_status trtr_sync(trtr_ctx* ctx) {
+    if (!ctx) return TRTR_EINVAL;
+    TRTR_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "sync");
+    TRTR_CUDA(ctx, cudaGetLastError(), "sync");
+    return TRTR_OK;
+}
+
+trtr_status trtr_launch_count(const trtr_ctx* ctx, long* launches) {
+    if (!ctx || !launches) return TRTR_EINVAL;
+    *launches = ctx->launches;
+    return TRTR_OK;
+}
+
+}  // extern "C"

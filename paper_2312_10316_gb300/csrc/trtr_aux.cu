@@ -1,0 +1,369 @@
+// trtr_aux.cu -- kernels around the step: coefficient fields, the pulse closed form,
+// equilibrium initialisation (shifted into the pull layout), the phi moment, the FP64
+// reductions (mass, RMS / relative L2 error of Eq. (33)) and population I/O.
+#include <math.h>
+
+#include <type_traits>
+
+#include "trtr_internal.cuh"
+
+namespace trtr {
+
+PulseTime pulse_at(const Pulse& p, double t) {
+    PulseTime r;
+    const double c = cos(p.omega * t), s = sin(p.omega * t);
+    r.cx = p.xc * c - p.yc * s;
+    r.cy = p.xc * s + p.yc * c;
+    const double s2 = p.sigma0 * p.sigma0 + 2.0 * p.D0 * t;
+    r.inv_s2 = 1.0 / s2;
+    r.amp = p.sigma0 * p.sigma0 / s2;
+    return r;
+}
+
+namespace {
+
+__constant__ int c_ex[kQ] = {0, 1, -1, 0, 0, 1, -1, 1, -1};
+__constant__ int c_ey[kQ] = {0, 0, 0, 1, -1, 1, -1, -1, 1};
+__constant__ double c_w[kQ] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
+                               1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+template <typename C>
+__global__ void convert_fields_kernel(C* ux, C* uy, C* Dh, const double* sux, const double* suy,
+                                      const double* sD, int nx, int ny, int pitch, double u_scale,
+                                      double d_scale, double dh_const, int use_const) {
+    const size_t n = (size_t)nx * ny;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(k / nx), i = (int)(k - (size_t)j * nx);
+        const size_t o = (size_t)j * pitch + i;
+        ux[o] = C(sux[k] * u_scale);
+        uy[o] = C(suy[k] * u_scale);
+        Dh[o] = C(use_const ? dh_const : sD[k] * d_scale);
+    }
+}
+
+template <typename C>
+__global__ void pulse_fields_kernel(C* ux, C* uy, C* Dh, C* tab_x, C* tab_y, int nx, int ny, int pitch,
+                                    double x0, double y0, double dx, double dt, Pulse pp, double dh_const,
+                                    int use_const) {
+    const size_t n = (size_t)nx * ny;
+    const double us = dt / dx, ds = dt / (dx * dx);
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(k / nx), i = (int)(k - (size_t)j * nx);
+        const double x = x0 + i * dx, y = y0 + j * dx;
+        const size_t o = (size_t)j * pitch + i;
+        ux[o] = C(-pp.omega * y * us);
+        uy[o] = C(pp.omega * x * us);
+        Dh[o] = C(use_const ? dh_const : pp.D0 * (1.0 + pp.D_amp * sin(M_PI * x) * sin(M_PI * y)) * ds);
+        if (j == 0) {
+            tab_x[i] = C(sin(M_PI * x));
+            tab_x[pitch + i] = C(cos(M_PI * x));
+        }
+        if (i == 0) {
+            tab_y[j] = C(sin(M_PI * y));
+            tab_y[ny + j] = C(cos(M_PI * y));
+        }
+    }
+}
+
+template <typename C>
+__global__ void convert_source_kernel(C* dst, const double* S, int nx, int ny, int pitch, double dt) {
+    const size_t n = (size_t)nx * ny;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(k / nx), i = (int)(k - (size_t)j * nx);
+        dst[(size_t)j * pitch + i] = C(dt * S[k]);
+    }
+}
+
+__device__ __forceinline__ double pulse_phi(const PulseTime& pt, double x, double y) {
+    const double rx = x - pt.cx, ry = y - pt.cy;
+    return pt.amp * exp(-0.5 * (rx * rx + ry * ry) * pt.inv_s2);
+}
+
+// Initial condition g_i(x) = g_i^eq(phi0(x), u(x)) stored in the pull layout:
+// P_i(x) = g_i(x + e_i).  Third-order Hermite equilibrium (Eq. (6)) in lattice units:
+// w_i phi [1 + 3 eu + 4.5 ((eu)^2 - |u|^2/3) + 4.5 ((eu)^3 - eu |u|^2)], eu = e_i . uhat.
+template <typename S, typename C>
+__global__ void init_eq_kernel(S* P, const C* ux, const C* uy, const double* phi0, int nx, int ny, int pitch,
+                               size_t plane, double x0, double y0, double dx, PulseTime pt, C phi_ref) {
+    const size_t n = (size_t)nx * ny;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(k / nx), i = (int)(k - (size_t)j * nx);
+        for (int q = 0; q < kQ; ++q) {
+            const int si = wrap(i + c_ex[q], nx), sj = wrap(j + c_ey[q], ny);
+            const double phi = phi0 ? phi0[(size_t)sj * nx + si] : pulse_phi(pt, x0 + si * dx, y0 + sj * dx);
+            const double u = (double)ux[(size_t)sj * pitch + si];
+            const double v = (double)uy[(size_t)sj * pitch + si];
+            const double eu = c_ex[q] * u + c_ey[q] * v;
+            const double uu = u * u + v * v;
+            const double geq = c_w[q] * phi * (1.0 + 3.0 * eu + 4.5 * (eu * eu - uu / 3.0) + 4.5 * (eu * eu * eu - eu * uu));
+            Store<S>::store(P + q * plane + (size_t)j * pitch + i, (C)geq, (C)(c_w[q]) * phi_ref);
+        }
+    }
+}
+
+// g_i(x, t_n) = P_i(x - e_i), decoded to the compute type.
+template <typename S, typename C>
+__device__ __forceinline__ C pulled(const S* P, int q, int i, int j, int nx, int ny, int pitch, size_t plane,
+                                    C phi_ref) {
+    const int si = wrap(i - c_ex[q], nx), sj = wrap(j - c_ey[q], ny);
+    return Store<S>::load(P + q * plane + (size_t)sj * pitch + si, (C)(c_w[q]) * phi_ref);
+}
+
+template <typename S, typename C>
+__device__ __forceinline__ double node_phi(const S* P, int i, int j, int nx, int ny, int pitch, size_t plane,
+                                           C phi_ref) {
+    double phi = 0.0;
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) phi += (double)pulled<S, C>(P, q, i, j, nx, ny, pitch, plane, phi_ref);
+    return phi;
+}
+
+template <typename S, typename C>
+__global__ void moments_kernel(double* out, const S* P, int nx, int ny, int pitch, size_t plane, C phi_ref) {
+    const size_t n = (size_t)nx * ny;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(k / nx), i = (int)(k - (size_t)j * nx);
+        out[k] = node_phi<S, C>(P, i, j, nx, ny, pitch, plane, phi_ref);
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Deterministic two-value block sum (fixed tree); result valid in thread 0.
+__device__ __forceinline__ void block_sum2(double& a, double& b) {
+    __shared__ double sa[kThreads / 32], sb[kThreads / 32];
+    a = warp_sum(a);
+    b = warp_sum(b);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        sa[w] = a;
+        sb[w] = b;
+    }
+    __syncthreads();
+    if (w == 0) {
+        a = lane < kThreads / 32 ? sa[lane] : 0.0;
+        b = lane < kThreads / 32 ? sb[lane] : 0.0;
+        a = warp_sum(a);
+        b = warp_sum(b);
+    }
+}
+
+// Per-block FP64 partial sums into scratch[2 * block + {0, 1}]:
+//  kind 0: sum phi;  1: sum (phi - phi_a)^2, sum phi_a^2;  2: same against phi_ref field;
+//  3: number of non-finite populations.
+template <typename S, typename C>
+__global__ void reduce_kernel(double* partial, const S* P, int nx, int ny, int pitch, size_t plane, C phi_ref,
+                              int kind, PulseTime pt, double x0, double y0, double dx, const double* ref) {
+    const size_t n = (size_t)nx * ny;
+    double a = 0.0, b = 0.0;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(k / nx), i = (int)(k - (size_t)j * nx);
+        if (kind == kReduceNonFinite) {
+            for (int q = 0; q < kQ; ++q) {
+                const double v = (double)pulled<S, C>(P, q, i, j, nx, ny, pitch, plane, phi_ref);
+                a += isfinite(v) ? 0.0 : 1.0;
+            }
+            continue;
+        }
+        const double phi = node_phi<S, C>(P, i, j, nx, ny, pitch, plane, phi_ref);
+        if (kind == kReduceMass) {
+            a += phi;
+        } else {
+            const double r = kind == kReducePulse ? pulse_phi(pt, x0 + i * dx, y0 + j * dx) : ref[k];
+            const double d = phi - r;
+            a += d * d;
+            b += r * r;
+        }
+    }
+    block_sum2(a, b);
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = a;
+        partial[2 * blockIdx.x + 1] = b;
+    }
+}
+
+__global__ void finish_kernel(double* out, const double* partial, int nblocks) {
+    double a = 0.0, b = 0.0;
+    for (int k = threadIdx.x; k < nblocks; k += blockDim.x) {
+        a += partial[2 * k];
+        b += partial[2 * k + 1];
+    }
+    block_sum2(a, b);
+    if (threadIdx.x == 0) {
+        out[0] = a;
+        out[1] = b;
+    }
+}
+
+template <typename S, typename C>
+__global__ void get_pop_kernel(double* g, const S* P, int nx, int ny, int pitch, size_t plane, C phi_ref) {
+    const size_t n = (size_t)nx * ny;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(k / nx), i = (int)(k - (size_t)j * nx);
+        for (int q = 0; q < kQ; ++q) g[q * n + k] = (double)pulled<S, C>(P, q, i, j, nx, ny, pitch, plane, phi_ref);
+    }
+}
+
+template <typename S, typename C>
+__global__ void set_pop_kernel(S* P, const double* g, int nx, int ny, int pitch, size_t plane, C phi_ref) {
+    const size_t n = (size_t)nx * ny;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(k / nx), i = (int)(k - (size_t)j * nx);
+        for (int q = 0; q < kQ; ++q) {
+            const int si = wrap(i + c_ex[q], nx), sj = wrap(j + c_ey[q], ny);
+            Store<S>::store(P + q * plane + (size_t)j * pitch + i, (C)g[q * n + (size_t)sj * nx + si],
+                            (C)(c_w[q]) * phi_ref);
+        }
+    }
+}
+
+template <typename S, typename C>
+__global__ void sample_kernel(double* out, const long* nodes, int count, const S* P, int nx, int ny, int pitch,
+                              size_t plane, C phi_ref) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count * kQ) return;
+    const int s = t / kQ, q = t - s * kQ;
+    const long k = nodes[s];
+    const int j = (int)(k / nx), i = (int)(k - (long)j * nx);
+    out[t] = (double)pulled<S, C>(P, q, i, j, nx, ny, pitch, plane, phi_ref);
+}
+
+int grid_for(const trtr_ctx* ctx, size_t n) {
+    const size_t want = (n + kThreads - 1) / kThreads;
+    const size_t cap = (size_t)ctx->num_sms * 8;
+    return (int)(want < 1 ? 1 : (want > cap ? cap : want));
+}
+
+template <typename F>
+cudaError_t dispatch(trtr_ctx* ctx, F&& f) {
+    switch (ctx->p.precision) {
+        case TRTR_F64: f((double*)nullptr, (double*)nullptr); break;
+        case TRTR_F32: f((float*)nullptr, (float*)nullptr); break;
+        case TRTR_F16_OFS: f((__half*)nullptr, (float*)nullptr); break;
+        case TRTR_BF16_OFS: f((__nv_bfloat16*)nullptr, (float*)nullptr); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_convert_fields(trtr_ctx* ctx, const double* ux, const double* uy, const double* D) {
+    const size_t n = (size_t)ctx->p.nx * ctx->p.ny;
+    const double us = ctx->p.dt / ctx->p.dx, ds = ctx->p.dt / (ctx->p.dx * ctx->p.dx);
+    const int use_const = ctx->p.tau1_const > 0.0;
+    const double dh = use_const ? (ctx->p.tau1_const - 0.5) / 3.0 : 0.0;
+    ctx->launches += 1;
+    return dispatch(ctx, [&](auto* sp, auto* cp) {
+        using C = std::remove_pointer_t<decltype(cp)>;
+        (void)sp;
+        convert_fields_kernel<C><<<grid_for(ctx, n), kThreads, 0, ctx->stream>>>(
+            (C*)ctx->ux, (C*)ctx->uy, (C*)ctx->Dh, ux, uy, D, ctx->p.nx, ctx->p.ny, ctx->pitch, us, ds, dh, use_const);
+    });
+}
+
+cudaError_t launch_pulse_fields(trtr_ctx* ctx) {
+    const size_t n = (size_t)ctx->p.nx * ctx->p.ny;
+    const int use_const = ctx->p.tau1_const > 0.0;
+    const double dh = use_const ? (ctx->p.tau1_const - 0.5) / 3.0 : 0.0;
+    ctx->launches += 1;
+    return dispatch(ctx, [&](auto* sp, auto* cp) {
+        using C = std::remove_pointer_t<decltype(cp)>;
+        (void)sp;
+        pulse_fields_kernel<C><<<grid_for(ctx, n), kThreads, 0, ctx->stream>>>(
+            (C*)ctx->ux, (C*)ctx->uy, (C*)ctx->Dh, (C*)ctx->tab_x, (C*)ctx->tab_y, ctx->p.nx, ctx->p.ny, ctx->pitch,
+            ctx->p.x0, ctx->p.y0, ctx->p.dx, ctx->p.dt, ctx->pulse, dh, use_const);
+    });
+}
+
+cudaError_t launch_convert_source(trtr_ctx* ctx, const double* S, void* dst) {
+    const size_t n = (size_t)ctx->p.nx * ctx->p.ny;
+    ctx->launches += 1;
+    return dispatch(ctx, [&](auto* sp, auto* cp) {
+        using C = std::remove_pointer_t<decltype(cp)>;
+        (void)sp;
+        convert_source_kernel<C><<<grid_for(ctx, n), kThreads, 0, ctx->stream>>>((C*)dst, S, ctx->p.nx, ctx->p.ny,
+                                                                                  ctx->pitch, ctx->p.dt);
+    });
+}
+
+cudaError_t launch_init_equilibrium(trtr_ctx* ctx, const double* phi0) {
+    const size_t n = (size_t)ctx->p.nx * ctx->p.ny;
+    const PulseTime pt = pulse_at(ctx->pulse, 0.0);
+    ctx->launches += 1;
+    return dispatch(ctx, [&](auto* sp, auto* cp) {
+        using S = std::remove_pointer_t<decltype(sp)>;
+        using C = std::remove_pointer_t<decltype(cp)>;
+        init_eq_kernel<S, C><<<grid_for(ctx, n), kThreads, 0, ctx->stream>>>(
+            (S*)ctx->pop[ctx->cur], (const C*)ctx->ux, (const C*)ctx->uy, phi0, ctx->p.nx, ctx->p.ny, ctx->pitch,
+            ctx->plane, ctx->p.x0, ctx->p.y0, ctx->p.dx, pt, (C)ctx->p.phi_ref);
+    });
+}
+
+cudaError_t launch_moments(trtr_ctx* ctx, double* phi_out) {
+    const size_t n = (size_t)ctx->p.nx * ctx->p.ny;
+    ctx->launches += 1;
+    return dispatch(ctx, [&](auto* sp, auto* cp) {
+        using S = std::remove_pointer_t<decltype(sp)>;
+        using C = std::remove_pointer_t<decltype(cp)>;
+        moments_kernel<S, C><<<grid_for(ctx, n), kThreads, 0, ctx->stream>>>(
+            phi_out, (const S*)ctx->pop[ctx->cur], ctx->p.nx, ctx->p.ny, ctx->pitch, ctx->plane, (C)ctx->p.phi_ref);
+    });
+}
+
+cudaError_t launch_reduce(trtr_ctx* ctx, int kind, const double* ref) {
+    const PulseTime pt = pulse_at(ctx->pulse, (double)ctx->step * ctx->p.dt);
+    ctx->launches += 2;
+    return dispatch(ctx, [&](auto* sp, auto* cp) {
+        using S = std::remove_pointer_t<decltype(sp)>;
+        using C = std::remove_pointer_t<decltype(cp)>;
+        reduce_kernel<S, C><<<ctx->red_blocks, kThreads, 0, ctx->stream>>>(
+            ctx->scratch, (const S*)ctx->pop[ctx->cur], ctx->p.nx, ctx->p.ny, ctx->pitch, ctx->plane,
+            (C)ctx->p.phi_ref, kind, pt, ctx->p.x0, ctx->p.y0, ctx->p.dx, ref);
+        finish_kernel<<<1, kThreads, 0, ctx->stream>>>(ctx->dres, ctx->scratch, ctx->red_blocks);
+    });
+}
+
+cudaError_t launch_get_populations(trtr_ctx* ctx, double* g) {
+    const size_t n = (size_t)ctx->p.nx * ctx->p.ny;
+    ctx->launches += 1;
+    return dispatch(ctx, [&](auto* sp, auto* cp) {
+        using S = std::remove_pointer_t<decltype(sp)>;
+        using C = std::remove_pointer_t<decltype(cp)>;
+        get_pop_kernel<S, C><<<grid_for(ctx, n), kThreads, 0, ctx->stream>>>(
+            g, (const S*)ctx->pop[ctx->cur], ctx->p.nx, ctx->p.ny, ctx->pitch, ctx->plane, (C)ctx->p.phi_ref);
+    });
+}
+
+cudaError_t launch_set_populations(trtr_ctx* ctx, const double* g) {
+    const size_t n = (size_t)ctx->p.nx * ctx->p.ny;
+    ctx->launches += 1;
+    return dispatch(ctx, [&](auto* sp, auto* cp) {
+        using S = std::remove_pointer_t<decltype(sp)>;
+        using C = std::remove_pointer_t<decltype(cp)>;
+        set_pop_kernel<S, C><<<grid_for(ctx, n), kThreads, 0, ctx->stream>>>(
+            (S*)ctx->pop[ctx->cur], g, ctx->p.nx, ctx->p.ny, ctx->pitch, ctx->plane, (C)ctx->p.phi_ref);
+    });
+}
+
+cudaError_t launch_sample(trtr_ctx* ctx, const long* nodes, int count, double* out) {
+    ctx->launches += 1;
+    const int total = count * kQ;
+    return dispatch(ctx, [&](auto* sp, auto* cp) {
+        using S = std::remove_pointer_t<decltype(sp)>;
+        using C = std::remove_pointer_t<decltype(cp)>;
+        sample_kernel<S, C><<<(total + kThreads - 1) / kThreads, kThreads, 0, ctx->stream>>>(
+            out, nodes, count, (const S*)ctx->pop[ctx->cur], ctx->p.nx, ctx->p.ny, ctx->pitch, ctx->plane,
+            (C)ctx->p.phi_ref);
+    });
+}
+
+}  // namespace trtr

@@ -1,0 +1,389 @@
+"""Python binding of the C ABI in ``include/trtr.h`` (argument marshalling only).
+
+Every function keeps the C name and forwards to ``libtrtr.so``; all computation runs in the
+library's CUDA kernels.  Arrays are numpy float64 (host, ``on_device=0``) or CUDA torch
+tensors of dtype float64 (device, ``on_device=1``); torch provides device memory and the
+stream handle only.  There is no fallback: if ``libtrtr.so`` is missing or fails to load,
+importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, fields as dc_fields
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtrtr.so")
+
+TRTR_OK, TRTR_EINVAL, TRTR_ENOMEM, TRTR_ECUDA, TRTR_EUNSTABLE, TRTR_ETIMEOUT, TRTR_ESTATE = range(7)
+TRTR_F64, TRTR_F32, TRTR_F16_OFS, TRTR_BF16_OFS = range(4)
+TRTR_TAU2_MAGIC, TRTR_TAU2_FIXED = range(2)
+TRTR_GRAD_PERIODIC, TRTR_GRAD_ONESIDED_EDGE = range(2)
+TRTR_SRC_NONE, TRTR_SRC_FIELD, TRTR_SRC_PULSE = range(3)
+
+PRECISIONS = {"f64": TRTR_F64, "f32": TRTR_F32, "f16": TRTR_F16_OFS, "bf16": TRTR_BF16_OFS}
+
+
+class TrtrError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+class trtr_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+        ("x0", ctypes.c_double), ("y0", ctypes.c_double),
+        ("dx", ctypes.c_double), ("dt", ctypes.c_double),
+        ("precision", ctypes.c_int), ("phi_ref", ctypes.c_double),
+        ("tau2_mode", ctypes.c_int), ("magic", ctypes.c_double), ("tau2", ctypes.c_double),
+        ("tau1_const", ctypes.c_double),
+        ("grad_mode", ctypes.c_int), ("src_mode", ctypes.c_int),
+        ("check_every", ctypes.c_int),
+    ]
+
+
+_dbl_p = ctypes.POINTER(ctypes.c_double)
+_vp = ctypes.c_void_p
+_st = ctypes.c_int
+
+_SIGNATURES = {
+    "trtr_create": (_st, [ctypes.POINTER(trtr_params), _vp, ctypes.POINTER(_vp)]),
+    "trtr_destroy": (_st, [_vp]),
+    "trtr_set_fields": (_st, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int]),
+    "trtr_set_source": (_st, [_vp, _vp, ctypes.c_int]),
+    "trtr_set_pulse": (_st, [_vp] + [ctypes.c_double] * 6),
+    "trtr_init_equilibrium": (_st, [_vp, _vp, ctypes.c_int]),
+    "trtr_step": (_st, [_vp, ctypes.c_long]),
+    "trtr_moments": (_st, [_vp, _vp, ctypes.c_int]),
+    "trtr_mass": (_st, [_vp, _dbl_p]),
+    "trtr_error_vs_pulse": (_st, [_vp, _dbl_p, _dbl_p]),
+    "trtr_error_vs": (_st, [_vp, _vp, ctypes.c_int, _dbl_p, _dbl_p]),
+    "trtr_get_populations": (_st, [_vp, _vp, ctypes.c_int]),
+    "trtr_set_populations": (_st, [_vp, _vp, ctypes.c_int, ctypes.c_long]),
+    "trtr_sample_populations": (_st, [_vp, ctypes.POINTER(ctypes.c_long), ctypes.c_int, _dbl_p]),
+    "trtr_time": (_st, [_vp, ctypes.POINTER(ctypes.c_long), _dbl_p]),
+    "trtr_save": (_st, [_vp, _vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "trtr_load": (_st, [_vp, _vp, ctypes.c_size_t]),
+    "trtr_sync": (_st, [_vp]),
+    "trtr_launch_count": (_st, [_vp, ctypes.POINTER(ctypes.c_long)]),
+    "trtr_status_str": (ctypes.c_char_p, [_st]),
+    "trtr_last_error": (ctypes.c_char_p, [_vp]),
+    "trtr_d2q9": (None, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _dbl_p]),
+    "trtr_abi_version": (ctypes.c_int, []),
+}
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_2312_10316_gb300.build.build_library()")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in _SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def symbols() -> list[str]:
+    return list(_SIGNATURES)
+
+
+# --------------------------------------------------------------------------------------
+# marshalling helpers
+
+
+def _arr(a, count: int | None = None):
+    """(pointer, on_device, keepalive) for a float64 numpy array or CUDA torch tensor."""
+    if a is None:
+        return None, 0, None
+    if isinstance(a, np.ndarray):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        if count is not None and a.size != count:
+            raise ValueError(f"expected {count} values, got {a.size}")
+        return a.ctypes.data, 0, a
+    # torch tensor
+    if getattr(a, "is_cuda", False):
+        import torch
+
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise ValueError("device arrays must be contiguous float64 tensors")
+        if count is not None and a.numel() != count:
+            raise ValueError(f"expected {count} values, got {a.numel()}")
+        return a.data_ptr(), 1, a
+    arr = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    return _arr(arr, count)
+
+
+def _check(ctx, status: int):
+    if status != TRTR_OK:
+        msg = lib.trtr_last_error(ctx).decode() if ctx else ""
+        raise TrtrError(status, f"{lib.trtr_status_str(status).decode()}: {msg}")
+
+
+# --------------------------------------------------------------------------------------
+# the C ABI, one function per entry point
+
+
+def trtr_create(params: trtr_params, cuda_stream: int | None = None):
+    out = _vp()
+    s = lib.trtr_create(ctypes.byref(params), cuda_stream, ctypes.byref(out))
+    if s != TRTR_OK:
+        raise TrtrError(s, f"trtr_create: {lib.trtr_status_str(s).decode()}")
+    return out
+
+
+def trtr_destroy(ctx):
+    _check(None, lib.trtr_destroy(ctx))
+
+
+def trtr_set_fields(ctx, n: int, ux, uy, D=None, S=None):
+    pu, du, ku = _arr(ux, n)
+    pv, dv, kv = _arr(uy, n)
+    pd, dd, kd = _arr(D, n)
+    ps, ds, ks = _arr(S, n)
+    devs = {d for p, d in ((pu, du), (pv, dv), (pd, dd), (ps, ds)) if p is not None}
+    if len(devs) != 1:
+        raise ValueError("fields must all be host arrays or all device tensors")
+    _check(ctx, lib.trtr_set_fields(ctx, pu, pv, pd, ps, devs.pop()))
+
+
+def trtr_set_source(ctx, n: int, S):
+    p, d, k = _arr(S, n)
+    _check(ctx, lib.trtr_set_source(ctx, p, d))
+
+
+def trtr_set_pulse(ctx, omega, xc, yc, sigma0, D0, D_amp):
+    _check(ctx, lib.trtr_set_pulse(ctx, omega, xc, yc, sigma0, D0, D_amp))
+
+
+def trtr_init_equilibrium(ctx, n: int, phi0=None):
+    p, d, k = _arr(phi0, n)
+    _check(ctx, lib.trtr_init_equilibrium(ctx, p, d))
+
+
+def trtr_step(ctx, n: int):
+    _check(ctx, lib.trtr_step(ctx, int(n)))
+
+
+def trtr_moments(ctx, out):
+    p, d, k = _arr(out)
+    if d == 0 and p is not None and k is not out:
+        raise ValueError("host output must be a contiguous float64 numpy array")
+    _check(ctx, lib.trtr_moments(ctx, p, d))
+    return out
+
+
+def trtr_mass(ctx) -> float:
+    v = ctypes.c_double()
+    _check(ctx, lib.trtr_mass(ctx, ctypes.byref(v)))
+    return v.value
+
+
+def trtr_error_vs_pulse(ctx):
+    rms, rel = ctypes.c_double(), ctypes.c_double()
+    _check(ctx, lib.trtr_error_vs_pulse(ctx, ctypes.byref(rms), ctypes.byref(rel)))
+    return rms.value, rel.value
+
+
+def trtr_error_vs(ctx, n: int, phi_ref):
+    p, d, k = _arr(phi_ref, n)
+    rms, rel = ctypes.c_double(), ctypes.c_double()
+    _check(ctx, lib.trtr_error_vs(ctx, p, d, ctypes.byref(rms), ctypes.byref(rel)))
+    return rms.value, rel.value
+
+
+def trtr_get_populations(ctx, out):
+    p, d, k = _arr(out)
+    if d == 0 and k is not out:
+        raise ValueError("host output must be a contiguous float64 numpy array")
+    _check(ctx, lib.trtr_get_populations(ctx, p, d))
+    return out
+
+
+def trtr_set_populations(ctx, n9: int, g, step: int = 0):
+    p, d, k = _arr(g, n9)
+    _check(ctx, lib.trtr_set_populations(ctx, p, d, int(step)))
+
+
+def trtr_sample_populations(ctx, nodes) -> np.ndarray:
+    idx = np.ascontiguousarray(np.asarray(nodes, dtype=np.int64))
+    out = np.zeros((idx.size, 9))
+    _check(ctx, lib.trtr_sample_populations(ctx, idx.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), int(idx.size),
+                                            out.ctypes.data_as(_dbl_p)))
+    return out
+
+
+def trtr_time(ctx):
+    n, t = ctypes.c_long(), ctypes.c_double()
+    _check(ctx, lib.trtr_time(ctx, ctypes.byref(n), ctypes.byref(t)))
+    return n.value, t.value
+
+
+def trtr_save(ctx) -> bytes:
+    size = ctypes.c_size_t()
+    _check(ctx, lib.trtr_save(ctx, None, ctypes.byref(size)))
+    buf = ctypes.create_string_buffer(size.value)
+    _check(ctx, lib.trtr_save(ctx, buf, ctypes.byref(size)))
+    return buf.raw[: size.value]
+
+
+def trtr_load(ctx, blob: bytes):
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check(ctx, lib.trtr_load(ctx, buf, len(blob)))
+
+
+def trtr_sync(ctx):
+    _check(ctx, lib.trtr_sync(ctx))
+
+
+def trtr_launch_count(ctx) -> int:
+    v = ctypes.c_long()
+    _check(ctx, lib.trtr_launch_count(ctx, ctypes.byref(v)))
+    return v.value
+
+
+def trtr_status_str(s: int) -> str:
+    return lib.trtr_status_str(s).decode()
+
+
+def trtr_last_error(ctx) -> str:
+    return lib.trtr_last_error(ctx).decode()
+
+
+def trtr_d2q9():
+    ex = (ctypes.c_int * 9)()
+    ey = (ctypes.c_int * 9)()
+    w = (ctypes.c_double * 9)()
+    lib.trtr_d2q9(ex, ey, w)
+    return np.array(ex[:]), np.array(ey[:]), np.array(w[:])
+
+
+def trtr_abi_version() -> int:
+    return int(lib.trtr_abi_version())
+
+
+# --------------------------------------------------------------------------------------
+# convenience object over the same calls
+
+
+@dataclass
+class Params:
+    nx: int
+    ny: int
+    dx: float
+    dt: float
+    x0: float = -1.0
+    y0: float = -1.0
+    precision: int = TRTR_F32
+    phi_ref: float = 0.0
+    tau2_mode: int = TRTR_TAU2_MAGIC
+    magic: float = 1.0 / 12.0
+    tau2: float = 1.0
+    tau1_const: float = 0.0
+    grad_mode: int = TRTR_GRAD_ONESIDED_EDGE
+    src_mode: int = TRTR_SRC_NONE
+    check_every: int = 0
+
+    def to_c(self) -> trtr_params:
+        return trtr_params(**{f.name: getattr(self, f.name) for f in dc_fields(self)})
+
+
+class Solver:
+    """Owns one trtr context; methods map 1:1 onto the C calls."""
+
+    def __init__(self, params: Params, stream: int | None = None):
+        self.params = params
+        self.n = params.nx * params.ny
+        self.ctx = trtr_create(params.to_c(), stream)
+
+    def close(self):
+        if self.ctx:
+            trtr_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_fields(self, ux, uy, D=None, S=None):
+        trtr_set_fields(self.ctx, self.n, ux, uy, D, S)
+
+    def set_source(self, S):
+        trtr_set_source(self.ctx, self.n, S)
+
+    def set_pulse(self, omega, xc, yc, sigma0, D0, D_amp=0.0):
+        trtr_set_pulse(self.ctx, omega, xc, yc, sigma0, D0, D_amp)
+
+    def init_equilibrium(self, phi0=None):
+        trtr_init_equilibrium(self.ctx, self.n, phi0)
+
+    def step(self, n: int = 1):
+        trtr_step(self.ctx, n)
+
+    def moments(self, out=None):
+        if out is None:
+            out = np.zeros((self.params.ny, self.params.nx))
+        return trtr_moments(self.ctx, out)
+
+    def mass(self) -> float:
+        return trtr_mass(self.ctx)
+
+    def error_vs_pulse(self):
+        return trtr_error_vs_pulse(self.ctx)
+
+    def error_vs(self, phi_ref):
+        return trtr_error_vs(self.ctx, self.n, phi_ref)
+
+    def get_populations(self, out=None):
+        if out is None:
+            out = np.zeros((9, self.params.ny, self.params.nx))
+        return trtr_get_populations(self.ctx, out)
+
+    def set_populations(self, g, step: int = 0):
+        trtr_set_populations(self.ctx, 9 * self.n, g, step)
+
+    def sample(self, nodes):
+        return trtr_sample_populations(self.ctx, nodes)
+
+    def time(self):
+        return trtr_time(self.ctx)
+
+    def save(self) -> bytes:
+        return trtr_save(self.ctx)
+
+    def load(self, blob: bytes):
+        trtr_load(self.ctx, blob)
+
+    def sync(self):
+        trtr_sync(self.ctx)
+
+    @property
+    def launches(self) -> int:
+        return trtr_launch_count(self.ctx)
+
+
+def pulse_solver(pulse, precision: int = TRTR_F32, stream: int | None = None, src_mode: int | None = None,
+                 **overrides) -> Solver:
+    """A Solver set up for a ``workloads.Pulse`` (fields from the closed form, on the device)."""
+    if src_mode is None:
+        src_mode = TRTR_SRC_PULSE if pulse.D_amp != 0.0 else TRTR_SRC_NONE
+    p = Params(nx=pulse.nx, ny=pulse.ny, dx=pulse.dx, dt=pulse.dt, x0=pulse.x0, y0=pulse.y0,
+               precision=precision, src_mode=src_mode, grad_mode=TRTR_GRAD_ONESIDED_EDGE, **overrides)
+    s = Solver(p, stream)
+    s.set_pulse(pulse.omega, pulse.xc, pulse.yc, pulse.sigma0, pulse.D0, pulse.D_amp)
+    s.init_equilibrium(None)
+    return s

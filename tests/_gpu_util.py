@@ -1,0 +1,47 @@
+"""Shared setup of the GPU parity tests: the same seeded inputs go to the CUDA library
+(through the C ABI binding) and to the FP64 oracle."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+from paper_2312_10316_gb300 import workloads as W
+
+# Relative-L2 tolerances on phi / populations against the FP64 oracle.
+TOL_F64 = 1e-12
+TOL_F32 = 1e-5
+
+
+def oracle_for_pulse(pulse: W.Pulse, src_mode: int | None = None) -> oracle.Sim:
+    if src_mode is None:
+        src_mode = 2 if pulse.D_amp != 0.0 else 0
+    sp = oracle.SimParams(nx=pulse.nx, ny=pulse.ny, dx=pulse.dx, dt=pulse.dt, x0=pulse.x0, y0=pulse.y0,
+                          src_mode=src_mode, grad_mode=1, omega=pulse.omega, xc=pulse.xc, yc=pulse.yc,
+                          sigma0=pulse.sigma0, D0=pulse.D0, D_amp=pulse.D_amp)
+    s = oracle.Sim(sp)
+    f = W.fields(pulse)
+    s.set_fields(f["ux"], f["uy"], f["D"])
+    s.init_equilibrium(f["phi0"])
+    return s
+
+
+def rel_l2(a, b) -> float:
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    den = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (den if den > 0 else 1.0))
+
+
+def random_case(seed: int, nx: int, ny: int, dx: float = 0.1, dt: float = 0.02):
+    """Seeded generic inputs: populations, u with |u dt/dx| <= 0.3, D giving tau1 in
+    (0.55, 1.5), and two source fields."""
+    rng = np.random.default_rng(seed)
+    c = dx / dt
+    g = W.random_populations(seed, ny, nx, base=1.0, amp=0.3)
+    ux = c * rng.uniform(-0.2, 0.2, size=(ny, nx))
+    uy = c * rng.uniform(-0.2, 0.2, size=(ny, nx))
+    tau1 = rng.uniform(0.55, 1.5, size=(ny, nx))
+    D = (tau1 - 0.5) * (c * c / 3.0) * dt
+    S1 = rng.uniform(-1.0, 1.0, size=(ny, nx))
+    S2 = rng.uniform(-1.0, 1.0, size=(ny, nx))
+    return dict(g=g, ux=ux, uy=uy, D=D, S1=S1, S2=S2, dx=dx, dt=dt)

@@ -1,0 +1,101 @@
+"""The C ABI library without a GPU: it loads, exports every function include/*.h declares,
+and its host-only calls and argument validation behave as documented."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2312_10316_gb300 import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
+
+
+def declared_functions():
+    names = []
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w]*\s*\*?\s+\**(trtr_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def T():
+    build.build_library()
+    from paper_2312_10316_gb300 import trtr
+
+    return trtr
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["trtr_create", "trtr_destroy", "trtr_set_fields", "trtr_set_source", "trtr_set_pulse",
+                     "trtr_init_equilibrium", "trtr_step", "trtr_moments", "trtr_mass", "trtr_error_vs_pulse",
+                     "trtr_error_vs", "trtr_time", "trtr_save", "trtr_load"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(T):
+    lib = ctypes.CDLL(T.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    out = subprocess.run(["nm", "-D", "--defined-only", T.LIB_PATH], capture_output=True, text=True)
+    if out.returncode == 0:
+        exported = set(re.findall(r"\s[TW]\s+(trtr_\w+)$", out.stdout, flags=re.M))
+        assert set(declared_functions()) <= exported
+
+
+def test_binding_covers_the_header(T):
+    assert set(T.symbols()) == set(declared_functions())
+
+
+def test_host_only_calls(T):
+    assert T.trtr_abi_version() == 1
+    ex, ey, w = T.trtr_d2q9()
+    assert np.isclose(w.sum(), 1.0)
+    assert np.array_equal(ex + 0, [0, 1, -1, 0, 0, 1, -1, 1, -1])
+    assert np.array_equal(ey + 0, [0, 0, 0, 1, -1, 1, -1, -1, 1])
+    # opposite directions sit in adjacent slots (1,2), (3,4), (5,6), (7,8)
+    for a in (1, 3, 5, 7):
+        assert ex[a] == -ex[a + 1] and ey[a] == -ey[a + 1]
+    assert T.trtr_status_str(T.TRTR_EUNSTABLE).startswith("non-finite")
+    assert T.trtr_last_error(None) == "null context"
+
+
+def test_library_and_oracle_share_the_lattice_convention(T):
+    import oracle
+
+    oex, oey, ow = oracle.d2q9()
+    ex, ey, w = T.trtr_d2q9()
+    assert np.array_equal(oex, ex) and np.array_equal(oey, ey) and np.array_equal(ow, w)
+
+
+BAD = [
+    dict(nx=0), dict(ny=-3), dict(dx=0.0), dict(dt=-1.0), dict(dx=float("nan")), dict(precision=7),
+    dict(tau2_mode=2), dict(magic=0.0), dict(tau2_mode=1, tau2=0.5), dict(tau1_const=0.4),
+    dict(grad_mode=5), dict(src_mode=3), dict(check_every=-1), dict(phi_ref=float("inf")),
+    dict(nx=70000, ny=40000),
+]
+
+
+@pytest.mark.parametrize("bad", BAD, ids=lambda d: ",".join(f"{k}={v}" for k, v in d.items()))
+def test_create_rejects_bad_parameters_before_touching_cuda(T, bad):
+    base = dict(nx=16, ny=16, dx=0.1, dt=0.01)
+    base.update(bad)
+    p = T.Params(**base)
+    with pytest.raises(T.TrtrError) as e:
+        T.trtr_create(p.to_c(), None)
+    assert e.value.status == T.TRTR_EINVAL
+
+
+def test_null_arguments(T):
+    lib = T.lib
+    assert lib.trtr_create(None, None, None) == T.TRTR_EINVAL
+    assert lib.trtr_destroy(None) == T.TRTR_OK
+    assert lib.trtr_step(None, 1) == T.TRTR_EINVAL
+    assert lib.trtr_sync(None) == T.TRTR_EINVAL

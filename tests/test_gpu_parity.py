@@ -1,0 +1,306 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances (relative L2 against the oracle): FP64 storage <= 1e-12, FP32 <= 1e-5; the
+half-precision offset storage is bounded by its rounding unit (see each test)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2312_10316_gb300 import workloads as W
+
+from ._gpu_util import TOL_F32, TOL_F64, oracle_for_pulse, random_case, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2312_10316_gb300 import trtr as T  # noqa: E402  (loads libtrtr.so)
+
+PREC = {"f64": T.TRTR_F64, "f32": T.TRTR_F32, "f16": T.TRTR_F16_OFS, "bf16": T.TRTR_BF16_OFS}
+ONE_STEP_TOL = {"f64": TOL_F64, "f32": TOL_F32, "f16": 2e-3, "bf16": 1.5e-2}
+
+
+# ------------------------------------------------------------------------ workload 1
+
+
+def test_pulse64_f64_against_oracle():
+    """64^2 rotating pulse, FP64, constant D, S = 0, Courant 0.2, 500 steps."""
+    pulse = W.C1_F64_64
+    o = oracle_for_pulse(pulse)
+    with T.pulse_solver(pulse, precision=T.TRTR_F64) as s:
+        m0 = s.mass()
+        assert abs(m0 - o.mass()) <= 1e-13 * abs(m0)
+        s.step(pulse.steps)
+        o.step(pulse.steps)
+        phi = s.moments()
+        assert rel_l2(phi, o.phi()) <= TOL_F64
+        assert rel_l2(s.get_populations(), o.get_g()) <= TOL_F64
+        # reductions
+        assert abs(s.mass() - o.mass()) <= 1e-13 * abs(m0)
+        assert abs(s.mass() - m0) <= 1e-13 * abs(m0)  # conservation with S = 0
+        pa = W.phi_analytic(pulse, pulse.steps * pulse.dt)
+        rms_o, rel_o = o.error(pa)
+        rms_g, rel_g = s.error_vs_pulse()
+        assert abs(rms_g - rms_o) <= 1e-10 * rms_o and abs(rel_g - rel_o) <= 1e-10 * rel_o
+        rms_f, rel_f = s.error_vs(pa)
+        assert abs(rms_f - rms_o) <= 1e-10 * rms_o and abs(rel_f - rel_o) <= 1e-10 * rel_o
+        n, t = s.time()
+        assert n == pulse.steps and abs(t - pulse.steps * pulse.dt) < 1e-15
+
+
+# ------------------------------------------------------------- random states, all modes
+
+GRIDS = [(1, 1), (1, 5), (7, 1), (2, 3), (5, 3), (33, 17), (37, 23), (64, 64), (100, 67), (129, 40)]
+
+
+def _pair(case, nx, ny, prec, src_mode, grad_mode, tau2_mode, tau1_const=0.0, phi_ref=0.0, pulse=None):
+    common = dict(nx=nx, ny=ny, dx=case["dx"], dt=case["dt"], x0=-0.3, y0=-0.2, tau2_mode=tau2_mode, magic=1 / 12,
+                  tau2=1.2, tau1_const=tau1_const, grad_mode=grad_mode, src_mode=src_mode)
+    pul = dict(omega=0.0, xc=0.0, yc=0.0, sigma0=0.1, D0=0.0, D_amp=0.0)
+    if pulse is not None:
+        pul = dict(omega=pulse[0], xc=pulse[1], yc=pulse[2], sigma0=pulse[3], D0=pulse[4], D_amp=pulse[5])
+    o = oracle.Sim(oracle.SimParams(**common, **pul))
+    s = T.Solver(T.Params(precision=prec, phi_ref=phi_ref, **common))
+    return o, s
+
+
+@pytest.mark.parametrize("nx,ny", GRIDS)
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("src_mode", [0, 1, 2])
+def test_random_state_steps(nx, ny, prec, src_mode):
+    case = random_case(100 + nx * 131 + ny, nx, ny)
+    grad_mode = (nx + ny) % 2
+    tau2_mode = (nx * ny) % 2
+    pulse = (0.0, -0.1, 0.05, 0.2, 5e-3, 0.5) if src_mode == 2 else None
+    o, s = _pair(case, nx, ny, PREC[prec], src_mode, grad_mode, tau2_mode, pulse=pulse)
+    with s:
+        S1 = case["S1"] if src_mode == 1 else None
+        o.set_fields(case["ux"], case["uy"], case["D"])
+        s.set_fields(case["ux"], case["uy"], case["D"], S1)
+        if src_mode == 1:
+            o.set_source(S1)
+        if src_mode == 2:
+            s.set_pulse(*pulse)
+            s.set_fields(case["ux"], case["uy"], case["D"])  # random u / D over the pulse's fields
+        o.set_g(case["g"], step=5)
+        s.set_populations(case["g"], step=5)
+        assert rel_l2(s.get_populations(), case["g"]) <= (TOL_F64 if prec == "f64" else 1e-7)
+        for k in range(3):
+            o.step(1)
+            s.step(1)
+            assert rel_l2(s.get_populations(), o.get_g()) <= ONE_STEP_TOL[prec], (k, prec)
+            if src_mode == 1:
+                Sn = case["S2"] if k % 2 == 0 else case["S1"]
+                o.set_source(Sn)
+                s.set_source(Sn)
+        assert rel_l2(s.moments(), o.phi()) <= ONE_STEP_TOL[prec]
+        assert abs(s.mass() - o.mass()) <= 10 * ONE_STEP_TOL[prec] * abs(o.mass())
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_tau1_const_and_fixed_tau2(prec):
+    nx, ny = 45, 38
+    case = random_case(7, nx, ny)
+    o, s = _pair(case, nx, ny, PREC[prec], 0, 0, 1, tau1_const=0.9)
+    with s:
+        o.set_fields(case["ux"], case["uy"], case["D"])
+        s.set_fields(case["ux"], case["uy"], None)
+        o.set_g(case["g"])
+        s.set_populations(case["g"])
+        o.step(4)
+        s.step(4)
+        assert rel_l2(s.get_populations(), o.get_g()) <= ONE_STEP_TOL[prec]
+
+
+@pytest.mark.parametrize("prec,phi_ref", [("f16", 1.0), ("bf16", 1.0), ("f16", 0.0), ("bf16", 0.0)])
+def test_half_offset_storage_one_step(prec, phi_ref):
+    """Populations stored as half-precision offsets g - w_i phi_ref, FP32 arithmetic: one
+    step stays within a few rounding units of the format (2^-11 f16, 2^-8 bf16)."""
+    nx, ny = 70, 41
+    case = random_case(11, nx, ny)
+    o, s = _pair(case, nx, ny, PREC[prec], 0, 1, 0, phi_ref=phi_ref)
+    with s:
+        o.set_fields(case["ux"], case["uy"], case["D"])
+        s.set_fields(case["ux"], case["uy"], case["D"])
+        o.set_g(case["g"])
+        s.set_populations(case["g"])
+        o.step(1)
+        s.step(1)
+        err = rel_l2(s.get_populations(), o.get_g())
+        unit = 2.0**-11 if prec == "f16" else 2.0**-8
+        assert err <= 4 * unit, err
+
+
+# ------------------------------------------------------------------- multi-step, FP32
+
+
+def test_pulse200_f32_variable_D_multistep():
+    """Workload-2 physics (variable D, manufactured source, Courant 0.8) on a 200^2 grid
+    (ragged against the 32 x 16 tiles), 1000 FP32 steps against the FP64 oracle."""
+    pulse = W.Pulse(n=200, D_amp=0.5, courant=0.8, steps=1000)
+    o = oracle_for_pulse(pulse)
+    with T.pulse_solver(pulse, precision=T.TRTR_F32) as s:
+        s.step(pulse.steps)
+        o.step(pulse.steps)
+        assert rel_l2(s.moments(), o.phi()) <= TOL_F32
+        rms_g, _ = s.error_vs_pulse()
+        rms_o, _ = o.error(W.phi_analytic(pulse, pulse.steps * pulse.dt))
+        assert abs(rms_g - rms_o) <= 1e-4 * rms_o
+
+
+# ------------------------------------------------------- full sizes, sampled one step
+
+
+def _sampled_step_check(pulse, prec, warm_steps, nsamples, tol, seed=0):
+    """After `warm_steps` GPU steps, the populations the GPU writes in one more step at
+    sampled nodes equal the oracle's single-node update of the GPU's own pre-collision
+    state (rotation u: d_y u_x = -omega, d_x u_y = omega exactly on the lattice)."""
+    rng = np.random.default_rng(seed)
+    n = pulse.nx
+    corners = [0, n - 1, (n - 1) * n, n * n - 1, n // 2, (n // 2) * n]
+    nodes = np.unique(np.concatenate([rng.integers(0, n * n, size=nsamples), corners]))
+    ex, ey, _ = T.trtr_d2q9()
+    op = oracle.SimParams(nx=n, ny=n, dx=pulse.dx, dt=pulse.dt, grad_mode=1, src_mode=2, omega=pulse.omega,
+                          xc=pulse.xc, yc=pulse.yc, sigma0=pulse.sigma0, D0=pulse.D0, D_amp=pulse.D_amp)
+    osim = oracle.Sim(oracle.SimParams(nx=1, ny=1, dx=pulse.dx, dt=pulse.dt, src_mode=2, omega=pulse.omega,
+                                       xc=pulse.xc, yc=pulse.yc, sigma0=pulse.sigma0, D0=pulse.D0,
+                                       D_amp=pulse.D_amp))
+    with T.pulse_solver(pulse, precision=prec) as s:
+        s.step(warm_steps)
+        g_n = s.sample(nodes)
+        step_n, t_n = s.time()
+        s.step(1)
+        j, i = nodes // n, nodes % n
+        pushed = [((j + ey[q]) % n) * n + (i + ex[q]) % n for q in range(9)]
+        after = [s.sample(pushed[q])[:, q] for q in range(9)]
+    gpu = np.stack(after, axis=1)
+    ref = np.zeros_like(gpu)
+    du = [0.0, -pulse.omega, pulse.omega, 0.0]
+    for k, node in enumerate(nodes):
+        x = pulse.x0 + (node % n) * pulse.dx
+        y = pulse.y0 + (node // n) * pulse.dx
+        D = pulse.D0 * (1 + pulse.D_amp * math.sin(math.pi * x) * math.sin(math.pi * y))
+        Sn = osim.pulse_source_at(x, y, t_n)
+        Sp = osim.pulse_source_at(x, y, t_n - pulse.dt) if step_n > 0 else Sn
+        ref[k] = oracle.node_post(op, g_n[k], -pulse.omega * y, pulse.omega * x, du, D, Sn, Sp)
+    err = rel_l2(gpu, ref)
+    assert err <= tol, err
+    return err
+
+
+@pytest.mark.parametrize("n", [1024, 4096])
+def test_fullsize_sampled_f32(n):
+    pulse = W.Pulse(n=n, D_amp=0.5, courant=0.8)
+    _sampled_step_check(pulse, T.TRTR_F32, 100, 4000, 2e-6)
+
+
+def test_fullsize_sampled_f64_8192():
+    pulse = W.Pulse(n=8192, D_amp=0.5, courant=0.8)
+    _sampled_step_check(pulse, T.TRTR_F64, 20, 2000, 1e-13)
+
+
+def test_mass_conserved_f32_1024():
+    """S = 0: FP64 sum of phi is conserved up to FP32 rounding of the stored populations."""
+    pulse = W.Pulse(n=1024, courant=0.8)
+    with T.pulse_solver(pulse, precision=T.TRTR_F32) as s:
+        m0 = s.mass()
+        s.step(500)
+        assert abs(s.mass() - m0) <= 1e-5 * abs(m0)
+
+
+# ------------------------------------------------------------------- host-side paths
+
+
+def test_device_tensors_and_stream_match_host_path():
+    pulse = W.Pulse(n=96, D_amp=0.5, courant=0.8)
+    f = W.fields(pulse)
+    stream = torch.cuda.Stream()
+    dev = {k: torch.from_numpy(v).cuda() for k, v in f.items()}
+    p = T.Params(nx=96, ny=96, dx=pulse.dx, dt=pulse.dt, precision=T.TRTR_F32, src_mode=T.TRTR_SRC_PULSE)
+    with T.Solver(p, stream.cuda_stream) as a, T.Solver(p) as b:
+        a.set_pulse(pulse.omega, pulse.xc, pulse.yc, pulse.sigma0, pulse.D0, pulse.D_amp)
+        b.set_pulse(pulse.omega, pulse.xc, pulse.yc, pulse.sigma0, pulse.D0, pulse.D_amp)
+        a.set_fields(dev["ux"], dev["uy"], dev["D"])
+        b.set_fields(f["ux"], f["uy"], f["D"])
+        a.init_equilibrium(dev["phi0"])
+        b.init_equilibrium(f["phi0"])
+        a.step(37)
+        b.step(37)
+        out = torch.empty((96, 96), dtype=torch.float64, device="cuda")
+        a.moments(out)
+        stream.synchronize()
+        assert np.array_equal(out.cpu().numpy(), b.moments())
+
+
+def test_save_load_roundtrip_is_bitwise():
+    pulse = W.Pulse(n=80, D_amp=0.5, courant=0.8)
+    with T.pulse_solver(pulse, precision=T.TRTR_F32) as s:
+        s.step(10)
+        blob = s.save()
+        s.step(25)
+        ref = s.get_populations().copy()
+        s.load(blob)
+        assert s.time()[0] == 10
+        s.step(25)
+        assert np.array_equal(s.get_populations(), ref)
+
+
+def test_field_source_save_load():
+    nx, ny = 40, 24
+    case = random_case(3, nx, ny)
+    p = T.Params(nx=nx, ny=ny, dx=case["dx"], dt=case["dt"], precision=T.TRTR_F64, src_mode=T.TRTR_SRC_FIELD)
+    with T.Solver(p) as s:
+        s.set_fields(case["ux"], case["uy"], case["D"], case["S1"])
+        s.set_populations(case["g"])
+        s.step(2)
+        s.set_source(case["S2"])
+        blob = s.save()
+        s.step(3)
+        ref = s.get_populations().copy()
+        s.load(blob)
+        s.step(3)
+        assert np.array_equal(s.get_populations(), ref)
+
+
+def test_unstable_run_is_reported():
+    """Host-side fault injection: a NaN population is detected by the periodic check."""
+    nx, ny = 32, 32
+    case = random_case(5, nx, ny)
+    g = case["g"].copy()
+    g[3, 7, 11] = np.nan
+    p = T.Params(nx=nx, ny=ny, dx=case["dx"], dt=case["dt"], precision=T.TRTR_F32, check_every=2)
+    with T.Solver(p) as s:
+        s.set_fields(case["ux"], case["uy"], case["D"])
+        s.set_populations(g)
+        with pytest.raises(T.TrtrError) as e:
+            s.step(4)
+        assert e.value.status == T.TRTR_EUNSTABLE
+
+
+def test_call_order_and_argument_errors():
+    p = T.Params(nx=16, ny=16, dx=0.1, dt=0.02, precision=T.TRTR_F32)
+    with T.Solver(p) as s:
+        with pytest.raises(T.TrtrError) as e:
+            s.step(1)
+        assert e.value.status == T.TRTR_ESTATE
+        case = random_case(1, 16, 16)
+        s.set_fields(case["ux"], case["uy"], case["D"])
+        s.set_populations(case["g"])
+        before = s.get_populations().copy()
+        s.step(0)
+        assert np.array_equal(s.get_populations(), before)
+        with pytest.raises(T.TrtrError) as e:
+            s.sample([256])
+        assert e.value.status == T.TRTR_EINVAL
+        with pytest.raises(T.TrtrError) as e:
+            s.step(-1)
+        assert e.value.status == T.TRTR_EINVAL
+        bad = case["D"].copy()
+        bad[0, 0] = -1.0
+        with pytest.raises(T.TrtrError) as e:
+            s.set_fields(case["ux"], case["uy"], bad)
+        assert e.value.status == T.TRTR_EINVAL
