@@ -192,7 +192,8 @@ def oracle_sample(pulse, target_seconds: float, warm_rows: int = 8):
     f = W.fields(pulse)
     sp = oracle.SimParams(nx=pulse.nx, ny=pulse.ny, dx=pulse.dx, dt=pulse.dt, x0=pulse.x0, y0=pulse.y0,
                           src_mode=2 if pulse.D_amp else 0, grad_mode=1, omega=pulse.omega, xc=pulse.xc,
-                          yc=pulse.yc, sigma0=pulse.sigma0, D0=pulse.D0, D_amp=pulse.D_amp)
+                          yc=pulse.yc, sigma0=pulse.sigma0, D0=pulse.D0, D_amp=pulse.D_amp,
+                          tau2_mode=0 if pulse.tau2 is None else 1, tau2=pulse.tau2 or 1.0)
     sim = oracle.Sim(sp)
     sim.set_fields(f["ux"], f["uy"], f["D"])
     sim.init_equilibrium(f["phi0"])
@@ -205,17 +206,27 @@ def oracle_sample(pulse, target_seconds: float, warm_rows: int = 8):
 
 
 def cpu_baseline(pulse, seconds: float):
+    """The oracle as it stands on this machine's host cores: whole-grid oracle steps (or a row
+    band when one step would exceed the budget) for about `seconds` seconds."""
     sim, rate, threads = oracle_sample(pulse, seconds)
-    rows = max(1, min(pulse.ny, int(rate * seconds / pulse.nx)))
-    j0 = max(0, pulse.ny // 2 - rows // 2)
+    full_step = pulse.nx * pulse.ny / rate
+    if full_step <= seconds:
+        reps = max(1, int(seconds / full_step))
+        rows, j0 = pulse.ny, 0
+    else:
+        reps = 1
+        rows = max(1, min(pulse.ny, int(rate * seconds / pulse.nx)))
+        j0 = max(0, pulse.ny // 2 - rows // 2)
     t = time.perf_counter()
-    sim.step_rows_sample(j0, j0 + rows)
+    for _ in range(reps):
+        sim.step_rows_sample(j0, j0 + rows)
     el = time.perf_counter() - t
     sim.close()
-    value = rows * pulse.nx / el / 1e9
+    value = reps * rows * pulse.nx / el / 1e9
+    what = "whole-grid" if rows == pulse.ny else f"rows {j0}..{j0 + rows - 1} of the"
     return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"one FP64 oracle step over rows {j0}..{j0 + rows - 1} of the {pulse.nx}x{pulse.ny} grid "
-                      f"({rows * pulse.nx} node updates, {el:.1f} s)"}
+            "sample": f"{reps} FP64 oracle step(s) over the {what} {pulse.nx}x{pulse.ny} grid "
+                      f"({reps * rows * pulse.nx} node updates, {el:.1f} s)"}
 
 
 # ------------------------------------------------------------------------------ ours
@@ -303,7 +314,9 @@ def run_ours(args):
             pinned[k_] = t_
         out = torch.empty((pulse.ny, pulse.nx), dtype=torch.float64, pin_memory=True)
         p = T.Params(nx=pulse.nx, ny=pulse.ny, dx=pulse.dx, dt=pulse.dt, x0=pulse.x0, y0=pulse.y0, precision=prec,
-                     src_mode=T.TRTR_SRC_PULSE if pulse.D_amp else T.TRTR_SRC_NONE)
+                     src_mode=T.TRTR_SRC_PULSE if pulse.D_amp else T.TRTR_SRC_NONE,
+                     tau2_mode=T.TRTR_TAU2_MAGIC if pulse.tau2 is None else T.TRTR_TAU2_FIXED,
+                     tau2=pulse.tau2 or 1.0)
         with T.Solver(p, sh) as s:
             s.set_pulse(pulse.omega, pulse.xc, pulse.yc, pulse.sigma0, pulse.D0, pulse.D_amp)
             s.sync()
@@ -336,7 +349,8 @@ def run_ours(args):
         "config": {"workload": args.workload, "nx": pulse.nx, "ny": pulse.ny, "precision": prec_key,
                    "courant": pulse.courant, "D": f"{pulse.D0}*(1+{pulse.D_amp} sin(pi x) sin(pi y))",
                    "source": "manufactured (in-kernel)" if pulse.D_amp else "none",
-                   "omega": pulse.omega, "sigma0": pulse.sigma0, "parallelism": f"replicas{world}",
+                   "omega": pulse.omega, "sigma0": pulse.sigma0,
+                   "tau2": "magic 1/12" if pulse.tau2 is None else pulse.tau2, "parallelism": f"replicas{world}",
                    "l2_flush": f"inputs larger than L2: {2 * 9 * pop_bytes * n_nodes / 1e9:.2f} GB of populations"},
         "roofline": roofline,
         "gpu_launches": gpu_launches,

@@ -73,15 +73,18 @@ trtr_status ensure_tmp(trtr_ctx* ctx, size_t doubles) {
     return TRTR_OK;
 }
 
-// Stages `count` doubles of caller input on the device; returns the device pointer to read.
+// Stages `count` doubles of caller input on the device into slot `slot` of the staging
+// buffer; returns the device pointer to read.  The caller must have sized the buffer for
+// every slot of the call with ensure_tmp first: growing it frees the old buffer, which
+// would invalidate pointers to slots staged earlier in the same call.
 trtr_status stage_in(trtr_ctx* ctx, const double* src, size_t count, int on_device, size_t slot,
                      const double** dev) {
     if (on_device) {
         *dev = src;
         return TRTR_OK;
     }
-    trtr_status s = ensure_tmp(ctx, (slot + 1) * count);
-    if (s != TRTR_OK) return s;
+    if (ctx->dtmp_len < (slot + 1) * count)
+        return fail(ctx, TRTR_ESTATE, "internal: staging buffer not sized for slot %zu", slot);
     double* d = ctx->dtmp + slot * count;
     TRTR_CUDA(ctx, cudaMemcpyAsync(d, src, count * sizeof(double), cudaMemcpyHostToDevice, ctx->stream),
               "host-to-device copy");
@@ -250,7 +253,8 @@ static trtr_status set_source_impl(trtr_ctx* ctx, const double* S, int on_device
     else if (ctx->S_prev == ctx->S_cur || ctx->S_prev < 0) dst = ctx->S_cur ^ 1;
     else dst = ctx->S_cur;
     const double* dev = nullptr;
-    trtr_status s = stage_in(ctx, S, n, on_device, 0, &dev);
+    trtr_status s = on_device ? TRTR_OK : ensure_tmp(ctx, n);
+    if (s == TRTR_OK) s = stage_in(ctx, S, n, on_device, 0, &dev);
     if (s != TRTR_OK) return s;
     s = check_launch(ctx, trtr::launch_convert_source(ctx, dev, ctx->S[dst]), "source conversion");
     if (s != TRTR_OK) return s;
@@ -271,7 +275,8 @@ trtr_status trtr_set_fields(trtr_ctx* ctx, const double* ux, const double* uy, c
                 return fail(ctx, TRTR_EINVAL, "D must be > 0 and finite at every node (node %zu: %g)", k, D[k]);
     }
     const double *dux, *duy, *dD = nullptr;
-    trtr_status s = stage_in(ctx, ux, n, on_device, 0, &dux);
+    trtr_status s = on_device ? TRTR_OK : ensure_tmp(ctx, 3 * n);
+    if (s == TRTR_OK) s = stage_in(ctx, ux, n, on_device, 0, &dux);
     if (s == TRTR_OK) s = stage_in(ctx, uy, n, on_device, 1, &duy);
     if (s == TRTR_OK && D) s = stage_in(ctx, D, n, on_device, 2, &dD);
     if (s != TRTR_OK) return s;
@@ -280,8 +285,7 @@ trtr_status trtr_set_fields(trtr_ctx* ctx, const double* ux, const double* uy, c
     ctx->fields_set = true;
     if (S) {
         ctx->S_cur = ctx->S_prev = -1;
-        // staging slot 0 is reused: wait for the conversion above to have read it
-        if (!on_device) TRTR_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "field conversion");
+        // staging slot 0 is reused; the copy into it is ordered after the conversion above
         s = set_source_impl(ctx, S, on_device);
         if (s != TRTR_OK) return s;
     }
@@ -319,8 +323,8 @@ trtr_status trtr_init_equilibrium(trtr_ctx* ctx, const double* phi0, int on_devi
         return fail(ctx, TRTR_ESTATE, "src_mode PULSE needs trtr_set_pulse");
     const double* dev = nullptr;
     if (phi0) {
-        if (!on_device) TRTR_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "staging");
-        trtr_status s = stage_in(ctx, phi0, n_nodes(ctx), on_device, 0, &dev);
+        trtr_status s = on_device ? TRTR_OK : ensure_tmp(ctx, n_nodes(ctx));
+        if (s == TRTR_OK) s = stage_in(ctx, phi0, n_nodes(ctx), on_device, 0, &dev);
         if (s != TRTR_OK) return s;
     }
     trtr_status s = check_launch(ctx, trtr::launch_init_equilibrium(ctx, dev), "init");
@@ -412,8 +416,8 @@ trtr_status trtr_error_vs(trtr_ctx* ctx, const double* phi_ref, int on_device, d
     trtr_status s;
     if (!ready(ctx, &s)) return s;
     const double* dev = nullptr;
-    if (!on_device) TRTR_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "staging");
-    s = stage_in(ctx, phi_ref, n_nodes(ctx), on_device, 0, &dev);
+    s = on_device ? TRTR_OK : ensure_tmp(ctx, n_nodes(ctx));
+    if (s == TRTR_OK) s = stage_in(ctx, phi_ref, n_nodes(ctx), on_device, 0, &dev);
     if (s != TRTR_OK) return s;
     double r[2];
     s = reduce(ctx, trtr::kReduceField, dev, r);
@@ -447,8 +451,8 @@ trtr_status trtr_set_populations(trtr_ctx* ctx, const double* g, int on_device, 
     if (!g || step < 0) return fail(ctx, TRTR_EINVAL, "g is NULL or step < 0");
     if (!ctx->fields_set) return fail(ctx, TRTR_ESTATE, "fields not set");
     const double* dev = nullptr;
-    if (!on_device) TRTR_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "staging");
-    trtr_status s = stage_in(ctx, g, trtr::kQ * n_nodes(ctx), on_device, 0, &dev);
+    trtr_status s = on_device ? TRTR_OK : ensure_tmp(ctx, trtr::kQ * n_nodes(ctx));
+    if (s == TRTR_OK) s = stage_in(ctx, g, trtr::kQ * n_nodes(ctx), on_device, 0, &dev);
     if (s != TRTR_OK) return s;
     s = check_launch(ctx, trtr::launch_set_populations(ctx, dev), "set populations");
     if (s != TRTR_OK) return s;

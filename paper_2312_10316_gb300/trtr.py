@@ -381,6 +381,9 @@ def pulse_solver(pulse, precision: int = TRTR_F32, stream: int | None = None, sr
     """A Solver set up for a ``workloads.Pulse`` (fields from the closed form, on the device)."""
     if src_mode is None:
         src_mode = TRTR_SRC_PULSE if pulse.D_amp != 0.0 else TRTR_SRC_NONE
+    if pulse.tau2 is not None:
+        overrides.setdefault("tau2_mode", TRTR_TAU2_FIXED)
+        overrides.setdefault("tau2", pulse.tau2)
     p = Params(nx=pulse.nx, ny=pulse.ny, dx=pulse.dx, dt=pulse.dt, x0=pulse.x0, y0=pulse.y0,
                precision=precision, src_mode=src_mode, grad_mode=TRTR_GRAD_ONESIDED_EDGE, **overrides)
     s = Solver(p, stream)

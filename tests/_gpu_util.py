@@ -17,7 +17,8 @@ def oracle_for_pulse(pulse: W.Pulse, src_mode: int | None = None) -> oracle.Sim:
         src_mode = 2 if pulse.D_amp != 0.0 else 0
     sp = oracle.SimParams(nx=pulse.nx, ny=pulse.ny, dx=pulse.dx, dt=pulse.dt, x0=pulse.x0, y0=pulse.y0,
                           src_mode=src_mode, grad_mode=1, omega=pulse.omega, xc=pulse.xc, yc=pulse.yc,
-                          sigma0=pulse.sigma0, D0=pulse.D0, D_amp=pulse.D_amp)
+                          sigma0=pulse.sigma0, D0=pulse.D0, D_amp=pulse.D_amp,
+                          tau2_mode=0 if pulse.tau2 is None else 1, tau2=pulse.tau2 or 1.0)
     s = oracle.Sim(sp)
     f = W.fields(pulse)
     s.set_fields(f["ux"], f["uy"], f["D"])

@@ -421,7 +421,24 @@ def pin_second_order_convergence(lib, sizes=(64, 128, 256)):
         assert errs[-1] < 1e-4, (key, errs)
 
 
+def pin_error_and_mass_definitions(lib):
+    """Eq. (33) and the mass on closed forms: a uniform state w_i * c has phi = c and mass
+    c * nx * ny; against phi_ref = c + delta the RMS error is |delta| and the relative L2
+    error |delta| / |c + delta|."""
+    nx, ny, c, delta = 6, 5, 0.7, 0.03
+    p = oracle.SimParams(nx=nx, ny=ny, dx=0.1, dt=0.01)
+    sim = oracle.Sim(p, lib)
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    sim.set_g(np.broadcast_to(w[:, None, None] * c, (9, ny, nx)).copy())
+    assert np.allclose(sim.phi(), c, atol=1e-15)
+    assert abs(sim.mass() - c * nx * ny) < 1e-13
+    rms, rel = sim.error(np.full((ny, nx), c + delta))
+    assert abs(rms - delta) < 1e-14 and abs(rel - delta / (c + delta)) < 1e-14
+    sim.close()
+
+
 ALL_PINS = [
+    pin_error_and_mass_definitions,
     pin_lattice,
     pin_equilibrium_moments,
     pin_collision_moment_space,
