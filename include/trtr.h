@@ -175,6 +175,39 @@ trtr_status trtr_sync(trtr_ctx* ctx);
 /* Number of kernels the library enqueued on this context since creation (launch count). */
 trtr_status trtr_launch_count(const trtr_ctx* ctx, long* launches);
 
+/* Largest grid height (rows) that trtr_phi_sums_noalloc accepts. */
+#define TRTR_NOALLOC_MAX_ROWS 16384
+
+/* The paper has no counterpart to this entry point; it exists for callers that cannot
+ * allocate device memory: code whose device memory is owned by another allocator (for
+ * example a framework's caching allocator that has reserved nearly all of HBM, so a
+ * cudaMalloc would fail or fragment it), latency-critical loops where the implicit
+ * synchronisation of cudaMalloc/cudaFree is not acceptable, and plug-in hosts whose policy
+ * forbids libraries from allocating.  It allocates nothing: no cudaMalloc, no cudaFree, no
+ * allocating library call.
+ *
+ * Computes, in FP64, out[0] = sum over nodes of phi = sum_i g_i, and, when phi_ref is not
+ * NULL, out[1] = sum (phi - phi_ref)^2 and out[2] = sum phi_ref^2 (else both 0), from which
+ * the caller forms the mass, the RMS error sqrt(out[1] / (nx ny)) and the relative L2 error
+ * sqrt(out[1] / out[2]).
+ *   g       device memory, [9][ny][nx] doubles: pre-collision populations (the layout that
+ *           trtr_get_populations writes);
+ *   phi_ref device memory, [ny][nx] doubles, or NULL;
+ *   out     device memory, 3 doubles, written by the last kernel of the call;
+ *   cuda_stream  a cudaStream_t (NULL = legacy default stream) the two kernels run on; the
+ *           call returns once they are enqueued.
+ * Its scratch is a fixed array of TRTR_NOALLOC_MAX_ROWS x 3 doubles (384 KiB) in static
+ * device memory, which every device that loads the library holds until the process exits.
+ * ny > TRTR_NOALLOC_MAX_ROWS, nx < 1, ny < 1 or a NULL g / out return TRTR_EINVAL with
+ * nothing enqueued.  The first call on a device (with that device current) looks up the
+ * array's device address; make that first call before any stream capture.  Every call
+ * shares the array and it keeps the last call's contents (each call overwrites rows
+ * [0, ny) before reading them, so nothing needs clearing); calls that overlap on the GPU --
+ * on different streams, or from several host threads -- race on it and must be serialised
+ * by the caller.  TRTR_ECUDA: the address lookup or a launch failed. */
+trtr_status trtr_phi_sums_noalloc(const double* g, int nx, int ny, const double* phi_ref, double* out,
+                                  void* cuda_stream);
+
 /* Static text of a status code. */
 const char* trtr_status_str(trtr_status s);
 

@@ -69,6 +69,7 @@ _SIGNATURES = {
     "trtr_load": (_st, [_vp, _vp, ctypes.c_size_t]),
     "trtr_sync": (_st, [_vp]),
     "trtr_launch_count": (_st, [_vp, ctypes.POINTER(ctypes.c_long)]),
+    "trtr_phi_sums_noalloc": (_st, [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]),
     "trtr_status_str": (ctypes.c_char_p, [_st]),
     "trtr_last_error": (ctypes.c_char_p, [_vp]),
     "trtr_d2q9": (None, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _dbl_p]),
@@ -246,6 +247,22 @@ def trtr_launch_count(ctx) -> int:
     v = ctypes.c_long()
     _check(ctx, lib.trtr_launch_count(ctx, ctypes.byref(v)))
     return v.value
+
+
+def trtr_phi_sums_noalloc(g, nx: int, ny: int, phi_ref, out, cuda_stream: int | None = None) -> int:
+    """FP64 sums of phi over caller-owned device populations with no device allocation:
+    g (9*ny*nx float64 CUDA tensor), phi_ref (ny*nx float64 CUDA tensor or None), out (3
+    float64 CUDA tensor).  Returns the status code (no exception), since callers of this
+    entry point often run where raising is not wanted."""
+    for name, t, count in (("g", g, 9 * nx * ny), ("out", out, 3)):
+        if not getattr(t, "is_cuda", False):
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.numel() < count:
+            raise ValueError(f"{name} holds {t.numel()} values, needs {count}")
+    if phi_ref is not None and (not getattr(phi_ref, "is_cuda", False) or phi_ref.numel() < nx * ny):
+        raise ValueError("phi_ref must be a CUDA tensor of ny*nx values or None")
+    return int(lib.trtr_phi_sums_noalloc(g.data_ptr(), int(nx), int(ny),
+                                         None if phi_ref is None else phi_ref.data_ptr(), out.data_ptr(), cuda_stream))
 
 
 def trtr_status_str(s: int) -> str:
