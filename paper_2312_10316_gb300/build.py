@@ -45,9 +45,10 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(f) <= t for f in _deps())
 
 
-def build_library(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None) -> str:
-    """Compile and link libtrtr.so; returns its path.  Raises on any compiler error."""
-    if not force and up_to_date():
+def build_library(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None,
+                  out: str | None = None) -> str:
+    """Compile and link libtrtr.so (or `out`); returns its path.  Raises on any compiler error."""
+    if not force and out is None and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
@@ -70,13 +71,14 @@ def build_library(force: bool = False, verbose: bool = False, extra_flags: list[
             errors.append(f"{s}:\n{out.decode(errors='replace')}")
     if errors:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
-    tmp = LIB + ".tmp"
+    target = out or LIB
+    tmp = target + ".tmp"
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout.decode(errors="replace"))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, target)
+    return target
 
 
 if __name__ == "__main__":

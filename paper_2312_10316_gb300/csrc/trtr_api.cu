@@ -97,12 +97,22 @@ trtr_status check_launch(trtr_ctx* ctx, cudaError_t e, const char* what) {
     return TRTR_OK;
 }
 
+// Synchronises the context's stream and reports a step kernel whose bounded wait gave up.
+trtr_status sync_and_check(trtr_ctx* ctx, const char* where) {
+    int* hflag = reinterpret_cast<int*>(ctx->hres + 3);
+    TRTR_CUDA(ctx, cudaMemcpyAsync(hflag, ctx->dflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), where);
+    TRTR_CUDA(ctx, cudaStreamSynchronize(ctx->stream), where);
+    if (*hflag != 0) return fail(ctx, TRTR_ETIMEOUT, "%s: a step kernel timed out waiting for its TMA loads", where);
+    return TRTR_OK;
+}
+
 trtr_status reduce(trtr_ctx* ctx, int kind, const double* ref_dev, double out[2]) {
     trtr_status s = check_launch(ctx, trtr::launch_reduce(ctx, kind, ref_dev), "reduction launch");
     if (s != TRTR_OK) return s;
     TRTR_CUDA(ctx, cudaMemcpyAsync(ctx->hres, ctx->dres, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
               "reduction result copy");
-    TRTR_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "reduction");
+    s = sync_and_check(ctx, "reduction");
+    if (s != TRTR_OK) return s;
     out[0] = ctx->hres[0];
     out[1] = ctx->hres[1];
     return TRTR_OK;
@@ -165,18 +175,20 @@ trtr_status trtr_create(const trtr_params* p, void* cuda_stream, trtr_ctx** out)
     if (p->grad_mode != TRTR_GRAD_PERIODIC && p->grad_mode != TRTR_GRAD_ONESIDED_EDGE) return TRTR_EINVAL;
     if (p->src_mode < TRTR_SRC_NONE || p->src_mode > TRTR_SRC_PULSE) return TRTR_EINVAL;
     if (p->check_every < 0 || !isfinite(p->phi_ref)) return TRTR_EINVAL;
-    const long long pitch = ((long long)p->nx + 31) / 32 * 32;
-    if (pitch * (long long)p->ny >= (1LL << 31)) return TRTR_EINVAL;
+    const trtr::PlaneLayout lp = trtr::make_layout(p->nx, p->ny, (int)es);
+    const trtr::PlaneLayout lf = trtr::make_layout(p->nx, p->ny, p->precision == TRTR_F64 ? 8 : 4);
+    if ((long long)trtr::kQ * (long long)lp.plane >= (1LL << 31) || 2LL * (long long)lf.plane >= (1LL << 31))
+        return TRTR_EINVAL;
 
     trtr_ctx* ctx = new (std::nothrow) trtr_ctx();
     if (!ctx) return TRTR_ENOMEM;
-    memset(ctx, 0, sizeof(*ctx));
+    memset(static_cast<void*>(ctx), 0, sizeof(*ctx));
     ctx->p = *p;
     ctx->stream = (cudaStream_t)cuda_stream;
     ctx->esize = (int)es;
     ctx->csize = p->precision == TRTR_F64 ? 8 : 4;
-    ctx->pitch = (int)pitch;
-    ctx->plane = (size_t)pitch * (size_t)p->ny;
+    ctx->lp = lp;
+    ctx->lf = lf;
     ctx->S_cur = ctx->S_prev = -1;
 
     cudaError_t e = cudaGetDevice(&ctx->device);
@@ -188,23 +200,23 @@ trtr_status trtr_create(const trtr_params* p, void* cuda_stream, trtr_ctx** out)
     }
     ctx->red_blocks = ctx->num_sms * 4;
 
-    const size_t pop_bytes = trtr::kQ * ctx->plane * es;
-    const size_t fld_bytes = ctx->plane * ctx->csize;
+    const size_t pop_bytes = trtr::kQ * lp.plane * es;
+    const size_t fld_bytes = lf.plane * ctx->csize;
     struct {
         void** ptr;
         size_t bytes;
+        bool zero;
     } allocs[] = {
-        {&ctx->pop[0], pop_bytes},
-        {&ctx->pop[1], pop_bytes},
-        {&ctx->ux, fld_bytes},
-        {&ctx->uy, fld_bytes},
-        {&ctx->Dh, fld_bytes},
-        {&ctx->S[0], p->src_mode == TRTR_SRC_FIELD ? fld_bytes : 0},
-        {&ctx->S[1], p->src_mode == TRTR_SRC_FIELD ? fld_bytes : 0},
-        {&ctx->tab_x, 2 * (size_t)pitch * ctx->csize},
-        {&ctx->tab_y, 2 * (size_t)p->ny * ctx->csize},
-        {(void**)&ctx->scratch, 2 * (size_t)ctx->red_blocks * sizeof(double)},
-        {(void**)&ctx->dres, 4 * sizeof(double)},
+        {&ctx->pop[0], pop_bytes, true},
+        {&ctx->pop[1], pop_bytes, true},
+        {&ctx->uv, 2 * fld_bytes, true},
+        {&ctx->Dh, fld_bytes, true},
+        {&ctx->S, p->src_mode == TRTR_SRC_FIELD ? 2 * fld_bytes : 0, true},
+        {&ctx->tab_x, 2 * (size_t)p->nx * ctx->csize, true},
+        {&ctx->tab_y, 2 * (size_t)p->ny * ctx->csize, true},
+        {(void**)&ctx->scratch, 2 * (size_t)ctx->red_blocks * sizeof(double), false},
+        {(void**)&ctx->dres, 4 * sizeof(double), false},
+        {(void**)&ctx->dflag, sizeof(int), true},
     };
     for (auto& a : allocs) {
         if (a.bytes == 0) continue;
@@ -213,19 +225,22 @@ trtr_status trtr_create(const trtr_params* p, void* cuda_stream, trtr_ctx** out)
             trtr_destroy(ctx);
             return TRTR_ENOMEM;
         }
+        // defined contents everywhere, padding and ghost cells included
+        if (a.zero && cudaMemsetAsync(*a.ptr, 0, a.bytes, ctx->stream) != cudaSuccess) {
+            cudaGetLastError();
+            trtr_destroy(ctx);
+            return TRTR_ECUDA;
+        }
     }
     if (cudaMallocHost((void**)&ctx->hres, 4 * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         trtr_destroy(ctx);
         return TRTR_ENOMEM;
     }
-    // Zero the padded population planes so that the pitch columns never hold garbage.
-    for (int b = 0; b < 2; ++b) {
-        if (cudaMemsetAsync(ctx->pop[b], 0, pop_bytes, ctx->stream) != cudaSuccess) {
-            cudaGetLastError();
-            trtr_destroy(ctx);
-            return TRTR_ECUDA;
-        }
+    if (trtr::encode_maps(ctx) != cudaSuccess) {
+        cudaGetLastError();
+        trtr_destroy(ctx);
+        return TRTR_ECUDA;
     }
     *out = ctx;
     return TRTR_OK;
@@ -235,8 +250,8 @@ trtr_status trtr_destroy(trtr_ctx* ctx) {
     if (!ctx) return TRTR_OK;
     cudaStreamSynchronize(ctx->stream);
     cudaGetLastError();
-    void* ptrs[] = {ctx->pop[0], ctx->pop[1], ctx->ux, ctx->uy, ctx->Dh, ctx->S[0], ctx->S[1],
-                    ctx->tab_x, ctx->tab_y, ctx->scratch, ctx->dres, ctx->dtmp};
+    void* ptrs[] = {ctx->pop[0], ctx->pop[1], ctx->uv,      ctx->Dh,   ctx->S,     ctx->tab_x,
+                    ctx->tab_y,  ctx->scratch, ctx->dres, ctx->dflag, ctx->dtmp};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (ctx->hres) cudaFreeHost(ctx->hres);
@@ -256,7 +271,7 @@ static trtr_status set_source_impl(trtr_ctx* ctx, const double* S, int on_device
     trtr_status s = on_device ? TRTR_OK : ensure_tmp(ctx, n);
     if (s == TRTR_OK) s = stage_in(ctx, S, n, on_device, 0, &dev);
     if (s != TRTR_OK) return s;
-    s = check_launch(ctx, trtr::launch_convert_source(ctx, dev, ctx->S[dst]), "source conversion");
+    s = check_launch(ctx, trtr::launch_convert_source(ctx, dev, dst), "source conversion");
     if (s != TRTR_OK) return s;
     ctx->S_cur = dst;
     return TRTR_OK;
@@ -379,8 +394,7 @@ trtr_status trtr_moments(trtr_ctx* ctx, double* phi_out, int on_device) {
     if (!on_device)
         TRTR_CUDA(ctx, cudaMemcpyAsync(phi_out, dev, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
                   "device-to-host copy");
-    TRTR_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "moments");
-    return TRTR_OK;
+    return sync_and_check(ctx, "moments");
 }
 
 trtr_status trtr_mass(trtr_ctx* ctx, double* sum_phi) {
@@ -442,8 +456,7 @@ trtr_status trtr_get_populations(trtr_ctx* ctx, double* g_out, int on_device) {
     if (!on_device)
         TRTR_CUDA(ctx, cudaMemcpyAsync(g_out, dev, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
                   "device-to-host copy");
-    TRTR_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "get populations");
-    return TRTR_OK;
+    return sync_and_check(ctx, "get populations");
 }
 
 trtr_status trtr_set_populations(trtr_ctx* ctx, const double* g, int on_device, long step) {
@@ -485,8 +498,7 @@ trtr_status trtr_sample_populations(trtr_ctx* ctx, const long* nodes, int count,
     TRTR_CUDA(ctx, cudaMemcpyAsync(out, dout, (size_t)count * trtr::kQ * sizeof(double), cudaMemcpyDeviceToHost,
                                    ctx->stream),
               "device-to-host copy");
-    TRTR_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "sample");
-    return TRTR_OK;
+    return sync_and_check(ctx, "sample");
 }
 
 trtr_status trtr_time(const trtr_ctx* ctx, long* step, double* t) {
@@ -500,8 +512,8 @@ trtr_status trtr_save(trtr_ctx* ctx, void* host_buf, size_t* bytes) {
     if (!ctx || !bytes) return TRTR_EINVAL;
     trtr_status s;
     if (!ready(ctx, &s)) return s;
-    const size_t pop_bytes = trtr::kQ * ctx->plane * ctx->esize;
-    const size_t src_bytes = ctx->p.src_mode == TRTR_SRC_FIELD ? 2 * ctx->plane * ctx->csize : 0;
+    const size_t pop_bytes = trtr::kQ * ctx->lp.plane * ctx->esize;
+    const size_t src_bytes = ctx->p.src_mode == TRTR_SRC_FIELD ? 2 * ctx->lf.plane * ctx->csize : 0;
     const size_t need = sizeof(SaveHeader) + pop_bytes + src_bytes;
     if (!host_buf) {
         *bytes = need;
@@ -524,15 +536,11 @@ trtr_status trtr_save(trtr_ctx* ctx, void* host_buf, size_t* bytes) {
     memcpy(b, &h, sizeof(h));
     TRTR_CUDA(ctx, cudaMemcpyAsync(b + sizeof(h), ctx->pop[ctx->cur], pop_bytes, cudaMemcpyDeviceToHost, ctx->stream),
               "save copy");
-    if (src_bytes) {
-        const size_t half = src_bytes / 2;
-        TRTR_CUDA(ctx, cudaMemcpyAsync(b + sizeof(h) + pop_bytes, ctx->S[0], half, cudaMemcpyDeviceToHost, ctx->stream),
+    if (src_bytes)
+        TRTR_CUDA(ctx, cudaMemcpyAsync(b + sizeof(h) + pop_bytes, ctx->S, src_bytes, cudaMemcpyDeviceToHost, ctx->stream),
                   "save copy");
-        TRTR_CUDA(ctx, cudaMemcpyAsync(b + sizeof(h) + pop_bytes + half, ctx->S[1], half, cudaMemcpyDeviceToHost,
-                                       ctx->stream),
-                  "save copy");
-    }
-    TRTR_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "save");
+    s = sync_and_check(ctx, "save");
+    if (s != TRTR_OK) return s;
     *bytes = need;
     return TRTR_OK;
 }
@@ -542,21 +550,18 @@ trtr_status trtr_load(trtr_ctx* ctx, const void* host_buf, size_t bytes) {
     if (bytes < sizeof(SaveHeader)) return fail(ctx, TRTR_EINVAL, "checkpoint too small");
     SaveHeader h;
     memcpy(&h, host_buf, sizeof(h));
-    const size_t pop_bytes = trtr::kQ * ctx->plane * ctx->esize;
-    const size_t src_bytes = ctx->p.src_mode == TRTR_SRC_FIELD ? 2 * ctx->plane * ctx->csize : 0;
+    const size_t pop_bytes = trtr::kQ * ctx->lp.plane * ctx->esize;
+    const size_t src_bytes = ctx->p.src_mode == TRTR_SRC_FIELD ? 2 * ctx->lf.plane * ctx->csize : 0;
     if (h.magic != kSaveMagic || h.nx != ctx->p.nx || h.ny != ctx->p.ny || h.precision != ctx->p.precision ||
         h.src_mode != ctx->p.src_mode || h.pop_bytes != pop_bytes || h.src_bytes != src_bytes ||
-        bytes < sizeof(h) + pop_bytes + src_bytes || h.step < 0)
+        bytes < sizeof(h) + pop_bytes + src_bytes || h.step < 0 || h.S_cur < -1 || h.S_cur > 1 || h.S_prev < -1 ||
+        h.S_prev > 1)
         return fail(ctx, TRTR_EINVAL, "checkpoint does not match this context");
     const char* b = (const char*)host_buf;
     TRTR_CUDA(ctx, cudaMemcpyAsync(ctx->pop[ctx->cur], b + sizeof(h), pop_bytes, cudaMemcpyHostToDevice, ctx->stream),
               "load copy");
     if (src_bytes) {
-        const size_t half = src_bytes / 2;
-        TRTR_CUDA(ctx, cudaMemcpyAsync(ctx->S[0], b + sizeof(h) + pop_bytes, half, cudaMemcpyHostToDevice, ctx->stream),
-                  "load copy");
-        TRTR_CUDA(ctx, cudaMemcpyAsync(ctx->S[1], b + sizeof(h) + pop_bytes + half, half, cudaMemcpyHostToDevice,
-                                       ctx->stream),
+        TRTR_CUDA(ctx, cudaMemcpyAsync(ctx->S, b + sizeof(h) + pop_bytes, src_bytes, cudaMemcpyHostToDevice, ctx->stream),
                   "load copy");
         ctx->S_cur = h.S_cur;
         ctx->S_prev = h.S_prev;
@@ -569,7 +574,8 @@ trtr_status trtr_load(trtr_ctx* ctx, const void* host_buf, size_t bytes) {
 
 trtr_status trtr_sync(trtr_ctx* ctx) {
     if (!ctx) return TRTR_EINVAL;
-    TRTR_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "sync");
+    trtr_status s = sync_and_check(ctx, "sync");
+    if (s != TRTR_OK) return s;
     TRTR_CUDA(ctx, cudaGetLastError(), "sync");
     return TRTR_OK;
 }

@@ -1,6 +1,7 @@
-// trtr_aux.cu -- kernels around the step: coefficient fields, the pulse closed form,
-// equilibrium initialisation (shifted into the pull layout), the phi moment, the FP64
-// reductions (mass, RMS / relative L2 error of Eq. (33)) and population I/O.
+// trtr_aux.cu -- kernels around the step: coefficient fields (with their ghost cells),
+// the pulse closed form, equilibrium initialisation (shifted into the pull layout), the
+// phi moment, the FP64 reductions (mass, RMS / relative L2 error of Eq. (33)) and
+// population I/O.
 #include <math.h>
 
 #include <type_traits>
@@ -20,6 +21,20 @@ PulseTime pulse_at(const Pulse& p, double t) {
     return r;
 }
 
+PlaneLayout make_layout(int nx, int ny, int elem_bytes) {
+    PlaneLayout L;
+    L.nx = nx;
+    L.ny = ny;
+    const int line = 128 / elem_bytes;  // elements per 128-byte line
+    L.gx = line;
+    long long pitch = ((long long)nx + 2LL * line + line - 1) / line * line;
+    if (pitch < 320) pitch = 320;  // wider than every TMA box (<= 256 elements + origin shift)
+    L.pitch = (int)pitch;
+    L.rows = ny + 2 < 16 ? 16 : ny + 2;
+    L.plane = (size_t)L.rows * (size_t)L.pitch;
+    return L;
+}
+
 namespace {
 
 __constant__ int c_ex[kQ] = {0, 1, -1, 0, 0, 1, -1, 1, -1};
@@ -31,50 +46,71 @@ constexpr int kThreads = 256;
 
 __device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
+// Value of a field at ghosted position (i, j), i in [-1, nx], j in [-1, ny], from its interior
+// values f(i, j): periodic wrap, or the linear extrapolation 2 f(edge) - f(edge -+ 1) (grad
+// mode one-sided; a single node repeats itself).  Corners compose the two rules.
+template <typename F>
+__device__ __forceinline__ double ghosted(const F& f, int i, int j, int nx, int ny, int grad_mode) {
+    auto along_x = [&](int jj) -> double {
+        if (i >= 0 && i < nx) return f(i, jj);
+        if (grad_mode == TRTR_GRAD_PERIODIC || nx == 1) return f(wrap(i, nx), jj);
+        return i < 0 ? 2.0 * f(0, jj) - f(1, jj) : 2.0 * f(nx - 1, jj) - f(nx - 2, jj);
+    };
+    if (j >= 0 && j < ny) return along_x(j);
+    if (grad_mode == TRTR_GRAD_PERIODIC || ny == 1) return along_x(wrap(j, ny));
+    return j < 0 ? 2.0 * along_x(0) - along_x(1) : 2.0 * along_x(ny - 1) - along_x(ny - 2);
+}
+
+// u (with ghosts) and D from caller arrays [ny][nx] in physical units.
 template <typename C>
-__global__ void convert_fields_kernel(C* ux, C* uy, C* Dh, const double* sux, const double* suy,
-                                      const double* sD, int nx, int ny, int pitch, double u_scale,
-                                      double d_scale, double dh_const, int use_const) {
-    const size_t n = (size_t)nx * ny;
+__global__ void convert_fields_kernel(C* uv, C* Dh, const double* sux, const double* suy, const double* sD,
+                                      PlaneLayout L, int grad_mode, double u_scale, double d_scale, double dh_const,
+                                      int use_const) {
+    const int gw = L.nx + 2, gh = L.ny + 2;
+    const size_t n = (size_t)gw * gh;
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-        const int j = (int)(k / nx), i = (int)(k - (size_t)j * nx);
-        const size_t o = (size_t)j * pitch + i;
-        ux[o] = C(sux[k] * u_scale);
-        uy[o] = C(suy[k] * u_scale);
-        Dh[o] = C(use_const ? dh_const : sD[k] * d_scale);
+        const int j = (int)(k / gw) - 1, i = (int)(k % gw) - 1;
+        auto fx = [&](int ii, int jj) { return sux[(size_t)jj * L.nx + ii]; };
+        auto fy = [&](int ii, int jj) { return suy[(size_t)jj * L.nx + ii]; };
+        uv[L.at(i, j)] = C(ghosted(fx, i, j, L.nx, L.ny, grad_mode) * u_scale);
+        uv[L.plane + L.at(i, j)] = C(ghosted(fy, i, j, L.nx, L.ny, grad_mode) * u_scale);
+        if (i >= 0 && i < L.nx && j >= 0 && j < L.ny)
+            Dh[L.at(i, j)] = C(use_const ? dh_const : sD[(size_t)j * L.nx + i] * d_scale);
     }
 }
 
 template <typename C>
-__global__ void pulse_fields_kernel(C* ux, C* uy, C* Dh, C* tab_x, C* tab_y, int nx, int ny, int pitch,
-                                    double x0, double y0, double dx, double dt, Pulse pp, double dh_const,
-                                    int use_const) {
-    const size_t n = (size_t)nx * ny;
+__global__ void pulse_fields_kernel(C* uv, C* Dh, C* tab_x, C* tab_y, PlaneLayout L, int grad_mode, double x0,
+                                    double y0, double dx, double dt, Pulse pp, double dh_const, int use_const) {
+    const int gw = L.nx + 2, gh = L.ny + 2;
+    const size_t n = (size_t)gw * gh;
     const double us = dt / dx, ds = dt / (dx * dx);
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-        const int j = (int)(k / nx), i = (int)(k - (size_t)j * nx);
+        const int j = (int)(k / gw) - 1, i = (int)(k % gw) - 1;
+        auto fx = [&](int ii, int jj) { return -pp.omega * (y0 + jj * dx); };
+        auto fy = [&](int ii, int jj) { return pp.omega * (x0 + ii * dx); };
+        uv[L.at(i, j)] = C(ghosted(fx, i, j, L.nx, L.ny, grad_mode) * us);
+        uv[L.plane + L.at(i, j)] = C(ghosted(fy, i, j, L.nx, L.ny, grad_mode) * us);
+        if (i < 0 || i >= L.nx || j < 0 || j >= L.ny) continue;
         const double x = x0 + i * dx, y = y0 + j * dx;
-        const size_t o = (size_t)j * pitch + i;
-        ux[o] = C(-pp.omega * y * us);
-        uy[o] = C(pp.omega * x * us);
-        Dh[o] = C(use_const ? dh_const : pp.D0 * (1.0 + pp.D_amp * sin(M_PI * x) * sin(M_PI * y)) * ds);
+        Dh[L.at(i, j)] = C(use_const ? dh_const : pp.D0 * (1.0 + pp.D_amp * sin(M_PI * x) * sin(M_PI * y)) * ds);
         if (j == 0) {
             tab_x[i] = C(sin(M_PI * x));
-            tab_x[pitch + i] = C(cos(M_PI * x));
+            tab_x[L.nx + i] = C(cos(M_PI * x));
         }
         if (i == 0) {
             tab_y[j] = C(sin(M_PI * y));
-            tab_y[ny + j] = C(cos(M_PI * y));
+            tab_y[L.ny + j] = C(cos(M_PI * y));
         }
     }
 }
 
 template <typename C>
-__global__ void convert_source_kernel(C* dst, const double* S, int nx, int ny, int pitch, double dt) {
-    const size_t n = (size_t)nx * ny;
+__global__ void convert_source_kernel(C* dst, const double* S, PlaneLayout L, double dt) {
+    const size_t n = (size_t)L.nx * L.ny;
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-        const int j = (int)(k / nx), i = (int)(k - (size_t)j * nx);
-        dst[(size_t)j * pitch + i] = C(dt * S[k]);
+        const int j = (int)(k / L.nx), i = (int)(k - (size_t)j * L.nx);
+        dst[L.at(i, j)] = C(dt * S[k]);
     }
 }
 
@@ -87,47 +123,47 @@ __device__ __forceinline__ double pulse_phi(const PulseTime& pt, double x, doubl
 // P_i(x) = g_i(x + e_i).  Third-order Hermite equilibrium (Eq. (6)) in lattice units:
 // w_i phi [1 + 3 eu + 4.5 ((eu)^2 - |u|^2/3) + 4.5 ((eu)^3 - eu |u|^2)], eu = e_i . uhat.
 template <typename S, typename C>
-__global__ void init_eq_kernel(S* P, const C* ux, const C* uy, const double* phi0, int nx, int ny, int pitch,
-                               size_t plane, double x0, double y0, double dx, PulseTime pt, C phi_ref) {
+__global__ void init_eq_kernel(S* P, const C* uv, const double* phi0, PlaneLayout lp, PlaneLayout lf, double x0,
+                               double y0, double dx, PulseTime pt, C phi_ref) {
+    const int nx = lp.nx, ny = lp.ny;
     const size_t n = (size_t)nx * ny;
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
         const int j = (int)(k / nx), i = (int)(k - (size_t)j * nx);
         for (int q = 0; q < kQ; ++q) {
             const int si = wrap(i + c_ex[q], nx), sj = wrap(j + c_ey[q], ny);
             const double phi = phi0 ? phi0[(size_t)sj * nx + si] : pulse_phi(pt, x0 + si * dx, y0 + sj * dx);
-            const double u = (double)ux[(size_t)sj * pitch + si];
-            const double v = (double)uy[(size_t)sj * pitch + si];
+            const double u = (double)uv[lf.at(si, sj)];
+            const double v = (double)uv[lf.plane + lf.at(si, sj)];
             const double eu = c_ex[q] * u + c_ey[q] * v;
             const double uu = u * u + v * v;
-            const double geq = c_w[q] * phi * (1.0 + 3.0 * eu + 4.5 * (eu * eu - uu / 3.0) + 4.5 * (eu * eu * eu - eu * uu));
-            Store<S>::store(P + q * plane + (size_t)j * pitch + i, (C)geq, (C)(c_w[q]) * phi_ref);
+            const double geq =
+                c_w[q] * phi * (1.0 + 3.0 * eu + 4.5 * (eu * eu - uu / 3.0) + 4.5 * (eu * eu * eu - eu * uu));
+            store_with_ghosts(P + q * lp.plane, lp, i, j, Store<S>::encode((C)geq, (C)(c_w[q]) * phi_ref));
         }
     }
 }
 
 // g_i(x, t_n) = P_i(x - e_i), decoded to the compute type.
 template <typename S, typename C>
-__device__ __forceinline__ C pulled(const S* P, int q, int i, int j, int nx, int ny, int pitch, size_t plane,
-                                    C phi_ref) {
-    const int si = wrap(i - c_ex[q], nx), sj = wrap(j - c_ey[q], ny);
-    return Store<S>::load(P + q * plane + (size_t)sj * pitch + si, (C)(c_w[q]) * phi_ref);
+__device__ __forceinline__ C pulled(const S* P, int q, int i, int j, const PlaneLayout& L, C phi_ref) {
+    const int si = wrap(i - c_ex[q], L.nx), sj = wrap(j - c_ey[q], L.ny);
+    return Store<S>::decode(P[q * L.plane + L.at(si, sj)], (C)(c_w[q]) * phi_ref);
 }
 
 template <typename S, typename C>
-__device__ __forceinline__ double node_phi(const S* P, int i, int j, int nx, int ny, int pitch, size_t plane,
-                                           C phi_ref) {
+__device__ __forceinline__ double node_phi(const S* P, int i, int j, const PlaneLayout& L, C phi_ref) {
     double phi = 0.0;
 #pragma unroll
-    for (int q = 0; q < kQ; ++q) phi += (double)pulled<S, C>(P, q, i, j, nx, ny, pitch, plane, phi_ref);
+    for (int q = 0; q < kQ; ++q) phi += (double)pulled<S, C>(P, q, i, j, L, phi_ref);
     return phi;
 }
 
 template <typename S, typename C>
-__global__ void moments_kernel(double* out, const S* P, int nx, int ny, int pitch, size_t plane, C phi_ref) {
-    const size_t n = (size_t)nx * ny;
+__global__ void moments_kernel(double* out, const S* P, PlaneLayout L, C phi_ref) {
+    const size_t n = (size_t)L.nx * L.ny;
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-        const int j = (int)(k / nx), i = (int)(k - (size_t)j * nx);
-        out[k] = node_phi<S, C>(P, i, j, nx, ny, pitch, plane, phi_ref);
+        const int j = (int)(k / L.nx), i = (int)(k - (size_t)j * L.nx);
+        out[k] = node_phi<S, C>(P, i, j, L, phi_ref);
     }
 }
 
@@ -160,20 +196,20 @@ __device__ __forceinline__ void block_sum2(double& a, double& b) {
 //  kind 0: sum phi;  1: sum (phi - phi_a)^2, sum phi_a^2;  2: same against phi_ref field;
 //  3: number of non-finite populations.
 template <typename S, typename C>
-__global__ void reduce_kernel(double* partial, const S* P, int nx, int ny, int pitch, size_t plane, C phi_ref,
-                              int kind, PulseTime pt, double x0, double y0, double dx, const double* ref) {
-    const size_t n = (size_t)nx * ny;
+__global__ void reduce_kernel(double* partial, const S* P, PlaneLayout L, C phi_ref, int kind, PulseTime pt,
+                              double x0, double y0, double dx, const double* ref) {
+    const size_t n = (size_t)L.nx * L.ny;
     double a = 0.0, b = 0.0;
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-        const int j = (int)(k / nx), i = (int)(k - (size_t)j * nx);
+        const int j = (int)(k / L.nx), i = (int)(k - (size_t)j * L.nx);
         if (kind == kReduceNonFinite) {
             for (int q = 0; q < kQ; ++q) {
-                const double v = (double)pulled<S, C>(P, q, i, j, nx, ny, pitch, plane, phi_ref);
+                const double v = (double)pulled<S, C>(P, q, i, j, L, phi_ref);
                 a += isfinite(v) ? 0.0 : 1.0;
             }
             continue;
         }
-        const double phi = node_phi<S, C>(P, i, j, nx, ny, pitch, plane, phi_ref);
+        const double phi = node_phi<S, C>(P, i, j, L, phi_ref);
         if (kind == kReduceMass) {
             a += phi;
         } else {
@@ -204,36 +240,35 @@ __global__ void finish_kernel(double* out, const double* partial, int nblocks) {
 }
 
 template <typename S, typename C>
-__global__ void get_pop_kernel(double* g, const S* P, int nx, int ny, int pitch, size_t plane, C phi_ref) {
-    const size_t n = (size_t)nx * ny;
+__global__ void get_pop_kernel(double* g, const S* P, PlaneLayout L, C phi_ref) {
+    const size_t n = (size_t)L.nx * L.ny;
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-        const int j = (int)(k / nx), i = (int)(k - (size_t)j * nx);
-        for (int q = 0; q < kQ; ++q) g[q * n + k] = (double)pulled<S, C>(P, q, i, j, nx, ny, pitch, plane, phi_ref);
+        const int j = (int)(k / L.nx), i = (int)(k - (size_t)j * L.nx);
+        for (int q = 0; q < kQ; ++q) g[q * n + k] = (double)pulled<S, C>(P, q, i, j, L, phi_ref);
     }
 }
 
 template <typename S, typename C>
-__global__ void set_pop_kernel(S* P, const double* g, int nx, int ny, int pitch, size_t plane, C phi_ref) {
-    const size_t n = (size_t)nx * ny;
+__global__ void set_pop_kernel(S* P, const double* g, PlaneLayout L, C phi_ref) {
+    const size_t n = (size_t)L.nx * L.ny;
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-        const int j = (int)(k / nx), i = (int)(k - (size_t)j * nx);
+        const int j = (int)(k / L.nx), i = (int)(k - (size_t)j * L.nx);
         for (int q = 0; q < kQ; ++q) {
-            const int si = wrap(i + c_ex[q], nx), sj = wrap(j + c_ey[q], ny);
-            Store<S>::store(P + q * plane + (size_t)j * pitch + i, (C)g[q * n + (size_t)sj * nx + si],
-                            (C)(c_w[q]) * phi_ref);
+            const int si = wrap(i + c_ex[q], L.nx), sj = wrap(j + c_ey[q], L.ny);
+            store_with_ghosts(P + q * L.plane, L, i, j,
+                              Store<S>::encode((C)g[q * n + (size_t)sj * L.nx + si], (C)(c_w[q]) * phi_ref));
         }
     }
 }
 
 template <typename S, typename C>
-__global__ void sample_kernel(double* out, const long* nodes, int count, const S* P, int nx, int ny, int pitch,
-                              size_t plane, C phi_ref) {
+__global__ void sample_kernel(double* out, const long* nodes, int count, const S* P, PlaneLayout L, C phi_ref) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= count * kQ) return;
     const int s = t / kQ, q = t - s * kQ;
     const long k = nodes[s];
-    const int j = (int)(k / nx), i = (int)(k - (long)j * nx);
-    out[t] = (double)pulled<S, C>(P, q, i, j, nx, ny, pitch, plane, phi_ref);
+    const int j = (int)(k / L.nx), i = (int)(k - (long)j * L.nx);
+    out[t] = (double)pulled<S, C>(P, q, i, j, L, phi_ref);
 }
 
 int grid_for(const trtr_ctx* ctx, size_t n) {
@@ -257,7 +292,7 @@ cudaError_t dispatch(trtr_ctx* ctx, F&& f) {
 }  // namespace
 
 cudaError_t launch_convert_fields(trtr_ctx* ctx, const double* ux, const double* uy, const double* D) {
-    const size_t n = (size_t)ctx->p.nx * ctx->p.ny;
+    const size_t n = (size_t)(ctx->p.nx + 2) * (ctx->p.ny + 2);
     const double us = ctx->p.dt / ctx->p.dx, ds = ctx->p.dt / (ctx->p.dx * ctx->p.dx);
     const int use_const = ctx->p.tau1_const > 0.0;
     const double dh = use_const ? (ctx->p.tau1_const - 0.5) / 3.0 : 0.0;
@@ -266,12 +301,12 @@ cudaError_t launch_convert_fields(trtr_ctx* ctx, const double* ux, const double*
         using C = std::remove_pointer_t<decltype(cp)>;
         (void)sp;
         convert_fields_kernel<C><<<grid_for(ctx, n), kThreads, 0, ctx->stream>>>(
-            (C*)ctx->ux, (C*)ctx->uy, (C*)ctx->Dh, ux, uy, D, ctx->p.nx, ctx->p.ny, ctx->pitch, us, ds, dh, use_const);
+            (C*)ctx->uv, (C*)ctx->Dh, ux, uy, D, ctx->lf, ctx->p.grad_mode, us, ds, dh, use_const);
     });
 }
 
 cudaError_t launch_pulse_fields(trtr_ctx* ctx) {
-    const size_t n = (size_t)ctx->p.nx * ctx->p.ny;
+    const size_t n = (size_t)(ctx->p.nx + 2) * (ctx->p.ny + 2);
     const int use_const = ctx->p.tau1_const > 0.0;
     const double dh = use_const ? (ctx->p.tau1_const - 0.5) / 3.0 : 0.0;
     ctx->launches += 1;
@@ -279,19 +314,19 @@ cudaError_t launch_pulse_fields(trtr_ctx* ctx) {
         using C = std::remove_pointer_t<decltype(cp)>;
         (void)sp;
         pulse_fields_kernel<C><<<grid_for(ctx, n), kThreads, 0, ctx->stream>>>(
-            (C*)ctx->ux, (C*)ctx->uy, (C*)ctx->Dh, (C*)ctx->tab_x, (C*)ctx->tab_y, ctx->p.nx, ctx->p.ny, ctx->pitch,
-            ctx->p.x0, ctx->p.y0, ctx->p.dx, ctx->p.dt, ctx->pulse, dh, use_const);
+            (C*)ctx->uv, (C*)ctx->Dh, (C*)ctx->tab_x, (C*)ctx->tab_y, ctx->lf, ctx->p.grad_mode, ctx->p.x0, ctx->p.y0,
+            ctx->p.dx, ctx->p.dt, ctx->pulse, dh, use_const);
     });
 }
 
-cudaError_t launch_convert_source(trtr_ctx* ctx, const double* S, void* dst) {
+cudaError_t launch_convert_source(trtr_ctx* ctx, const double* S, int buffer) {
     const size_t n = (size_t)ctx->p.nx * ctx->p.ny;
     ctx->launches += 1;
     return dispatch(ctx, [&](auto* sp, auto* cp) {
         using C = std::remove_pointer_t<decltype(cp)>;
         (void)sp;
-        convert_source_kernel<C><<<grid_for(ctx, n), kThreads, 0, ctx->stream>>>((C*)dst, S, ctx->p.nx, ctx->p.ny,
-                                                                                  ctx->pitch, ctx->p.dt);
+        convert_source_kernel<C><<<grid_for(ctx, n), kThreads, 0, ctx->stream>>>(
+            (C*)ctx->S + (size_t)buffer * ctx->lf.plane, S, ctx->lf, ctx->p.dt);
     });
 }
 
@@ -303,8 +338,8 @@ cudaError_t launch_init_equilibrium(trtr_ctx* ctx, const double* phi0) {
         using S = std::remove_pointer_t<decltype(sp)>;
         using C = std::remove_pointer_t<decltype(cp)>;
         init_eq_kernel<S, C><<<grid_for(ctx, n), kThreads, 0, ctx->stream>>>(
-            (S*)ctx->pop[ctx->cur], (const C*)ctx->ux, (const C*)ctx->uy, phi0, ctx->p.nx, ctx->p.ny, ctx->pitch,
-            ctx->plane, ctx->p.x0, ctx->p.y0, ctx->p.dx, pt, (C)ctx->p.phi_ref);
+            (S*)ctx->pop[ctx->cur], (const C*)ctx->uv, phi0, ctx->lp, ctx->lf, ctx->p.x0, ctx->p.y0, ctx->p.dx, pt,
+            (C)ctx->p.phi_ref);
     });
 }
 
@@ -314,8 +349,8 @@ cudaError_t launch_moments(trtr_ctx* ctx, double* phi_out) {
     return dispatch(ctx, [&](auto* sp, auto* cp) {
         using S = std::remove_pointer_t<decltype(sp)>;
         using C = std::remove_pointer_t<decltype(cp)>;
-        moments_kernel<S, C><<<grid_for(ctx, n), kThreads, 0, ctx->stream>>>(
-            phi_out, (const S*)ctx->pop[ctx->cur], ctx->p.nx, ctx->p.ny, ctx->pitch, ctx->plane, (C)ctx->p.phi_ref);
+        moments_kernel<S, C><<<grid_for(ctx, n), kThreads, 0, ctx->stream>>>(phi_out, (const S*)ctx->pop[ctx->cur],
+                                                                             ctx->lp, (C)ctx->p.phi_ref);
     });
 }
 
@@ -326,8 +361,8 @@ cudaError_t launch_reduce(trtr_ctx* ctx, int kind, const double* ref) {
         using S = std::remove_pointer_t<decltype(sp)>;
         using C = std::remove_pointer_t<decltype(cp)>;
         reduce_kernel<S, C><<<ctx->red_blocks, kThreads, 0, ctx->stream>>>(
-            ctx->scratch, (const S*)ctx->pop[ctx->cur], ctx->p.nx, ctx->p.ny, ctx->pitch, ctx->plane,
-            (C)ctx->p.phi_ref, kind, pt, ctx->p.x0, ctx->p.y0, ctx->p.dx, ref);
+            ctx->scratch, (const S*)ctx->pop[ctx->cur], ctx->lp, (C)ctx->p.phi_ref, kind, pt, ctx->p.x0, ctx->p.y0,
+            ctx->p.dx, ref);
         finish_kernel<<<1, kThreads, 0, ctx->stream>>>(ctx->dres, ctx->scratch, ctx->red_blocks);
     });
 }
@@ -338,8 +373,8 @@ cudaError_t launch_get_populations(trtr_ctx* ctx, double* g) {
     return dispatch(ctx, [&](auto* sp, auto* cp) {
         using S = std::remove_pointer_t<decltype(sp)>;
         using C = std::remove_pointer_t<decltype(cp)>;
-        get_pop_kernel<S, C><<<grid_for(ctx, n), kThreads, 0, ctx->stream>>>(
-            g, (const S*)ctx->pop[ctx->cur], ctx->p.nx, ctx->p.ny, ctx->pitch, ctx->plane, (C)ctx->p.phi_ref);
+        get_pop_kernel<S, C><<<grid_for(ctx, n), kThreads, 0, ctx->stream>>>(g, (const S*)ctx->pop[ctx->cur], ctx->lp,
+                                                                             (C)ctx->p.phi_ref);
     });
 }
 
@@ -349,8 +384,8 @@ cudaError_t launch_set_populations(trtr_ctx* ctx, const double* g) {
     return dispatch(ctx, [&](auto* sp, auto* cp) {
         using S = std::remove_pointer_t<decltype(sp)>;
         using C = std::remove_pointer_t<decltype(cp)>;
-        set_pop_kernel<S, C><<<grid_for(ctx, n), kThreads, 0, ctx->stream>>>(
-            (S*)ctx->pop[ctx->cur], g, ctx->p.nx, ctx->p.ny, ctx->pitch, ctx->plane, (C)ctx->p.phi_ref);
+        set_pop_kernel<S, C><<<grid_for(ctx, n), kThreads, 0, ctx->stream>>>((S*)ctx->pop[ctx->cur], g, ctx->lp,
+                                                                             (C)ctx->p.phi_ref);
     });
 }
 
@@ -361,8 +396,7 @@ cudaError_t launch_sample(trtr_ctx* ctx, const long* nodes, int count, double* o
         using S = std::remove_pointer_t<decltype(sp)>;
         using C = std::remove_pointer_t<decltype(cp)>;
         sample_kernel<S, C><<<(total + kThreads - 1) / kThreads, kThreads, 0, ctx->stream>>>(
-            out, nodes, count, (const S*)ctx->pop[ctx->cur], ctx->p.nx, ctx->p.ny, ctx->pitch, ctx->plane,
-            (C)ctx->p.phi_ref);
+            out, nodes, count, (const S*)ctx->pop[ctx->cur], ctx->lp, (C)ctx->p.phi_ref);
     });
 }
 

@@ -1,18 +1,29 @@
 // trtr_internal.cuh -- context layout, storage traits and kernel launchers of the TRT-R
 // library (not part of the public ABI).
 //
-// Device layout (all buffers owned by the context):
-//   populations  2 x [9][ny][pitch]   stored post-collision values P_i(x) of the previous
-//                                     step; the pre-collision population is the pull
-//                                     g_i(x, t_n) = P_i(x - e_i) (periodic)
-//   fields       ux, uy, Dh [ny][pitch] in the compute type, lattice units:
-//                uhat = u dt/dx, Dh = D dt/dx^2  (tau1 = 1/2 + 3 Dh)
-//   source       2 x [ny][pitch] dt*S (TRTR_SRC_FIELD only)
-//   pulse tab    sin(pi x_i), cos(pi x_i) [pitch] and sin(pi y_j), cos(pi y_j) [ny]
+// Device layout (all buffers owned by the context).  Every plane is "ghosted": the interior
+// node (i, j) sits at row j + 1 and column gx + i of a [rows][pitch] plane, where gx is one
+// 128-byte line of columns, so interior rows start on a 128-byte boundary and the column
+// before / after the interior and the row above / below it hold ghost copies:
+//
+//   populations  2 x [9][rows][pitch] in the storage type: the post-collision values P_i(x)
+//                of the previous step; the pre-collision population is the pull
+//                g_i(x, t_n) = P_i(x - e_i).  The ghost cells repeat the opposite edge
+//                (periodic), so the pull never wraps and TMA tiles never need to.
+//   fields       uv = [2][rows][pitch] (uhat_x, uhat_y) and Dh = [rows][pitch] in the compute
+//                type, lattice units: uhat = u dt/dx, Dh = D dt/dx^2 (tau1 = 1/2 + 3 Dh).  The
+//                u ghosts hold the periodic wrap (TRTR_GRAD_PERIODIC) or the linear
+//                extrapolation 2u(edge) - u(edge -+ 1) (TRTR_GRAD_ONESIDED_EDGE), for which the
+//                central difference at the edge node equals the one-sided difference.
+//   source       [2][rows][pitch] dt*S in the compute type (TRTR_SRC_FIELD only)
+//   pulse tab    [2][nx] sin(pi x_i), cos(pi x_i) and [2][ny] sin(pi y_j), cos(pi y_j)
 //   scratch      FP64 partial sums of the reductions, one pair per reduction block
-// pitch = nx rounded up to 32 elements so that every row starts on a 128-byte boundary.
+//   flag         device int set by a kernel whose bounded wait gave up
+// rows >= ny + 2 and pitch >= nx + 2 gx are padded so that every TMA box fits inside the
+// allocation.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -35,6 +46,19 @@ struct PulseTime {
     double amp;       // s0^2 / s^2(t)
 };
 
+struct PlaneLayout {
+    int nx, ny;
+    int gx;        // column of interior x = 0 (128 bytes of columns)
+    int pitch;     // elements per row
+    int rows;      // rows per plane (>= ny + 2)
+    size_t plane;  // rows * pitch
+    __host__ __device__ __forceinline__ size_t at(int i, int j) const {
+        return (size_t)(j + 1) * (size_t)pitch + (size_t)(i + gx);
+    }
+};
+
+PlaneLayout make_layout(int nx, int ny, int elem_bytes);
+
 // Storage traits: how a population is kept in memory and turned into the compute type.
 template <typename S>
 struct Store;
@@ -42,83 +66,73 @@ struct Store;
 template <>
 struct Store<double> {
     using C = double;
-    static __device__ __forceinline__ double load(const double* p, double) { return __ldg(p); }
-    static __device__ __forceinline__ void store(double* p, double v, double) { *p = v; }
+    static __device__ __forceinline__ double decode(double v, double) { return v; }
+    static __device__ __forceinline__ double encode(double v, double) { return v; }
 };
 
 template <>
 struct Store<float> {
     using C = float;
-    static __device__ __forceinline__ float load(const float* p, float) { return __ldg(p); }
-    static __device__ __forceinline__ void store(float* p, float v, float) { *p = v; }
+    static __device__ __forceinline__ float decode(float v, float) { return v; }
+    static __device__ __forceinline__ float encode(float v, float) { return v; }
 };
 
 // Half-precision offset storage: h = g - w_i phi_ref.
 template <>
 struct Store<__half> {
     using C = float;
-    static __device__ __forceinline__ float load(const __half* p, float off) {
-        return __half2float(__ldg(p)) + off;
-    }
-    static __device__ __forceinline__ void store(__half* p, float v, float off) { *p = __float2half_rn(v - off); }
+    static __device__ __forceinline__ float decode(__half v, float off) { return __half2float(v) + off; }
+    static __device__ __forceinline__ __half encode(float v, float off) { return __float2half_rn(v - off); }
 };
 
 template <>
 struct Store<__nv_bfloat16> {
     using C = float;
-    static __device__ __forceinline__ float load(const __nv_bfloat16* p, float off) {
-        return __bfloat162float(__ldg(p)) + off;
-    }
-    static __device__ __forceinline__ void store(__nv_bfloat16* p, float v, float off) {
-        *p = __float2bfloat16_rn(v - off);
-    }
+    static __device__ __forceinline__ float decode(__nv_bfloat16 v, float off) { return __bfloat162float(v) + off; }
+    static __device__ __forceinline__ __nv_bfloat16 encode(float v, float off) { return __float2bfloat16_rn(v - off); }
 };
 
-// Arguments of the fused step kernel (one launch per time step).
+// Uniform arguments of the fused step kernel (one launch per time step).
 template <typename C>
 struct StepArgs {
-    const void* src;        // P of the previous step
-    void* dst;              // P written by this step
-    const C* ux;
-    const C* uy;
-    const C* Dh;
-    const C* S_cur;         // dt * S^n       (TRTR_SRC_FIELD)
-    const C* S_prev;        // dt * S^{n-1}
-    const C* tab_x;         // [2][pitch]: sin(pi x_i), cos(pi x_i)
-    const C* tab_y;         // [2][ny]   : sin(pi y_j), cos(pi y_j)
-    int nx, ny, pitch;
-    size_t plane;           // ny * pitch
-    int grad_mode;
+    void* dst;              // P written by this step (plain stores, with ghosts)
+    const C* tab_x;         // [2][nx]: sin(pi x_i), cos(pi x_i)
+    const C* tab_y;         // [2][ny]: sin(pi y_j), cos(pi y_j)
+    int* flag;              // set when a bounded wait gives up
+    PlaneLayout lp;         // populations
+    PlaneLayout lf;         // fields
+    int s_cur, s_prev;      // source buffer indices (TRTR_SRC_FIELD)
     int tau2_fixed;
     C magic;                // Lambda
     C omega2_fixed;         // 1 / tau2 (TRTR_TAU2_FIXED)
-    C tau1_const_dh;        // unused by the kernel (Dh holds it)
     C phi_ref;
     // pulse source (TRTR_SRC_PULSE), physical units
     C x0, y0, dx, dt;
     C dD_amp;               // D0 * D_amp
     C cx_n, cy_n, inv_s2_n, amp_n;     // at t_n
-    C cx_p, cy_p, inv_s2_p, amp_p;     // at t_{n-1} (== t_n at the first step)
+    C cx_p, cy_p, inv_s2_p, amp_p;     // at t_{n-1}
     int first_step;         // F^{-1} := F^0
 };
+
+enum MapId { kMapPop0 = 0, kMapPop1 = 1, kMapU = 2, kMapD = 3, kMapS = 4, kNumMaps = 5 };
 
 }  // namespace trtr
 
 struct trtr_ctx {
+    CUtensorMap maps[trtr::kNumMaps];  // TMA descriptors (64-byte aligned type)
     trtr_params p;
     cudaStream_t stream;
     int device;
     int num_sms;
     int esize;        // bytes per stored population
     int csize;        // bytes per compute value (fields)
-    int pitch;        // elements per row
-    size_t plane;     // ny * pitch
+    trtr::PlaneLayout lp;  // population planes
+    trtr::PlaneLayout lf;  // field planes
     void* pop[2];
     int cur;          // index of the buffer holding P for the current step
-    void* ux;
-    void* uy;
+    void* uv;         // [2][rows][pitch] uhat_x, uhat_y
     void* Dh;
-    void* S[2];       // TRTR_SRC_FIELD buffers (dt * S)
+    void* S;          // [2][rows][pitch] (TRTR_SRC_FIELD)
     int S_cur;        // buffer holding S^n (-1: none set)
     int S_prev;       // buffer holding S^{n-1} (-1: use S^n)
     void* tab_x;
@@ -127,9 +141,10 @@ struct trtr_ctx {
     int red_blocks;
     double* dres;     // device result of the reductions (4 doubles)
     double* hres;     // pinned host copy
+    int* dflag;       // device timeout flag
     double* dtmp;     // device staging for double I/O
     size_t dtmp_len;  // in doubles
-    bool fields_set, pulse_set, initialized;
+    bool fields_set, pulse_set, initialized, maps_ready;
     trtr::Pulse pulse;
     long step;
     long launches;
@@ -140,10 +155,11 @@ namespace trtr {
 
 // Launchers (defined in trtr_step.cu and trtr_aux.cu).  All enqueue on ctx->stream and
 // return the cudaGetLastError() of the launch.
+cudaError_t encode_maps(trtr_ctx* ctx);
 cudaError_t launch_step(trtr_ctx* ctx);
 cudaError_t launch_convert_fields(trtr_ctx* ctx, const double* ux, const double* uy, const double* D);
 cudaError_t launch_pulse_fields(trtr_ctx* ctx);
-cudaError_t launch_convert_source(trtr_ctx* ctx, const double* S, void* dst);
+cudaError_t launch_convert_source(trtr_ctx* ctx, const double* S, int buffer);
 cudaError_t launch_init_equilibrium(trtr_ctx* ctx, const double* phi0 /* device or NULL = pulse */);
 cudaError_t launch_moments(trtr_ctx* ctx, double* phi_out_dev);
 cudaError_t launch_reduce(trtr_ctx* ctx, int kind, const double* phi_ref_dev);
@@ -154,5 +170,27 @@ cudaError_t launch_sample(trtr_ctx* ctx, const long* nodes_dev, int count, doubl
 enum ReduceKind { kReduceMass = 0, kReducePulse = 1, kReduceField = 2, kReduceNonFinite = 3 };
 
 PulseTime pulse_at(const Pulse& p, double t);
+
+// D2Q9 in the library's order: 0:(0,0) 1:(1,0) 2:(-1,0) 3:(0,1) 4:(0,-1) 5:(1,1) 6:(-1,-1)
+// 7:(1,-1) 8:(-1,1).
+__host__ __device__ constexpr int lattice_ex(int q) { return q == 1 || q == 5 || q == 7 ? 1 : (q == 2 || q == 6 || q == 8 ? -1 : 0); }
+__host__ __device__ constexpr int lattice_ey(int q) { return q == 3 || q == 5 || q == 8 ? 1 : (q == 4 || q == 6 || q == 7 ? -1 : 0); }
+
+// Stores one population value at interior node (i, j) and at every ghost cell that repeats
+// it (the periodic images just outside the interior).
+template <typename T>
+__device__ __forceinline__ void store_with_ghosts(T* plane, const PlaneLayout& L, int i, int j, T v) {
+    plane[L.at(i, j)] = v;
+    const bool xl = i == 0, xr = i == L.nx - 1, yl = j == 0, yr = j == L.ny - 1;
+    if (!(xl || xr || yl || yr)) return;
+    if (xl) plane[L.at(L.nx, j)] = v;
+    if (xr) plane[L.at(-1, j)] = v;
+    if (yl) plane[L.at(i, L.ny)] = v;
+    if (yr) plane[L.at(i, -1)] = v;
+    if (xl && yl) plane[L.at(L.nx, L.ny)] = v;
+    if (xl && yr) plane[L.at(L.nx, -1)] = v;
+    if (xr && yl) plane[L.at(-1, L.ny)] = v;
+    if (xr && yr) plane[L.at(-1, -1)] = v;
+}
 
 }  // namespace trtr
