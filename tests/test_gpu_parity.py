@@ -308,3 +308,44 @@ def test_call_order_and_argument_errors():
         with pytest.raises(T.TrtrError) as e:
             s.set_fields(case["ux"], case["uy"], bad)
         assert e.value.status == T.TRTR_EINVAL
+
+
+# ------------------------------------------------------ half-precision storage, many steps
+
+
+def _half_tol(prec: str, steps: int) -> float:
+    """Each step rounds every stored population to the half format (unit roundoff 2^-11 for
+    FP16, 2^-8 for BF16, relative to |g - w phi_ref|); independent roundings accumulate like
+    sqrt(n), so the relative L2 error of phi after n steps stays below u * sqrt(n)."""
+    u = 2.0**-11 if prec == "f16" else 2.0**-8
+    return u * math.sqrt(steps)
+
+
+@pytest.mark.parametrize("prec", ["f16", "bf16"])
+def test_half_offset_storage_multistep_against_oracle(prec):
+    """200^2 pulse with the 1024^2 relaxation times, 1000 steps, phi_ref = 0."""
+    base = W.Pulse(n=200, courant=0.8)
+    D0 = 0.2766 / 3.0 * base.dx**2 / base.dt
+    pulse = W.Pulse(n=200, D_amp=0.5, D0=D0, courant=0.8, steps=1000)
+    o = oracle_for_pulse(pulse)
+    with T.pulse_solver(pulse, precision=PREC[prec]) as s:
+        s.step(pulse.steps)
+        o.step(pulse.steps)
+        err = rel_l2(s.moments(), o.phi())
+    assert err <= _half_tol(prec, pulse.steps), err
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", ["f32", "f16", "bf16"])
+def test_precision_1024_against_oracle(prec):
+    """The 1024^2 workload (variable D, manufactured source, Courant 0.8, magic tau2) for 300
+    steps: each storage precision against the FP64 oracle at the same size."""
+    pulse = W.C2A_F32_1024
+    steps = 300
+    o = oracle_for_pulse(pulse)
+    with T.pulse_solver(pulse, precision=PREC[prec]) as s:
+        s.step(steps)
+        o.step(steps)
+        err = rel_l2(s.moments(), o.phi())
+    tol = TOL_F32 if prec == "f32" else _half_tol(prec, steps)
+    assert err <= tol, err
