@@ -42,6 +42,8 @@ WORKLOADS = {
     "pulse4096_f16_varD_mms": (W.C2B_F32_4096, "f16", 2),
 }
 DEFAULT_WORKLOAD = "pulse4096_f32_varD_mms"
+# batched workloads: 256 seeded pulses, square grids drawn from {64 ... 1024}, one launch per step
+BATCH_WORKLOADS = {"batch256_f32": ("f32", 4), "batch256_f16": ("f16", 2)}
 STEP_SOURCES = ["paper_2312_10316_gb300/csrc/trtr_step.cu", "paper_2312_10316_gb300/csrc/trtr_internal.cuh"]
 
 
@@ -50,7 +52,9 @@ def parse_args():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10000)
     ap.add_argument("--warmup", type=int, default=50)
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS))
+    ap.add_argument("--baseline-steps", type=int, default=50,
+                    help="steps of the per-instance-launch comparison (batched workloads)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample length")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -374,7 +378,11 @@ def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return None
-    pulse, prec_key, pop_bytes = WORKLOADS[args.workload]
+    if args.workload in BATCH_WORKLOADS:  # sample the batch's largest instance
+        prec_key = BATCH_WORKLOADS[args.workload][0]
+        pulse = max((bi.pulse for bi in W.batch_instances(seed=0, count=256)), key=lambda p: p.nx * p.ny)
+    else:
+        pulse, prec_key, pop_bytes = WORKLOADS[args.workload]
     budget = 150.0  # seconds for the whole --warmup W --steps K run
     sim, rate, threads = oracle_sample(pulse, 0.0)
     per_step = budget / max(1, args.steps + args.warmup)
@@ -402,9 +410,111 @@ def run_reference(args):
     }
 
 
+def run_batch(args):
+    """256 uneven pulse instances advanced by one persistent launch per step (CUDA-graph
+    replays), autotuned; compared with one launch per instance per step."""
+    import torch
+
+    from paper_2312_10316_gb300 import trtr as T
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    prec_key, pop_bytes = BATCH_WORKLOADS[args.workload]
+    prec = T.PRECISIONS[prec_key]
+    pulses = [bi.pulse for bi in W.batch_instances(seed=0, count=256)]
+    nodes = sum(p.nx * p.ny for p in pulses)
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+
+    batch = T.Batch([T.pulse_instance(p, prec) for p in pulses], sh)
+    t0 = time.perf_counter()
+    best, tune_ms = batch.tune(10)
+    tune_s = time.perf_counter() - t0
+    batch.step(args.warmup)
+    batch.sync()
+    barrier(world)
+    props = torch.cuda.get_device_properties(local)
+    uuid = str(getattr(props, "uuid", "")) or None
+    clocks = ClockSampler(("GPU-" + uuid) if uuid and not uuid.startswith("GPU-") else uuid)
+    clocks.start()
+    time.sleep(0.4)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    batch.step(args.steps)
+    e1.record(stream)
+    stream.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    batch.sync()
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    value = nodes * args.steps * world / (ms * 1e-3) / 1e9
+    step_ms = ms / args.steps
+    solves_per_s = len(pulses) * world * args.steps / pulses[0].steps / (ms * 1e-3)
+    batch.close()
+
+    # one launch per instance per step, same instances, same stream
+    solvers = [T.pulse_solver(p, precision=prec, stream=sh) for p in pulses]
+    for s_ in solvers:
+        s_.step(2)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.baseline_steps):
+        for s_ in solvers:
+            T.trtr_step(s_.ctx, 1)
+    e1.record(stream)
+    stream.synchronize()
+    base_ms = e0.elapsed_time(e1)
+    for s_ in solvers:
+        s_.close()
+    base_value = nodes * args.baseline_steps / (base_ms * 1e-3) / 1e9
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+        return None
+    bpn = algorithmic_bytes_per_node(pop_bytes)
+    peak, peak_kind = measured_hbm_peak()
+    achieved = bpn * nodes / (step_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(step_ms, 5), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": prec_key, "data": "synthetic",
+        "config": {"workload": args.workload, "instances": len(pulses), "nodes": nodes,
+                   "sizes": "square, drawn from {64,128,256,512,1024}, seed 0", "courant": pulses[0].courant,
+                   "launch": T.trtr_batch_config_name(best), "parallelism": f"replicas{world}",
+                   "l2_flush": f"inputs larger than L2: {2 * 9 * pop_bytes * nodes / 1e9:.2f} GB of populations"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": f"{peak_kind} copy bandwidth",
+                     "bytes_per_node": bpn, "kernel": "batch_kernel"},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+        "batch": {"solves_per_s": round(solves_per_s, 3), "steps_per_solve": pulses[0].steps,
+                  "per_instance_launch_glups": round(base_value, 3),
+                  "speedup_vs_per_instance_launches": round(value / world / base_value, 3),
+                  "tuned_config": T.trtr_batch_config_name(best), "tune_seconds": round(tune_s, 2),
+                  "tune_ms_per_step": {T.trtr_batch_config_name(c): round(m, 4) for c, m in enumerate(tune_ms)}},
+    }
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return line
+
+
 def main():
     args = parse_args()
-    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if args.impl == "reference":
+        line = run_reference(args)
+    elif args.workload in BATCH_WORKLOADS:
+        line = run_batch(args)
+    else:
+        line = run_ours(args)
     if line is not None:
         print(json.dumps(line), flush=True)
 

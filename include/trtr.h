@@ -175,6 +175,57 @@ trtr_status trtr_sync(trtr_ctx* ctx);
 /* Number of kernels the library enqueued on this context since creation (launch count). */
 trtr_status trtr_launch_count(const trtr_ctx* ctx, long* launches);
 
+/* ---- Batched instances ----------------------------------------------------------------
+ * Many independent problems of uneven sizes advanced together, each by the same step of
+ * Eq. (14).  The paper solves one problem at a time; this is a throughput mode of its step.
+ * One persistent kernel launch per time step walks a work-list of (instance, tile) pairs
+ * spanning every instance; trtr_batch_step replays a two-step CUDA graph of those launches.
+ * Each instance is an ordinary context (trtr_batch_instance gives it out for queries). */
+typedef struct {
+    trtr_params p;  /* the instance's lattice and options.  precision: the same for every
+                       instance, TRTR_F32, TRTR_F16_OFS or TRTR_BF16_OFS; src_mode: NONE or
+                       PULSE (the manufactured source of its pulse)                        */
+    double omega, xc, yc, sigma0, D0, D_amp; /* its pulse, as for trtr_set_pulse          */
+} trtr_instance;
+
+typedef struct trtr_batch trtr_batch; /* opaque, library-owned */
+
+/* Creates one context per instance on cuda_stream (NULL: the batch creates its own stream;
+ * graphs cannot be captured on the legacy default stream), fills each with its pulse's
+ * fields and initial condition g = g^eq(phi_a(x, 0), u), and builds the work-list of the
+ * default configuration.  On error nothing is left allocated. */
+trtr_status trtr_batch_create(const trtr_instance* inst, int count, void* cuda_stream, trtr_batch** out);
+
+/* Frees the batch and its instance contexts.  NULL is accepted. */
+trtr_status trtr_batch_destroy(trtr_batch* b);
+
+/* Number of launch configurations (tile shape x CTA-to-tile schedule) and their names. */
+int trtr_batch_config_count(void);
+const char* trtr_batch_config_name(int config);
+
+/* Autotuner: times every configuration over trial_steps (>= 2) steps with CUDA events and
+ * keeps the fastest; *config_out (may be NULL) receives it and ms_out (may be NULL, else
+ * trtr_batch_config_count() floats) the milliseconds per step of each.  A batch tuned at
+ * step 0 is reset to its initial condition afterwards; otherwise the trial steps advance
+ * every instance.  Synchronises. */
+trtr_status trtr_batch_tune(trtr_batch* b, int trial_steps, int* config_out, float* ms_out);
+
+/* Selects a configuration explicitly. */
+trtr_status trtr_batch_set_config(trtr_batch* b, int config);
+
+/* Advances every instance by n >= 0 steps (asynchronous on the batch's stream).  Instances
+ * must not be stepped through their own contexts in between (TRTR_ESTATE). */
+trtr_status trtr_batch_step(trtr_batch* b, long n);
+
+/* Waits for the batch's stream; TRTR_ETIMEOUT if a step kernel gave up a bounded wait. */
+trtr_status trtr_batch_sync(trtr_batch* b);
+
+/* The context of instance k (owned by the batch): moments, mass, error, populations. */
+trtr_status trtr_batch_instance(trtr_batch* b, int k, trtr_ctx** ctx);
+
+/* Instance count, total nodes, step counter and current configuration (any may be NULL). */
+trtr_status trtr_batch_info(const trtr_batch* b, int* count, long long* nodes, long* step, int* config);
+
 /* Largest grid height (rows) that trtr_phi_sums_noalloc accepts. */
 #define TRTR_NOALLOC_MAX_ROWS 16384
 

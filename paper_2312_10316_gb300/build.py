@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtrtr.so")
 
-SOURCES = ["trtr_api.cu", "trtr_step.cu", "trtr_aux.cu", "trtr_noalloc.cu"]
+SOURCES = ["trtr_api.cu", "trtr_step.cu", "trtr_aux.cu", "trtr_noalloc.cu", "trtr_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
                      "-I", INCLUDE, "-I", CSRC]
@@ -64,11 +64,11 @@ def build_library(force: bool = False, verbose: bool = False, extra_flags: list[
         procs.append((s, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
     errors = []
     for s, p in procs:
-        out, _ = p.communicate()
-        if verbose and out:
-            sys.stderr.write(out.decode(errors="replace"))
+        log, _ = p.communicate()
+        if verbose and log:
+            sys.stderr.write(log.decode(errors="replace"))
         if p.returncode != 0:
-            errors.append(f"{s}:\n{out.decode(errors='replace')}")
+            errors.append(f"{s}:\n{log.decode(errors='replace')}")
     if errors:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
     target = out or LIB

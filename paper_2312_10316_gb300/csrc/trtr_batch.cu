@@ -1,0 +1,642 @@
+// trtr_batch.cu -- many independent pulse problems of uneven sizes advanced together.
+//
+// Every instance is an ordinary context (its own ghosted planes, fields and reductions).
+// One persistent kernel launch per time step walks a work-list of (instance, tile) pairs
+// spanning all instances; per tile the producer thread issues the instance's TMA loads,
+// then copies the instance's step arguments from a device descriptor into a shared-memory
+// slot of the stage and gives the stage's mbarrier its second arrival, so the consumers
+// read the arguments after their acquire-wait.  The arithmetic per node is the single-grid
+// step's (Eq. (14)); only the work distribution differs.
+//
+// Time-dependent uniforms (the pulse source at t_n and t_{n-1}) live in a device table
+// that the last CTA to finish a step advances, together with a device step clock, so a
+// two-step CUDA graph of the launches can be replayed with no host involvement.
+//
+// The autotuner (trtr_batch_tune) times every tile shape x schedule and keeps the fastest.
+#include <math.h>
+#include <stddef.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "trtr_step_core.cuh"
+
+namespace trtr {
+namespace {
+
+using namespace core;
+
+struct BatchClock {
+    long long n;
+    unsigned int done;
+    unsigned int pad;
+};
+
+template <typename C>
+struct alignas(64) InstanceDesc {
+    CUtensorMap mp[2];    // populations, source buffer 0 / 1
+    CUtensorMap mu;       // uhat_x, uhat_y
+    CUtensorMap md;       // Dh
+    StepArgs<C> base[2];  // step arguments by source-buffer parity (dst differs); time part unused
+    Pulse pulse;
+    double dt;
+};
+static_assert(sizeof(StepArgs<float>) % 16 == 0 && sizeof(TimeFields<float>) % 16 == 0, "16-byte chunks");
+static_assert(offsetof(InstanceDesc<float>, base) % 16 == 0, "16-byte aligned arguments");
+
+struct Geometry {
+    int bx, by;
+};
+constexpr Geometry kGeoms[] = {{128, 8}, {64, 8}, {128, 4}};
+constexpr int kNumGeoms = 3;
+constexpr int kNumSchedules = 3;  // 0 interleaved, 1 chunked, 2 chunked with the largest instances first
+constexpr int kNumConfigs = kNumGeoms * kNumSchedules;
+constexpr int kDefaultConfig = 1;  // 128 x 8 tiles, chunked
+
+// Pulse source uniforms of step n (t_n = n dt and t_{n-1}), in double, stored as float.
+__host__ __device__ inline TimeFields<float> time_fields(const Pulse& p, double dt, long long n) {
+    TimeFields<float> u;
+    const double tn = (double)n * dt, tp = (double)(n - 1) * dt;
+    const double cn = cos(p.omega * tn), sn = sin(p.omega * tn);
+    const double cp = cos(p.omega * tp), sp = sin(p.omega * tp);
+    const double s2n = p.sigma0 * p.sigma0 + 2.0 * p.D0 * tn, s2p = p.sigma0 * p.sigma0 + 2.0 * p.D0 * tp;
+    u.cx_n = (float)(p.xc * cn - p.yc * sn);
+    u.cy_n = (float)(p.xc * sn + p.yc * cn);
+    u.inv_s2_n = (float)(1.0 / s2n);
+    u.amp_n = (float)(p.sigma0 * p.sigma0 / s2n);
+    u.cx_p = (float)(p.xc * cp - p.yc * sp);
+    u.cy_p = (float)(p.xc * sp + p.yc * cp);
+    u.inv_s2_p = (float)(1.0 / s2p);
+    u.amp_p = (float)(p.sigma0 * p.sigma0 / s2p);
+    u.first_step = n == 0;
+    return u;
+}
+
+// Asynchronous copy of `bytes` (a multiple of 16) from global to shared memory.
+__device__ __forceinline__ void cp_async_16(void* sdst, const void* gsrc, int bytes) {
+    for (int o = 0; o < bytes; o += 16)
+        asm volatile(
+            "{\n\t.reg .u64 g;\n\tcvta.to.global.u64 g, %1;\n\t"
+            "cp.async.cg.shared.global [%0], [g], 16;\n\t}" ::"r"(smem_addr(static_cast<char*>(sdst) + o)),
+            "l"(static_cast<const char*>(gsrc) + o)
+            : "memory");
+}
+
+template <int BY>
+constexpr int min_blocks() {
+    return BY == 8 ? 2 : 4;  // keeps the register budget at 128 per thread
+}
+
+template <typename S, int SRC, int BX, int BY, int STAGES>
+__global__ void __launch_bounds__(32 * BY, min_blocks<BY>())
+    batch_kernel(const InstanceDesc<typename Store<S>::C>* __restrict__ desc, const int4* __restrict__ tiles,
+                 int ntiles, TimeFields<float>* tu, BatchClock* clk, int count, int parity, int interleaved) {
+    using C = typename Store<S>::C;
+    using T = Tile<S, SRC, BX, BY>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(16) StepArgs<C> sargs[STAGES];
+    __shared__ int s_abort, s_last;
+    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) &
+                                                           ~static_cast<uintptr_t>(127));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * T::STAGE);
+    const int tid = threadIdx.x, lane = tid & 31, r = tid >> 5;
+
+    const int chunk = (ntiles + gridDim.x - 1) / gridDim.x;
+    const int first = interleaved ? blockIdx.x : blockIdx.x * chunk;
+    const int stride = interleaved ? gridDim.x : 1;
+    const int my_tiles = interleaved ? (first < ntiles ? (ntiles - 1 - first) / stride + 1 : 0)
+                                     : (first < ntiles ? min(chunk, ntiles - first) : 0);
+
+    // A stage's barrier completes after two arrivals and the TMA bytes: the producer's
+    // arrival with the byte count goes out right before the tile loads; the second arrives
+    // when its asynchronous copies of the instance's arguments into the stage's shared slot
+    // land (cp.async.mbarrier.arrive), so the producer never waits on global memory.
+    auto issue = [&](int k, int s) {
+        const int4 t = tiles[first + k * stride];  // (instance, i0, j0, gx_p | gx_f << 16)
+        const InstanceDesc<C>* d = desc + t.x;
+        const int gxp = t.w & 0xffff, gxf = t.w >> 16;
+        unsigned char* stage = smem + s * T::STAGE;
+        uint64_t* bar = &full[s];
+        mbar_expect_tx(bar, T::TX);
+#pragma unroll
+        for (int q = 0; q < kQ; ++q)
+            tma_load_3d(stage + q * T::POP_PLANE, &d->mp[parity], bar, t.y + gxp - (lattice_ex(q) == 1 ? T::A : 0),
+                        t.z + 1 - lattice_ey(q), q);
+        tma_load_3d(stage + T::POP, &d->mu, bar, t.y + gxf - T::AC, t.z, 0);
+        tma_load_2d(stage + T::POP + T::U, &d->md, bar, t.y + gxf, t.z + 1);
+        constexpr int kStatic = (int)(sizeof(StepArgs<C>) - sizeof(TimeFields<C>));
+        cp_async_16(&sargs[s], &d->base[parity], kStatic);
+        if (SRC == TRTR_SRC_PULSE) cp_async_16(&sargs[s].tf, &tu[t.x], (int)sizeof(TimeFields<C>));
+        asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+    };
+
+    if (tid == 0) {
+        s_abort = 0;
+        for (int s = 0; s < STAGES; ++s) mbar_init(&full[s], 2);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int k = 0; k < STAGES && k < my_tiles; ++k) issue(k, k);
+
+    for (int k = 0; k < my_tiles; ++k) {
+        const int s = k % STAGES;
+        const int4 t = tiles[first + k * stride];
+        const int i0 = t.y, j0 = t.z, j = j0 + r;
+
+        F2 sx[BX / 64 > 0 ? BX / 64 : 1], cx[BX / 64 > 0 ? BX / 64 : 1];
+        float sy = 0.f, cy = 0.f;
+        if (SRC == TRTR_SRC_PULSE) {  // per-column tables, fetched before the wait
+            const StepArgs<C>& g = desc[t.x].base[0];
+            const int nx = g.lp.nx, ny = g.lp.ny;
+            const float* tx = reinterpret_cast<const float*>(g.tab_x);
+#pragma unroll
+            for (int m = 0; m < BX / 64; ++m) {
+                const int i = i0 + 64 * m + 2 * lane;
+                const float s0 = i < nx ? __ldg(tx + i) : 0.f, s1 = i + 1 < nx ? __ldg(tx + i + 1) : 0.f;
+                const float c0 = i < nx ? __ldg(tx + nx + i) : 0.f, c1 = i + 1 < nx ? __ldg(tx + nx + i + 1) : 0.f;
+                sx[m] = F2(s0, s1);
+                cx[m] = F2(c0, c1);
+            }
+            if (j < ny) {
+                const float* ty = reinterpret_cast<const float*>(g.tab_y);
+                sy = __ldg(ty + j);
+                cy = __ldg(ty + ny + j);
+            }
+        }
+
+        const bool ok = mbar_wait_bounded(&full[s], (k / STAGES) & 1);
+        if (!ok) s_abort = 1;
+        if (ok && j < sargs[s].lp.ny)
+            tile_row_pairs<S, SRC, BX, BY>(smem + s * T::STAGE, r, lane, i0, j, sargs[s], sx, cx, sy, cy);
+        __syncthreads();
+        if (s_abort) {
+            if (tid == 0) {
+                atomicExch(desc[t.x].base[0].flag, 1);
+                for (int kk = k + 1; kk < my_tiles && kk < k + STAGES; ++kk)
+                    mbar_wait_bounded(&full[kk % STAGES], (kk / STAGES) & 1);
+            }
+            return;
+        }
+        if (tid == 0 && k + STAGES < my_tiles) issue(k + STAGES, s);
+    }
+
+    // The last CTA to finish advances the step clock and every instance's time uniforms.
+    if (tid == 0) {
+        __threadfence();
+        s_last = atomicAdd(&clk->done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        const long long n1 = clk->n + 1;
+        if (SRC == TRTR_SRC_PULSE)
+            for (int k = tid; k < count; k += blockDim.x) tu[k] = time_fields(desc[k].pulse, desc[k].dt, n1);
+        __syncthreads();
+        if (tid == 0) {
+            clk->n = n1;
+            clk->done = 0;
+            __threadfence();
+        }
+    }
+}
+
+}  // namespace
+}  // namespace trtr
+
+using trtr::BatchClock;
+using TimeUniforms = trtr::TimeFields<float>;
+
+struct trtr_batch {
+    int count;
+    trtr_ctx** ctx;
+    cudaStream_t stream;
+    bool own_stream;
+    int precision;
+    int src;
+    void* d_desc;
+    int4* d_tiles;
+    int ntiles;
+    TimeUniforms* d_tu;  // per-instance pulse uniforms of the current step
+    BatchClock* d_clk;
+    int* d_flag;
+    int* h_flag;
+    int config;
+    int grid;
+    cudaGraphExec_t graph;
+    bool graph_valid;
+    long step;
+    int parity;
+    long long nodes;
+    std::vector<trtr::Pulse> pulses;
+};
+
+namespace trtr {
+namespace {
+
+template <typename S, int SRC, int BX, int BY>
+struct BatchLaunch {
+    using C = typename Store<S>::C;
+    using T = Tile<S, SRC, BX, BY>;
+    static constexpr int kStages = 2 * T::STAGE + 256 <= 227 * 1024 ? 2 : 1;
+    static size_t smem() { return (size_t)kStages * T::STAGE + 128 + kStages * sizeof(uint64_t); }
+    static cudaError_t configure(int device, int num_sms, int* grid_cap) {
+        auto kernel = batch_kernel<S, SRC, BX, BY, kStages>;
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem());
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32 * BY, smem());
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        *grid_cap = num_sms * per_sm;
+        (void)device;
+        return cudaSuccess;
+    }
+    static cudaError_t launch(trtr_batch* b, int parity, int interleaved) {
+        auto kernel = batch_kernel<S, SRC, BX, BY, kStages>;
+        kernel<<<b->grid, 32 * BY, smem(), b->stream>>>(static_cast<const InstanceDesc<C>*>(b->d_desc), b->d_tiles,
+                                                         b->ntiles, b->d_tu, b->d_clk, b->count, parity, interleaved);
+        return cudaGetLastError();
+    }
+    static bool encode_desc(trtr_batch* b, InstanceDesc<C>* h) {
+        for (int k = 0; k < b->count; ++k) {
+            const trtr_ctx* c = b->ctx[k];
+            InstanceDesc<C>& d = h[k];
+            bool ok = true;
+            for (int p = 0; p < 2; ++p)
+                ok = ok && encode(&d.mp[p], tma_type<S>(), sizeof(S), c->pop[p], c->lp, kQ, T::PW, BY, 1);
+            ok = ok && encode(&d.mu, tma_type<C>(), sizeof(C), c->uv, c->lf, 2, T::UW, T::UH, 2);
+            ok = ok && encode(&d.md, tma_type<C>(), sizeof(C), c->Dh, c->lf, 1, BX, BY, 1);
+            if (!ok) return false;
+            StepArgs<C>& a = d.base[0];
+            memset(static_cast<void*>(&a), 0, sizeof(a));
+            a.tab_x = static_cast<const C*>(c->tab_x);
+            a.tab_y = static_cast<const C*>(c->tab_y);
+            a.flag = b->d_flag;
+            a.lp = c->lp;
+            a.lf = c->lf;
+            a.tau2_fixed = c->p.tau2_mode == TRTR_TAU2_FIXED;
+            a.magic = C(c->p.magic);
+            a.omega2_fixed = C(c->p.tau2_mode == TRTR_TAU2_FIXED ? 1.0 / c->p.tau2 : 0.0);
+            a.phi_ref = C(c->p.phi_ref);
+            a.x0 = C(c->p.x0);
+            a.y0 = C(c->p.y0);
+            a.dx = C(c->p.dx);
+            a.dt = C(c->p.dt);
+            a.dD_amp = C(c->pulse.D0 * c->pulse.D_amp);
+            d.base[1] = a;
+            d.base[0].dst = c->pop[1];  // source buffer 0 -> write buffer 1
+            d.base[1].dst = c->pop[0];
+            d.pulse = c->pulse;
+            d.dt = c->p.dt;
+        }
+        return true;
+    }
+};
+
+template <typename S, int SRC>
+cudaError_t dispatch_geom(trtr_batch* b, int geom, int what, int parity, int interleaved, bool* enc_ok) {
+    // what: 0 configure, 1 launch, 2 encode descriptors
+    switch (geom) {
+        case 0: {
+            using L = BatchLaunch<S, SRC, 128, 8>;
+            if (what == 0) return L::configure(b->ctx[0]->device, b->ctx[0]->num_sms, &b->grid);
+            if (what == 1) return L::launch(b, parity, interleaved);
+            break;
+        }
+        case 1: {
+            using L = BatchLaunch<S, SRC, 64, 8>;
+            if (what == 0) return L::configure(b->ctx[0]->device, b->ctx[0]->num_sms, &b->grid);
+            if (what == 1) return L::launch(b, parity, interleaved);
+            break;
+        }
+        default: {
+            using L = BatchLaunch<S, SRC, 128, 4>;
+            if (what == 0) return L::configure(b->ctx[0]->device, b->ctx[0]->num_sms, &b->grid);
+            if (what == 1) return L::launch(b, parity, interleaved);
+            break;
+        }
+    }
+    // what == 2: descriptors are built host-side
+    using C = typename Store<S>::C;
+    std::vector<InstanceDesc<C>> h(b->count);
+    bool ok = geom == 0   ? BatchLaunch<S, SRC, 128, 8>::encode_desc(b, h.data())
+              : geom == 1 ? BatchLaunch<S, SRC, 64, 8>::encode_desc(b, h.data())
+                          : BatchLaunch<S, SRC, 128, 4>::encode_desc(b, h.data());
+    *enc_ok = ok;
+    if (!ok) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemcpyAsync(b->d_desc, h.data(), sizeof(InstanceDesc<C>) * b->count, cudaMemcpyHostToDevice,
+                                    b->stream);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(b->stream);  // h goes out of scope
+}
+
+cudaError_t dispatch(trtr_batch* b, int geom, int what, int parity = 0, int interleaved = 0) {
+    bool enc_ok = true;
+    const bool pulse = b->src == TRTR_SRC_PULSE;
+    switch (b->precision) {
+        case TRTR_F32:
+            return pulse ? dispatch_geom<float, TRTR_SRC_PULSE>(b, geom, what, parity, interleaved, &enc_ok)
+                         : dispatch_geom<float, TRTR_SRC_NONE>(b, geom, what, parity, interleaved, &enc_ok);
+        case TRTR_F16_OFS:
+            return pulse ? dispatch_geom<__half, TRTR_SRC_PULSE>(b, geom, what, parity, interleaved, &enc_ok)
+                         : dispatch_geom<__half, TRTR_SRC_NONE>(b, geom, what, parity, interleaved, &enc_ok);
+        case TRTR_BF16_OFS:
+            return pulse ? dispatch_geom<__nv_bfloat16, TRTR_SRC_PULSE>(b, geom, what, parity, interleaved, &enc_ok)
+                         : dispatch_geom<__nv_bfloat16, TRTR_SRC_NONE>(b, geom, what, parity, interleaved, &enc_ok);
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+size_t desc_size(int precision) {
+    return precision == TRTR_F64 ? sizeof(InstanceDesc<double>) : sizeof(InstanceDesc<float>);
+}
+
+// Work-list of (instance, i0, j0) for a tile shape and schedule.
+std::vector<int4> make_tiles(const trtr_batch* b, int geom, int schedule) {
+    const int bx = kGeoms[geom].bx, by = kGeoms[geom].by;
+    std::vector<int> order(b->count);
+    for (int k = 0; k < b->count; ++k) order[k] = k;
+    if (schedule == 2)
+        std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+            return (long long)b->ctx[a]->p.nx * b->ctx[a]->p.ny > (long long)b->ctx[c]->p.nx * b->ctx[c]->p.ny;
+        });
+    std::vector<int4> t;
+    for (int k : order) {
+        const int nx = b->ctx[k]->p.nx, ny = b->ctx[k]->p.ny;
+        const int gx = b->ctx[k]->lp.gx | (b->ctx[k]->lf.gx << 16);
+        for (int j0 = 0; j0 < ny; j0 += by)
+            for (int i0 = 0; i0 < nx; i0 += bx) t.push_back(make_int4(k, i0, j0, gx));
+    }
+    return t;
+}
+
+trtr_status apply_config(trtr_batch* b, int config) {
+    const int geom = config / kNumSchedules, schedule = config % kNumSchedules;
+    if (b->graph_valid) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph_valid = false;
+    }
+    if (dispatch(b, geom, 0) != cudaSuccess) return TRTR_ECUDA;
+    if (dispatch(b, geom, 2) != cudaSuccess) return TRTR_ECUDA;
+    std::vector<int4> t = make_tiles(b, geom, schedule);
+    if (b->d_tiles) {
+        cudaStreamSynchronize(b->stream);
+        cudaFree(b->d_tiles);
+        b->d_tiles = nullptr;
+    }
+    if (cudaMalloc(&b->d_tiles, t.size() * sizeof(int4)) != cudaSuccess) return TRTR_ENOMEM;
+    if (cudaMemcpy(b->d_tiles, t.data(), t.size() * sizeof(int4), cudaMemcpyHostToDevice) != cudaSuccess)
+        return TRTR_ECUDA;
+    b->ntiles = (int)t.size();
+    if (b->grid > b->ntiles) b->grid = b->ntiles;
+    b->config = config;
+    return TRTR_OK;
+}
+
+cudaError_t launch_one(trtr_batch* b, int parity) {
+    const int geom = b->config / kNumSchedules, schedule = b->config % kNumSchedules;
+    return dispatch(b, geom, 1, parity, schedule == 0);
+}
+
+// Two-step graph: parity 0 then parity 1.
+trtr_status build_graph(trtr_batch* b) {
+    if (b->graph_valid) return TRTR_OK;
+    cudaGraph_t g;
+    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return TRTR_ECUDA;
+    cudaError_t e0 = launch_one(b, 0);
+    cudaError_t e1 = launch_one(b, 1);
+    cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    if (e0 != cudaSuccess || e1 != cudaSuccess || e != cudaSuccess) {
+        cudaGetLastError();
+        return TRTR_ECUDA;
+    }
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return TRTR_ECUDA;
+    b->graph_valid = true;
+    return TRTR_OK;
+}
+
+trtr_status reset_clock(trtr_batch* b) {
+    std::vector<TimeUniforms> u(b->count);
+    for (int k = 0; k < b->count; ++k) u[k] = time_fields(b->pulses[k], b->ctx[k]->p.dt, b->step);
+    BatchClock c;
+    c.n = b->step;
+    c.done = 0;
+    c.pad = 0;
+    if (cudaMemcpyAsync(b->d_tu, u.data(), u.size() * sizeof(TimeUniforms), cudaMemcpyHostToDevice, b->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(b->d_clk, &c, sizeof(c), cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return TRTR_ECUDA;
+    return TRTR_OK;
+}
+
+trtr_status advance(trtr_batch* b, long n) {
+    for (int k = 0; k < b->count; ++k)
+        if (b->ctx[k]->step != b->step || b->ctx[k]->cur != b->parity) return TRTR_ESTATE;
+    long left = n;
+    if (left > 0 && b->parity == 1) {  // bring the ping-pong to parity 0 for the graph
+        if (launch_one(b, 1) != cudaSuccess) return TRTR_ECUDA;
+        --left;
+    }
+    if (left >= 2) {
+        trtr_status s = build_graph(b);
+        if (s != TRTR_OK) return s;
+        for (; left >= 2; left -= 2)
+            if (cudaGraphLaunch(b->graph, b->stream) != cudaSuccess) return TRTR_ECUDA;
+    }
+    if (left == 1 && launch_one(b, 0) != cudaSuccess) return TRTR_ECUDA;
+    b->step += n;
+    b->parity = (int)((b->parity + n) & 1);
+    for (int k = 0; k < b->count; ++k) {
+        b->ctx[k]->step = b->step;
+        b->ctx[k]->cur = b->parity;
+        b->ctx[k]->launches += n;
+    }
+    return TRTR_OK;
+}
+
+}  // namespace
+}  // namespace trtr
+
+extern "C" {
+
+trtr_status trtr_batch_create(const trtr_instance* inst, int count, void* cuda_stream, trtr_batch** out) {
+    if (!out) return TRTR_EINVAL;
+    *out = nullptr;
+    if (!inst || count < 1) return TRTR_EINVAL;
+    const int prec = inst[0].p.precision;
+    if (prec != TRTR_F32 && prec != TRTR_F16_OFS && prec != TRTR_BF16_OFS) return TRTR_EINVAL;
+    int src = TRTR_SRC_NONE;
+    for (int k = 0; k < count; ++k) {
+        if (inst[k].p.precision != prec) return TRTR_EINVAL;
+        if (inst[k].p.src_mode == TRTR_SRC_FIELD) return TRTR_EINVAL;
+        if (inst[k].p.src_mode == TRTR_SRC_PULSE) src = TRTR_SRC_PULSE;
+    }
+    trtr_batch* b = new (std::nothrow) trtr_batch();
+    if (!b) return TRTR_ENOMEM;
+    b->count = count;
+    b->precision = prec;
+    b->src = src;
+    b->config = trtr::kDefaultConfig;
+    b->ctx = static_cast<trtr_ctx**>(calloc(count, sizeof(trtr_ctx*)));
+    if (!b->ctx) {
+        delete b;
+        return TRTR_ENOMEM;
+    }
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (!b->stream) {  // graphs cannot be captured on the legacy default stream
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            free(b->ctx);
+            delete b;
+            return TRTR_ECUDA;
+        }
+        b->own_stream = true;
+    }
+    trtr_status s = TRTR_OK;
+    for (int k = 0; k < count && s == TRTR_OK; ++k) {
+        const trtr_instance& in = inst[k];
+        s = trtr_create(&in.p, b->stream, &b->ctx[k]);
+        if (s == TRTR_OK) s = trtr_set_pulse(b->ctx[k], in.omega, in.xc, in.yc, in.sigma0, in.D0, in.D_amp);
+        if (s == TRTR_OK) s = trtr_init_equilibrium(b->ctx[k], nullptr, 0);
+        if (s == TRTR_OK) {
+            b->nodes += (long long)in.p.nx * in.p.ny;
+            b->pulses.push_back(b->ctx[k]->pulse);
+        }
+    }
+    if (s == TRTR_OK &&
+        (cudaMalloc(&b->d_desc, trtr::desc_size(prec) * count) != cudaSuccess ||
+         cudaMalloc(&b->d_tu, sizeof(TimeUniforms) * count) != cudaSuccess ||
+         cudaMalloc(&b->d_clk, sizeof(BatchClock)) != cudaSuccess || cudaMalloc(&b->d_flag, sizeof(int)) != cudaSuccess ||
+         cudaMallocHost(&b->h_flag, sizeof(int)) != cudaSuccess ||
+         cudaMemsetAsync(b->d_flag, 0, sizeof(int), b->stream) != cudaSuccess)) {
+        cudaGetLastError();
+        s = TRTR_ENOMEM;
+    }
+    if (s == TRTR_OK) s = trtr::apply_config(b, b->config);
+    if (s == TRTR_OK) s = trtr::reset_clock(b);
+    if (s != TRTR_OK) {
+        trtr_batch_destroy(b);
+        return s;
+    }
+    *out = b;
+    return TRTR_OK;
+}
+
+trtr_status trtr_batch_destroy(trtr_batch* b) {
+    if (!b) return TRTR_OK;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->graph_valid) cudaGraphExecDestroy(b->graph);
+    for (int k = 0; k < b->count; ++k)
+        if (b->ctx && b->ctx[k]) trtr_destroy(b->ctx[k]);
+    void* ptrs[] = {b->d_desc, b->d_tiles, b->d_tu, b->d_clk, b->d_flag};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (b->h_flag) cudaFreeHost(b->h_flag);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    cudaGetLastError();
+    free(b->ctx);
+    delete b;
+    return TRTR_OK;
+}
+
+int trtr_batch_config_count(void) { return trtr::kNumConfigs; }
+
+const char* trtr_batch_config_name(int config) {
+    static const char* names[trtr::kNumConfigs] = {
+        "tile 128x8, interleaved",  "tile 128x8, chunked", "tile 128x8, chunked largest-first",
+        "tile 64x8, interleaved",   "tile 64x8, chunked",  "tile 64x8, chunked largest-first",
+        "tile 128x4, interleaved",  "tile 128x4, chunked", "tile 128x4, chunked largest-first"};
+    return config >= 0 && config < trtr::kNumConfigs ? names[config] : "invalid";
+}
+
+trtr_status trtr_batch_set_config(trtr_batch* b, int config) {
+    if (!b || config < 0 || config >= trtr::kNumConfigs) return TRTR_EINVAL;
+    return trtr::apply_config(b, config);
+}
+
+trtr_status trtr_batch_step(trtr_batch* b, long n) {
+    if (!b || n < 0) return TRTR_EINVAL;
+    return trtr::advance(b, n);
+}
+
+trtr_status trtr_batch_sync(trtr_batch* b) {
+    if (!b) return TRTR_EINVAL;
+    if (cudaMemcpyAsync(b->h_flag, b->d_flag, sizeof(int), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return TRTR_ECUDA;
+    }
+    return *b->h_flag ? TRTR_ETIMEOUT : TRTR_OK;
+}
+
+trtr_status trtr_batch_tune(trtr_batch* b, int trial_steps, int* config_out, float* ms_out) {
+    if (!b || trial_steps < 2) return TRTR_EINVAL;
+    const bool restart = b->step == 0;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return TRTR_ECUDA;
+    int best = b->config;
+    float best_ms = 1e30f;
+    trtr_status s = TRTR_OK;
+    for (int c = 0; c < trtr::kNumConfigs && s == TRTR_OK; ++c) {
+        s = trtr::apply_config(b, c);
+        if (s != TRTR_OK) break;
+        s = trtr::advance(b, 2);  // warm-up (graph capture, caches)
+        if (s != TRTR_OK) break;
+        cudaEventRecord(e0, b->stream);
+        s = trtr::advance(b, trial_steps - trial_steps % 2);
+        cudaEventRecord(e1, b->stream);
+        if (s != TRTR_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            s = TRTR_ECUDA;
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= (float)(trial_steps - trial_steps % 2);
+        if (ms_out) ms_out[c] = ms;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != TRTR_OK) return s;
+    s = trtr::apply_config(b, best);
+    if (s == TRTR_OK && restart) {  // trials started from the initial condition: restore it
+        for (int k = 0; k < b->count && s == TRTR_OK; ++k) {
+            b->ctx[k]->cur = 0;
+            s = trtr_init_equilibrium(b->ctx[k], nullptr, 0);
+        }
+        b->step = 0;
+        b->parity = 0;
+        if (s == TRTR_OK) s = trtr::reset_clock(b);
+    }
+    if (s == TRTR_OK && config_out) *config_out = best;
+    return s;
+}
+
+trtr_status trtr_batch_instance(trtr_batch* b, int k, trtr_ctx** ctx) {
+    if (!b || !ctx || k < 0 || k >= b->count) return TRTR_EINVAL;
+    *ctx = b->ctx[k];
+    return TRTR_OK;
+}
+
+trtr_status trtr_batch_info(const trtr_batch* b, int* count, long long* nodes, long* step, int* config) {
+    if (!b) return TRTR_EINVAL;
+    if (count) *count = b->count;
+    if (nodes) *nodes = b->nodes;
+    if (step) *step = b->step;
+    if (config) *config = b->config;
+    return TRTR_OK;
+}
+
+}  // extern "C"

@@ -92,9 +92,19 @@ struct Store<__nv_bfloat16> {
     static __device__ __forceinline__ __nv_bfloat16 encode(float v, float off) { return __float2bfloat16_rn(v - off); }
 };
 
-// Uniform arguments of the fused step kernel (one launch per time step).
+// Time-dependent uniforms of the pulse source (centre, 1/s^2, amplitude at t_n and t_{n-1}).
 template <typename C>
-struct StepArgs {
+struct alignas(16) TimeFields {
+    C cx_n, cy_n, inv_s2_n, amp_n;     // at t_n
+    C cx_p, cy_p, inv_s2_p, amp_p;     // at t_{n-1}
+    int first_step;         // F^{-1} := F^0
+};
+
+// Uniform arguments of the fused step kernel (one launch per time step).  The static part
+// precedes tf and is a whole number of 16-byte chunks, so the batched kernel can copy the
+// two parts into shared memory with asynchronous 16-byte copies.
+template <typename C>
+struct alignas(16) StepArgs {
     void* dst;              // P written by this step (plain stores, with ghosts)
     const C* tab_x;         // [2][nx]: sin(pi x_i), cos(pi x_i)
     const C* tab_y;         // [2][ny]: sin(pi y_j), cos(pi y_j)
@@ -109,9 +119,7 @@ struct StepArgs {
     // pulse source (TRTR_SRC_PULSE), physical units
     C x0, y0, dx, dt;
     C dD_amp;               // D0 * D_amp
-    C cx_n, cy_n, inv_s2_n, amp_n;     // at t_n
-    C cx_p, cy_p, inv_s2_p, amp_p;     // at t_{n-1}
-    int first_step;         // F^{-1} := F^0
+    TimeFields<C> tf;       // pulse source uniforms of this step (a separate 16-byte block)
 };
 
 enum MapId { kMapPop0 = 0, kMapPop1 = 1, kMapU = 2, kMapD = 3, kMapS = 4, kNumMaps = 5 };

@@ -1,0 +1,470 @@
+// trtr_step_core.cuh -- device machinery of the fused TRT-R step shared by the single-grid
+// kernel (trtr_step.cu) and the batched kernel (trtr_batch.cu): TMA / mbarrier helpers,
+// packed FP32 pair arithmetic, the moment-space node update of Eq. (14), and the routines
+// that compute one tile row from a shared-memory stage.  Tile geometry is BX x BY nodes
+// (one warp per tile row).  Internal to the library.
+#pragma once
+
+#include <cudaTypedefs.h>
+
+#include <type_traits>
+
+#include "trtr_internal.cuh"
+
+namespace trtr {
+namespace core {
+
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+template <typename S, int SRC, int BX, int BY>
+struct Tile {
+    using C = typename Store<S>::C;
+    static constexpr int A = 16 / (int)sizeof(S);    // TMA x quantum of the populations
+    static constexpr int PW = BX + A;                // population tile width
+    static constexpr int AC = 16 / (int)sizeof(C);   // TMA x quantum of the fields
+    static constexpr int UW = BX + 2 * AC;           // u tile width (halo rounded to AC)
+    static constexpr int UH = BY + 2;
+    static constexpr uint32_t pad128(uint32_t b) { return (b + 127) / 128 * 128; }
+    // shared-memory tiles start on 128-byte boundaries (TMA destinations)
+    static constexpr uint32_t POP_PLANE = pad128(BY * PW * sizeof(S));
+    static constexpr int PLANE_ELEMS = POP_PLANE / sizeof(S);
+    static constexpr uint32_t POP = kQ * POP_PLANE;
+    static constexpr uint32_t U = pad128(2 * UH * UW * sizeof(C));
+    static constexpr uint32_t D = pad128(BY * BX * sizeof(C));
+    static constexpr uint32_t S_TILE = pad128(BY * BX * sizeof(C));
+    static constexpr uint32_t SRCB = SRC == TRTR_SRC_FIELD ? 2 * S_TILE : 0;
+    // bytes the TMA delivers per stage (the boxes, without the padding)
+    static constexpr uint32_t TX = kQ * BY * PW * sizeof(S) + 2 * UH * UW * sizeof(C) + BY * BX * sizeof(C) +
+                                   (SRC == TRTR_SRC_FIELD ? 2 * BY * BX * sizeof(C) : 0);
+    static constexpr uint32_t STAGE = POP + U + D + SRCB;
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Waits for the phase `parity` of `bar` to complete, for at most kWaitCycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], "
+        "[%2];" ::"r"(smem_addr(dst)),
+        "l"(map), "r"(smem_addr(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, "
+        "%5}], [%2];" ::"r"(smem_addr(dst)),
+        "l"(map), "r"(smem_addr(bar)), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+
+// ---- arithmetic types --------------------------------------------------------------------
+// FP32-computing storages work on pairs of adjacent nodes with the packed FP32 instructions
+// of sm_100-family SMs (two lanes of FP32 per FADD2 / FMUL2 / FFMA2); FP64 works per node.
+struct F2 {
+    float2 v;
+    __device__ __forceinline__ F2() {}
+    __device__ __forceinline__ F2(float s) : v(make_float2(s, s)) {}
+    __device__ __forceinline__ F2(float a, float b) : v(make_float2(a, b)) {}
+    __device__ __forceinline__ explicit F2(float2 x) : v(x) {}
+};
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return F2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return F2(__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v)); }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return F2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 vfma(F2 a, F2 b, F2 c) { return F2(__ffma2_rn(a.v, b.v, c.v)); }
+__device__ __forceinline__ double vfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ F2 vdiv(F2 a, F2 b) { return F2(__fdividef(a.v.x, b.v.x), __fdividef(a.v.y, b.v.y)); }
+__device__ __forceinline__ double vdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ F2 vexp(F2 a) { return F2(__expf(a.v.x), __expf(a.v.y)); }
+__device__ __forceinline__ double vexp(double a) { return exp(a); }
+
+template <class V>
+struct ScalarOf;
+template <>
+struct ScalarOf<F2> {
+    using type = float;
+};
+template <>
+struct ScalarOf<double> {
+    using type = double;
+};
+
+// Manufactured pulse source at (x, y) for the time level (cx, cy, inv_s2, amp):
+//   S = phi_a / s^2 [grad D . r - (D - D0)(|r|^2 / s^2 - 2)],  r = x - c(t).
+template <class V>
+__device__ __forceinline__ V pulse_source(V x, V y, V cx, V cy, V inv_s2, V amp, V dD, V dDx, V dDy) {
+    using T = typename ScalarOf<V>::type;
+    const V rx = x - cx, ry = y - cy;
+    const V r2 = vfma(rx, rx, ry * ry);
+    const V e = amp * vexp(r2 * (V(T(-0.5)) * inv_s2));
+    const V br = vfma(dD, vfma(r2, V(T(0)) - inv_s2, V(T(2))), vfma(dDx, rx, dDy * ry));
+    return (e * inv_s2) * br;
+}
+
+// The node update of Eq. (14) in moment space; g: pre-collision populations, out: P_i(x).
+template <class V>
+__device__ __forceinline__ void collide_node(const V g[kQ], V ux, V uy, V ax, V ay, V Dh, V s, V magic, V w2_fixed,
+                                             bool tau2_fixed, V out[kQ]) {
+    using T = typename ScalarOf<V>::type;
+    // relaxation rates: tau1 - 1/2 = 3 Dh (Sec. 2.4); tau2 from Lambda (Eq. (28)) or fixed
+    const V t1m = V(T(3)) * Dh;
+    const V w1 = vdiv(V(T(1)), V(T(0.5)) + t1m);
+    const V w2 = tau2_fixed ? w2_fixed : vdiv(t1m, vfma(V(T(0.5)), t1m, magic));
+    const V k1 = V(T(1)) - w1, k2 = V(T(1)) - w2;
+    const V kh = vfma(V(T(-0.5)), w1, V(T(1)));
+
+    // a2 + a4: moments (pair sums and differences of opposite directions)
+    const V p12 = g[1] + g[2], p34 = g[3] + g[4], p56 = g[5] + g[6], p78 = g[7] + g[8];
+    const V d12 = g[1] - g[2], d34 = g[3] - g[4], d56 = g[5] - g[6], d78 = g[7] - g[8];
+    const V pdiag = p56 + p78;
+    const V phi = (g[0] + p12) + (p34 + pdiag);
+    const V jx = d12 + (d56 + d78);
+    const V jy = d34 + (d56 - d78);
+    const V pxx = p12 + pdiag;
+    const V pyy = p34 + pdiag;
+    const V pxy = p56 - p78;
+
+    // a5 + a6 + a7: post-collision Hermite coefficients
+    const V phux = phi * ux, phuy = phi * uy;
+    const V euxx = phux * ux, euyy = phuy * uy, euxy = phux * uy;
+    const V m0 = phi + s;
+    const V m1x = vfma(kh, vfma(phi, ax, ux * s), vfma(k1, jx - phux, phux));
+    const V m1y = vfma(kh, vfma(phi, ay, uy * s), vfma(k1, jy - phuy, phuy));
+    const V third = phi * V(T(1.0 / 3.0));
+    const V Axx = vfma(k2, (pxx - third) - euxx, euxx);
+    const V Ayy = vfma(k2, (pyy - third) - euyy, euyy);
+    const V Axy = vfma(k2, pxy - euxy, euxy);
+    const V Txxy = euxx * uy, Txyy = euxy * uy;
+
+    // rebuild from even (E) and odd (O) halves of the opposite pairs, weights folded in:
+    //   f_i = w_i [m0 + 3 e.m1 + 4.5 H2:A + 13.5 (H_xxy T_xxy + H_xyy T_xyy)]
+    const V Asum = Axx + Ayy;
+    const V m9 = m0 * V(T(1.0 / 9.0));
+    const V E1 = vfma(V(T(-1.0 / 6.0)), Ayy, vfma(V(T(1.0 / 3.0)), Axx, m9));
+    const V E3 = vfma(V(T(-1.0 / 6.0)), Axx, vfma(V(T(1.0 / 3.0)), Ayy, m9));
+    const V O1 = vfma(V(T(-0.5)), Txyy, m1x * V(T(1.0 / 3.0)));
+    const V O3 = vfma(V(T(-0.5)), Txxy, m1y * V(T(1.0 / 3.0)));
+    const V Ed = vfma(V(T(1.0 / 12.0)), Asum, m0 * V(T(1.0 / 36.0)));
+    const V E5 = vfma(V(T(0.25)), Axy, Ed);
+    const V E7 = vfma(V(T(-0.25)), Axy, Ed);
+    const V O5 = vfma(V(T(0.25)), Txxy + Txyy, (m1x + m1y) * V(T(1.0 / 12.0)));
+    const V O7 = vfma(V(T(0.25)), Txyy - Txxy, (m1x - m1y) * V(T(1.0 / 12.0)));
+    out[0] = vfma(V(T(-2.0 / 3.0)), Asum, m0 * V(T(4.0 / 9.0)));
+    out[1] = E1 + O1;
+    out[2] = E1 - O1;
+    out[3] = E3 + O3;
+    out[4] = E3 - O3;
+    out[5] = E5 + O5;
+    out[6] = E5 - O5;
+    out[7] = E7 + O7;
+    out[8] = E7 - O7;
+}
+
+template <typename C>
+__device__ __forceinline__ C weight(int q) {
+    return q == 0 ? C(4.0 / 9.0) : (q < 5 ? C(1.0 / 9.0) : C(1.0 / 36.0));
+}
+
+// Shared-memory column offset of plane q's tile (see the TMA origin in issue_tile).
+template <int A>
+__device__ __forceinline__ constexpr int plane_offset(int q) {
+    return lattice_ex(q) == 1 ? A - 1 : (lattice_ex(q) == -1 ? 1 : 0);
+}
+
+// Pair (2-element) storage vectors and their conversion to / from packed FP32.
+template <typename S>
+struct Pair;
+template <>
+struct Pair<float> {
+    using type = float2;
+    static __device__ __forceinline__ F2 decode(float2 v, float) { return F2(v); }
+    static __device__ __forceinline__ F2 decode(float a, float b, float) { return F2(a, b); }
+    static __device__ __forceinline__ float2 encode(F2 v, float) { return v.v; }
+};
+template <>
+struct Pair<__half> {
+    using type = __half2;
+    static __device__ __forceinline__ F2 decode(__half2 v, float off) {
+        const float2 f = __half22float2(v);
+        return F2(f.x + off, f.y + off);
+    }
+    static __device__ __forceinline__ F2 decode(__half a, __half b, float off) {
+        return F2(__half2float(a) + off, __half2float(b) + off);
+    }
+    static __device__ __forceinline__ __half2 encode(F2 v, float off) {
+        return __floats2half2_rn(v.v.x - off, v.v.y - off);
+    }
+};
+template <>
+struct Pair<__nv_bfloat16> {
+    using type = __nv_bfloat162;
+    static __device__ __forceinline__ F2 decode(__nv_bfloat162 v, float off) {
+        const float2 f = __bfloat1622float2(v);
+        return F2(f.x + off, f.y + off);
+    }
+    static __device__ __forceinline__ F2 decode(__nv_bfloat16 a, __nv_bfloat16 b, float off) {
+        return F2(__bfloat162float(a) + off, __bfloat162float(b) + off);
+    }
+    static __device__ __forceinline__ __nv_bfloat162 encode(F2 v, float off) {
+        return __floats2bfloat162_rn(v.v.x - off, v.v.y - off);
+    }
+};
+
+template <typename S, int SRC, int BX, int BY>
+__device__ __forceinline__ void issue_tile(unsigned char* stage, uint64_t* bar, const CUtensorMap* mp,
+                                           const CUtensorMap* mu, const CUtensorMap* md, const CUtensorMap* ms,
+                                           int i0, int j0, const StepArgs<typename Store<S>::C>& a) {
+    using T = Tile<S, SRC, BX, BY>;
+    mbar_expect_tx(bar, T::TX);
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+        const int x = i0 + a.lp.gx - (lattice_ex(q) == 1 ? T::A : 0);
+        const int y = j0 + 1 - lattice_ey(q);
+        tma_load_3d(stage + q * T::POP_PLANE, mp, bar, x, y, q);
+    }
+    tma_load_3d(stage + T::POP, mu, bar, i0 + a.lf.gx - T::AC, j0, 0);
+    tma_load_2d(stage + T::POP + T::U, md, bar, i0 + a.lf.gx, j0 + 1);
+    if (SRC == TRTR_SRC_FIELD) {
+        unsigned char* s = stage + T::POP + T::U + T::D;
+        tma_load_3d(s, ms, bar, i0 + a.lf.gx, j0 + 1, a.s_cur);
+        tma_load_3d(s + T::S_TILE, ms, bar, i0 + a.lf.gx, j0 + 1, a.s_prev);
+    }
+}
+
+// One tile row (warp r) of the FP32-computing storages: lane handles the node pairs
+// (i0 + 64 m + 2 lane, + 1), m = 0, 1.
+template <typename S, int SRC, int BX, int BY>
+__device__ __forceinline__ void tile_row_pairs(const unsigned char* st, int r, int lane, int i0, int j,
+                                               const StepArgs<float>& a, const F2* sx, const F2* cx, float sy,
+                                               float cy) {
+    constexpr int NM = BX / 64;  // node pairs per lane
+    using T = Tile<S, SRC, BX, BY>;
+    using P = Pair<S>;
+    using S2 = typename P::type;
+    const int nx = a.lp.nx, ny = a.lp.ny;
+    const S* sp = reinterpret_cast<const S*>(st) + r * T::PW;
+    const float* su = reinterpret_cast<const float*>(st + T::POP) + (r + 1) * T::UW + T::AC;
+    const float* sv = su + T::UH * T::UW;
+    const float* sd = reinterpret_cast<const float*>(st + T::POP + T::U) + r * BX;
+    const float* ss = reinterpret_cast<const float*>(st + T::POP + T::U + T::D) + r * BX;
+    const float phi_ref = a.phi_ref;
+    S* dst = static_cast<S*>(a.dst);
+    const size_t pl = a.lp.plane;
+    const F2 magic(a.magic), w2f(a.omega2_fixed);
+#pragma unroll 1
+    for (int m = 0; m < NM; ++m) {
+        const int c = 64 * m + 2 * lane;  // column of the pair inside the tile
+        const int i = i0 + c;
+        if (i >= nx) break;
+        // a1: pull-streaming from the shifted tiles
+        F2 g[kQ];
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            const S* pq = sp + q * T::PLANE_ELEMS + c + plane_offset<T::A>(q);
+            const float off = weight<float>(q) * phi_ref;
+            if (plane_offset<T::A>(q) % 2 == 0)
+                g[q] = P::decode(*reinterpret_cast<const S2*>(pq), off);
+            else
+                g[q] = P::decode(pq[0], pq[1], off);
+        }
+        // u, its central differences (ghosts make edges one-sided or periodic), D
+        const float2 uc = *reinterpret_cast<const float2*>(su + c);
+        const float2 vc = *reinterpret_cast<const float2*>(sv + c);
+        const F2 ux(uc), uy(vc);
+        const F2 dxux = F2(0.5f) * (F2(uc.y, su[c + 2]) - F2(su[c - 1], uc.x));
+        const F2 dxuy = F2(0.5f) * (F2(vc.y, sv[c + 2]) - F2(sv[c - 1], vc.x));
+        const F2 dyux = F2(0.5f) * (F2(*reinterpret_cast<const float2*>(su + c + T::UW)) -
+                                    F2(*reinterpret_cast<const float2*>(su + c - T::UW)));
+        const F2 dyuy = F2(0.5f) * (F2(*reinterpret_cast<const float2*>(sv + c + T::UW)) -
+                                    F2(*reinterpret_cast<const float2*>(sv + c - T::UW)));
+        const F2 ax = vfma(ux, dxux, uy * dyux);  // (u.grad) u_x
+        const F2 ay = vfma(ux, dxuy, uy * dyuy);  // (u.grad) u_y
+        const F2 Dh(*reinterpret_cast<const float2*>(sd + c));
+
+        // a7: s = dt S^n + dt/2 (S^n - S^{n-1})
+        F2 src(0.f);
+        if (SRC == TRTR_SRC_FIELD) {
+            const F2 sn(*reinterpret_cast<const float2*>(ss + c));
+            const F2 sp_(*reinterpret_cast<const float2*>(ss + T::S_TILE / sizeof(float) + c));
+            src = vfma(F2(1.5f), sn, F2(-0.5f) * sp_);
+        } else if (SRC == TRTR_SRC_PULSE) {
+            const F2 x = vfma(F2((float)i, (float)(i + 1)), F2(a.dx), F2(a.x0));
+            const F2 y(a.y0 + (float)j * a.dx);
+            F2 sxm = sx[0], cxm = cx[0];  // compile-time indices only (no local-memory arrays)
+#pragma unroll
+            for (int mm = 1; mm < NM; ++mm)
+                if (m == mm) {
+                    sxm = sx[mm];
+                    cxm = cx[mm];
+                }
+            const F2 dD = F2(a.dD_amp * sy) * sxm;
+            const F2 dDx = F2(a.dD_amp * 3.14159265358979323846f * sy) * cxm;
+            const F2 dDy = F2(a.dD_amp * 3.14159265358979323846f * cy) * sxm;
+            const F2 Sn = pulse_source(x, y, F2(a.tf.cx_n), F2(a.tf.cy_n), F2(a.tf.inv_s2_n), F2(a.tf.amp_n), dD, dDx, dDy);
+            const F2 Sp = a.tf.first_step
+                              ? Sn
+                              : pulse_source(x, y, F2(a.tf.cx_p), F2(a.tf.cy_p), F2(a.tf.inv_s2_p), F2(a.tf.amp_p), dD, dDx, dDy);
+            src = F2(a.dt) * vfma(F2(1.5f), Sn, F2(-0.5f) * Sp);
+        }
+
+        F2 out[kQ];
+        collide_node<F2>(g, ux, uy, ax, ay, Dh, src, magic, w2f, a.tau2_fixed, out);
+
+        // a8: store P_i(x); edge nodes also write their periodic ghost copies
+        const bool edge = j == 0 || j == ny - 1 || i == 0 || i + 1 >= nx - 1;
+        if (!edge) {
+            S* d0 = dst + a.lp.at(i, j);
+#pragma unroll
+            for (int q = 0; q < kQ; ++q)
+                *reinterpret_cast<S2*>(d0 + q * pl) = P::encode(out[q], weight<float>(q) * phi_ref);
+        } else {
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) {
+                const float off = weight<float>(q) * phi_ref;
+                store_with_ghosts(dst + q * pl, a.lp, i, j, Store<S>::encode(out[q].v.x, off));
+                if (i + 1 < nx) store_with_ghosts(dst + q * pl, a.lp, i + 1, j, Store<S>::encode(out[q].v.y, off));
+            }
+        }
+    }
+}
+
+// One tile row of the FP64 path: lane handles nodes i0 + 32 m + lane, m = 0..3.
+template <int SRC, int BX, int BY>
+__device__ __forceinline__ void tile_row_f64(const unsigned char* st, int r, int lane, int i0, int j,
+                                             const StepArgs<double>& a) {
+    using T = Tile<double, SRC, BX, BY>;
+    const int nx = a.lp.nx, ny = a.lp.ny;
+    const double* sp = reinterpret_cast<const double*>(st) + r * T::PW;
+    const double* su = reinterpret_cast<const double*>(st + T::POP) + (r + 1) * T::UW + T::AC;
+    const double* sv = su + T::UH * T::UW;
+    const double* sd = reinterpret_cast<const double*>(st + T::POP + T::U) + r * BX;
+    const double* ss = reinterpret_cast<const double*>(st + T::POP + T::U + T::D) + r * BX;
+    double* dst = static_cast<double*>(a.dst);
+    const size_t pl = a.lp.plane;
+    double sy = 0.0, cy = 0.0;
+    if (SRC == TRTR_SRC_PULSE) {
+        sy = __ldg(a.tab_y + j);
+        cy = __ldg(a.tab_y + ny + j);
+    }
+#pragma unroll 1
+    for (int m = 0; m < BX / 32; ++m) {
+        const int c = 32 * m + lane;
+        const int i = i0 + c;
+        if (i >= nx) break;
+        double g[kQ];
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) g[q] = sp[q * T::PLANE_ELEMS + c + plane_offset<T::A>(q)];
+        const double ux = su[c], uy = sv[c];
+        const double dxux = 0.5 * (su[c + 1] - su[c - 1]);
+        const double dxuy = 0.5 * (sv[c + 1] - sv[c - 1]);
+        const double dyux = 0.5 * (su[c + T::UW] - su[c - T::UW]);
+        const double dyuy = 0.5 * (sv[c + T::UW] - sv[c - T::UW]);
+        const double ax = fma(ux, dxux, uy * dyux);
+        const double ay = fma(ux, dxuy, uy * dyuy);
+        double src = 0.0;
+        if (SRC == TRTR_SRC_FIELD) {
+            src = fma(1.5, ss[c], -0.5 * ss[T::S_TILE / sizeof(double) + c]);
+        } else if (SRC == TRTR_SRC_PULSE) {
+            const double x = a.x0 + (double)i * a.dx, y = a.y0 + (double)j * a.dx;
+            const double sx = __ldg(a.tab_x + i), cx = __ldg(a.tab_x + nx + i);
+            const double dD = a.dD_amp * sx * sy;
+            const double dDx = a.dD_amp * 3.14159265358979323846 * cx * sy;
+            const double dDy = a.dD_amp * 3.14159265358979323846 * sx * cy;
+            const double Sn = pulse_source(x, y, a.tf.cx_n, a.tf.cy_n, a.tf.inv_s2_n, a.tf.amp_n, dD, dDx, dDy);
+            const double Sp =
+                a.tf.first_step ? Sn : pulse_source(x, y, a.tf.cx_p, a.tf.cy_p, a.tf.inv_s2_p, a.tf.amp_p, dD, dDx, dDy);
+            src = a.dt * fma(1.5, Sn, -0.5 * Sp);
+        }
+        double out[kQ];
+        collide_node<double>(g, ux, uy, ax, ay, sd[c], src, a.magic, a.omega2_fixed, a.tau2_fixed, out);
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) store_with_ghosts(dst + q * pl, a.lp, i, j, out[q]);
+    }
+}
+
+
+// ---- host side: TMA descriptors --------------------------------------------------------
+
+// L2 fill granularity of the TMA loads: 0 none, 1 64 B, 2 128 B, 3 256 B.
+#ifndef TRTR_L2_PROMOTION
+#define TRTR_L2_PROMOTION 0
+#endif
+
+template <typename S>
+CUtensorMapDataType tma_type();
+template <>
+inline CUtensorMapDataType tma_type<double>() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT64; }
+template <>
+inline CUtensorMapDataType tma_type<float>() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT32; }
+template <>
+inline CUtensorMapDataType tma_type<__half>() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT16; }
+template <>
+inline CUtensorMapDataType tma_type<__nv_bfloat16>() { return CU_TENSOR_MAP_DATA_TYPE_BFLOAT16; }
+
+inline PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+constexpr CUtensorMapL2promotion kPromotion =
+    TRTR_L2_PROMOTION == 1   ? CU_TENSOR_MAP_L2_PROMOTION_L2_64B
+    : TRTR_L2_PROMOTION == 2 ? CU_TENSOR_MAP_L2_PROMOTION_L2_128B
+    : TRTR_L2_PROMOTION == 3 ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B
+                             : CU_TENSOR_MAP_L2_PROMOTION_NONE;
+
+inline bool encode(CUtensorMap* m, CUtensorMapDataType t, int elem, void* base, const PlaneLayout& L, int depth, int bw,
+            int bh, int bd) {
+    auto fn = get_encoder();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)L.pitch, (cuuint64_t)L.rows, (cuuint64_t)depth};
+    const cuuint64_t strides[2] = {(cuuint64_t)L.pitch * elem, (cuuint64_t)L.plane * elem};
+    const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, (cuuint32_t)bd};
+    const cuuint32_t es[3] = {1, 1, 1};
+    const cuuint32_t rank = depth > 1 ? 3 : 2;
+    return fn(m, t, rank, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              kPromotion, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+
+}  // namespace core
+}  // namespace trtr

@@ -45,6 +45,11 @@ class trtr_params(ctypes.Structure):
     ]
 
 
+class trtr_instance(ctypes.Structure):
+    _fields_ = [("p", trtr_params), ("omega", ctypes.c_double), ("xc", ctypes.c_double), ("yc", ctypes.c_double),
+                ("sigma0", ctypes.c_double), ("D0", ctypes.c_double), ("D_amp", ctypes.c_double)]
+
+
 _dbl_p = ctypes.POINTER(ctypes.c_double)
 _vp = ctypes.c_void_p
 _st = ctypes.c_int
@@ -70,6 +75,17 @@ _SIGNATURES = {
     "trtr_sync": (_st, [_vp]),
     "trtr_launch_count": (_st, [_vp, ctypes.POINTER(ctypes.c_long)]),
     "trtr_phi_sums_noalloc": (_st, [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]),
+    "trtr_batch_create": (_st, [ctypes.POINTER(trtr_instance), ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
+    "trtr_batch_destroy": (_st, [_vp]),
+    "trtr_batch_config_count": (ctypes.c_int, []),
+    "trtr_batch_config_name": (ctypes.c_char_p, [ctypes.c_int]),
+    "trtr_batch_tune": (_st, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]),
+    "trtr_batch_set_config": (_st, [_vp, ctypes.c_int]),
+    "trtr_batch_step": (_st, [_vp, ctypes.c_long]),
+    "trtr_batch_sync": (_st, [_vp]),
+    "trtr_batch_instance": (_st, [_vp, ctypes.c_int, ctypes.POINTER(_vp)]),
+    "trtr_batch_info": (_st, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong),
+                              ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_int)]),
     "trtr_status_str": (ctypes.c_char_p, [_st]),
     "trtr_last_error": (ctypes.c_char_p, [_vp]),
     "trtr_d2q9": (None, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _dbl_p]),
@@ -407,3 +423,136 @@ def pulse_solver(pulse, precision: int = TRTR_F32, stream: int | None = None, sr
     s.set_pulse(pulse.omega, pulse.xc, pulse.yc, pulse.sigma0, pulse.D0, pulse.D_amp)
     s.init_equilibrium(None)
     return s
+
+
+# --------------------------------------------------------------------------------------
+# batched instances
+
+
+def _bcheck(status: int, what: str):
+    if status != TRTR_OK:
+        raise TrtrError(status, f"{what}: {lib.trtr_status_str(status).decode()}")
+
+
+def trtr_batch_create(instances, cuda_stream: int | None = None):
+    arr = (trtr_instance * len(instances))(*instances)
+    out = _vp()
+    _bcheck(lib.trtr_batch_create(arr, len(instances), cuda_stream, ctypes.byref(out)), "trtr_batch_create")
+    return out
+
+
+def trtr_batch_destroy(b):
+    _bcheck(lib.trtr_batch_destroy(b), "trtr_batch_destroy")
+
+
+def trtr_batch_config_count() -> int:
+    return int(lib.trtr_batch_config_count())
+
+
+def trtr_batch_config_name(c: int) -> str:
+    return lib.trtr_batch_config_name(c).decode()
+
+
+def trtr_batch_tune(b, trial_steps: int):
+    n = trtr_batch_config_count()
+    ms = (ctypes.c_float * n)()
+    best = ctypes.c_int()
+    _bcheck(lib.trtr_batch_tune(b, int(trial_steps), ctypes.byref(best), ms), "trtr_batch_tune")
+    return best.value, list(ms)
+
+
+def trtr_batch_set_config(b, config: int):
+    _bcheck(lib.trtr_batch_set_config(b, int(config)), "trtr_batch_set_config")
+
+
+def trtr_batch_step(b, n: int):
+    _bcheck(lib.trtr_batch_step(b, int(n)), "trtr_batch_step")
+
+
+def trtr_batch_sync(b):
+    _bcheck(lib.trtr_batch_sync(b), "trtr_batch_sync")
+
+
+def trtr_batch_instance(b, k: int):
+    out = _vp()
+    _bcheck(lib.trtr_batch_instance(b, int(k), ctypes.byref(out)), "trtr_batch_instance")
+    return out
+
+
+def trtr_batch_info(b):
+    c, nodes, step, cfg = ctypes.c_int(), ctypes.c_longlong(), ctypes.c_long(), ctypes.c_int()
+    _bcheck(lib.trtr_batch_info(b, ctypes.byref(c), ctypes.byref(nodes), ctypes.byref(step), ctypes.byref(cfg)),
+            "trtr_batch_info")
+    return {"count": c.value, "nodes": nodes.value, "step": step.value, "config": cfg.value}
+
+
+def pulse_instance(pulse, precision: int = TRTR_F32, **overrides) -> trtr_instance:
+    """A trtr_instance for a workloads.Pulse (source mode PULSE when D varies)."""
+    src = TRTR_SRC_PULSE if pulse.D_amp != 0.0 else TRTR_SRC_NONE
+    if pulse.tau2 is not None:
+        overrides.setdefault("tau2_mode", TRTR_TAU2_FIXED)
+        overrides.setdefault("tau2", pulse.tau2)
+    p = Params(nx=pulse.nx, ny=pulse.ny, dx=pulse.dx, dt=pulse.dt, x0=pulse.x0, y0=pulse.y0, precision=precision,
+               src_mode=src, grad_mode=TRTR_GRAD_ONESIDED_EDGE, **overrides)
+    return trtr_instance(p.to_c(), pulse.omega, pulse.xc, pulse.yc, pulse.sigma0, pulse.D0, pulse.D_amp)
+
+
+class InstanceView(Solver):
+    """A Solver-like view of one instance of a batch (the batch owns the context)."""
+
+    def __init__(self, batch: "Batch", k: int, params: Params):
+        self.params = params
+        self.n = params.nx * params.ny
+        self.ctx = trtr_batch_instance(batch.b, k)
+        self._batch = batch
+
+    def close(self):
+        self.ctx = None  # owned by the batch
+
+    def step(self, n: int = 1):
+        raise TrtrError(TRTR_ESTATE, "instances of a batch advance through Batch.step")
+
+
+class Batch:
+    """Owns a trtr_batch; methods map onto the C calls."""
+
+    def __init__(self, instances, stream: int | None = None):
+        self.instances = list(instances)
+        self.b = trtr_batch_create(self.instances, stream)
+
+    def close(self):
+        if self.b:
+            trtr_batch_destroy(self.b)
+            self.b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def tune(self, trial_steps: int = 10):
+        return trtr_batch_tune(self.b, trial_steps)
+
+    def set_config(self, c: int):
+        trtr_batch_set_config(self.b, c)
+
+    def step(self, n: int = 1):
+        trtr_batch_step(self.b, n)
+
+    def sync(self):
+        trtr_batch_sync(self.b)
+
+    def info(self):
+        return trtr_batch_info(self.b)
+
+    def instance(self, k: int) -> InstanceView:
+        ip = self.instances[k].p
+        params = Params(**{name: getattr(ip, name) for name, _ in trtr_params._fields_})
+        return InstanceView(self, k, params)

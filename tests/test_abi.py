@@ -99,3 +99,16 @@ def test_null_arguments(T):
     assert lib.trtr_destroy(None) == T.TRTR_OK
     assert lib.trtr_step(None, 1) == T.TRTR_EINVAL
     assert lib.trtr_sync(None) == T.TRTR_EINVAL
+
+
+def test_batch_rejects_bad_instances_before_touching_cuda(T):
+    from paper_2312_10316_gb300 import workloads as W
+
+    a = T.pulse_instance(W.Pulse(n=32), T.TRTR_F32)
+    b = T.pulse_instance(W.Pulse(n=40), T.TRTR_F16_OFS)
+    for bad in ([a, b], [T.pulse_instance(W.Pulse(n=32), T.TRTR_F64)], []):
+        with pytest.raises(T.TrtrError) as e:
+            T.trtr_batch_create(bad)
+        assert e.value.status == T.TRTR_EINVAL
+    assert T.trtr_batch_config_count() == 9
+    assert "128x8" in T.trtr_batch_config_name(0) and T.trtr_batch_config_name(99) == "invalid"
