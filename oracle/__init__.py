@@ -92,6 +92,7 @@ def load(path: str | None = None):
         "oracle_node_post": (None, [ctypes.POINTER(Params), _dbl_p, ctypes.c_double, ctypes.c_double, _dbl_p,
                                     ctypes.c_double, ctypes.c_double, ctypes.c_double, _dbl_p]),
         "oracle_pulse_source_at": (ctypes.c_double, [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
+        "oracle_adjoint": (ctypes.c_int, [vp, ctypes.c_long, _dbl_p, _dbl_p, _dbl_p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -278,6 +279,18 @@ class Sim:
         if g.shape != (Q,) + self.shape:
             raise ValueError("bad population shape")
         self.lib.oracle_set_g(self.h, _ptr(g), int(step))
+
+    def adjoint(self, nsteps: int, lamN, want_lam0: bool = False):
+        """Runs nsteps forward (the state advances) and sweeps back: returns dJ/dD [ny][nx]
+        (and dJ/dg^0 [9][ny][nx]) for lamN = dJ/dphi^N."""
+        lamN = self._field(lamN)
+        grad = np.zeros(self.shape)
+        lam0 = np.zeros((Q,) + self.shape) if want_lam0 else None
+        rc = self.lib.oracle_adjoint(self.h, int(nsteps), _ptr(lamN), _ptr(grad),
+                                     _ptr(lam0) if want_lam0 else None)
+        if rc != 0:
+            raise MemoryError("oracle_adjoint: out of memory")
+        return (grad, lam0) if want_lam0 else grad
 
     def mass(self) -> float:
         return float(self.lib.oracle_mass(self.h))

@@ -499,3 +499,164 @@ int oracle_num_threads(void) {
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------------------ */
+/* Discrete adjoint of the step (for gradients with respect to D).                       */
+
+/* Derivatives of the right-hand side of Eq. (14) at one node with respect to tau1 and tau2
+ * (the per-node relaxation times), from Eqs. (12), (16) and (3):
+ *   d/dtau1: (1/tau1^2) w_i H_ia B_a^neq / cs^2 + dt dG_i/dtau1 + dt dF_i^n/dtau1
+ *            + dt/2 (dF_i^n/dtau1 - dF_i^{n-1}/dtau1),
+ *            dG_i/dtau1 = w_i e_ia/cs^2 phi u_b d_b u_a / (2 tau1^2),
+ *            dF_i/dtau1 = w_i e_ia u_a S / (cs^2 2 tau1^2);
+ *   d/dtau2: (1/tau2^2) w_i H_iab B_ab^neq / (2 cs^4). */
+static void node_dpost_dtau(const oracle_lattice* L, double dt, const double g[Q], const double u[2],
+                            const double du[2][2], double tau1, double tau2, double Sn, double Snm1, double d1[Q],
+                            double d2[Q]) {
+    const double cs2 = L->cs2, cs4 = cs2 * cs2;
+    double phi = 0.0;
+    for (int i = 0; i < Q; ++i) phi += g[i];
+    double geq[Q], gneq[Q];
+    equilibrium(L, phi, u, geq);
+    for (int i = 0; i < Q; ++i) gneq[i] = g[i] - geq[i];
+    double B1[2] = {0.0, 0.0};
+    double B2[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+    for (int i = 0; i < Q; ++i)
+        for (int a = 0; a < 2; ++a) {
+            B1[a] += L->H1[i][a] * gneq[i];
+            for (int b = 0; b < 2; ++b) B2[a][b] += L->H2[i][a][b] * gneq[i];
+        }
+    double adv[2];
+    for (int a = 0; a < 2; ++a) {
+        adv[a] = 0.0;
+        for (int b = 0; b < 2; ++b) adv[a] += u[b] * du[a][b];
+    }
+    const double dk1 = 1.0 / (tau1 * tau1), dkh = 1.0 / (2.0 * tau1 * tau1), dk2 = 1.0 / (tau2 * tau2);
+    for (int i = 0; i < Q; ++i) {
+        double r1 = 0.0, r2 = 0.0, ea = 0.0, eu = 0.0;
+        for (int a = 0; a < 2; ++a) {
+            r1 += L->H1[i][a] * B1[a];
+            ea += L->e[i][a] * adv[a];
+            eu += L->e[i][a] * u[a];
+            for (int b = 0; b < 2; ++b) r2 += L->H2[i][a][b] * B2[a][b];
+        }
+        const double dG = WEIGHT[i] * ea / cs2 * dkh * phi;
+        const double dFn = WEIGHT[i] * eu * Sn / cs2 * dkh;
+        const double dFnm1 = WEIGHT[i] * eu * Snm1 / cs2 * dkh;
+        d1[i] = dk1 * WEIGHT[i] * r1 / cs2 + dt * dG + dt * dFn + (dt / 2.0) * (dFn - dFnm1);
+        d2[i] = dk2 * WEIGHT[i] * r2 / (2.0 * cs4);
+    }
+}
+
+static void node_sources(const oracle_sim* s, int i, int j, const double* Scur, const double* Sprev, int prev_valid,
+                         long step, double* Sn, double* Snm1) {
+    *Sn = 0.0;
+    *Snm1 = 0.0;
+    const size_t k = (size_t)j * s->p.nx + i;
+    if (s->p.src_mode == 1) {
+        *Sn = Scur[k];
+        *Snm1 = prev_valid ? Sprev[k] : *Sn;
+    } else if (s->p.src_mode == 2) {
+        const double x = node_x(s, i), y = node_y(s, j);
+        *Sn = pulse_source(s, x, y, (double)step * s->p.dt);
+        *Snm1 = step > 0 ? pulse_source(s, x, y, (double)(step - 1) * s->p.dt) : *Sn;
+    }
+}
+
+/* Runs `nsteps` steps forward from the current state, keeping every state, then sweeps
+ * back: with J any function of the final phi and lamN = dJ/dphi^N ([ny][nx]),
+ *   lambda^N_i(x) = lamN(x);
+ *   mu_i(x) = lambda^{n+1}_i(x + e_i)          (transpose of the push of Eq. (14))
+ *   lambda^n_j(x) = sum_i A_ij(x) mu_i(x)      (A(x): the node map's Jacobian in g)
+ *   dJ/dD(x) += sum_i mu_i(x) dpost_i/dD(x, g^n(x))
+ * with dpost/dD = dtau1/dD (dpost/dtau1 + dtau2/dtau1 dpost/dtau2), dtau1/dD = 1/(cs^2 dt),
+ * dtau2/dtau1 = -Lambda/(tau1 - 1/2)^2 for the magic parameter and 0 for a fixed tau2.
+ * A(x) is built column by column from the node map applied to unit vectors minus its value
+ * at zero (the map is affine in g).  src_mode 1 keeps one source field for every step.
+ * Outputs grad [ny][nx] (dJ/dD) and, if lam0 is not NULL, lam0 [9][ny][nx] = dJ/dg^0.
+ * Returns 0, or -1 if memory runs out. */
+int oracle_adjoint(oracle_sim* s, long nsteps, const double* lamN, double* grad, double* lam0) {
+    const int nx = s->p.nx, ny = s->p.ny;
+    const size_t n = s->n, st = Q * n;
+    double* states = (double*)malloc((size_t)(nsteps + 1) * st * sizeof(double));
+    double* Sstore = s->p.src_mode == 1 ? (double*)malloc(2 * n * sizeof(double)) : NULL;
+    double* jac = (double*)malloc(n * Q * Q * sizeof(double));
+    double* lam = (double*)malloc(st * sizeof(double));
+    double* lnext = (double*)malloc(st * sizeof(double));
+    if (!states || !jac || !lam || !lnext || (s->p.src_mode == 1 && !Sstore)) {
+        free(states); free(Sstore); free(jac); free(lam); free(lnext);
+        return -1;
+    }
+    const long step0 = s->step;
+    const int prev_valid0 = s->S_prev_valid;
+    if (Sstore) {
+        memcpy(Sstore, s->S_cur, n * sizeof(double));
+        memcpy(Sstore + n, s->S_prev, n * sizeof(double));
+    }
+    memcpy(states, s->g, st * sizeof(double));
+    for (long k = 0; k < nsteps; ++k) {
+        oracle_step(s, 1);
+        memcpy(states + (size_t)(k + 1) * st, s->g, st * sizeof(double));
+    }
+    /* node Jacobians (independent of g and of time) */
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            const size_t k = (size_t)j * nx + i;
+            const double u[2] = {s->ux[k], s->uy[k]};
+            double du[2][2], tau1, tau2, zero[Q] = {0}, e[Q], p0[Q], pe[Q];
+            grad_u(s, i, j, du);
+            node_taus(s, k, &tau1, &tau2);
+            node_post(&s->L, s->p.dt, zero, u, du, tau1, tau2, 0.0, 0.0, p0);
+            for (int c = 0; c < Q; ++c) {
+                for (int q = 0; q < Q; ++q) e[q] = q == c ? 1.0 : 0.0;
+                node_post(&s->L, s->p.dt, e, u, du, tau1, tau2, 0.0, 0.0, pe);
+                for (int q = 0; q < Q; ++q) jac[(k * Q + q) * Q + c] = pe[q] - p0[q];
+            }
+        }
+    for (size_t k = 0; k < n; ++k) {
+        grad[k] = 0.0;
+        for (int q = 0; q < Q; ++q) lam[q * n + k] = lamN[k];
+    }
+    const double dtau1_dD = 1.0 / (s->L.cs2 * s->p.dt);
+    for (long m = nsteps - 1; m >= 0; --m) {
+        const double* gm = states + (size_t)m * st;
+        const long stepm = step0 + m;
+        const int prev_valid = m == 0 ? prev_valid0 : 1;
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const size_t k = (size_t)j * nx + i;
+                double mu[Q], g[Q], d1[Q], d2[Q];
+                for (int q = 0; q < Q; ++q) {
+                    const int it = ((i + EHAT[q][0]) % nx + nx) % nx;
+                    const int jt = ((j + EHAT[q][1]) % ny + ny) % ny;
+                    mu[q] = lam[q * n + (size_t)jt * nx + it];
+                    g[q] = gm[q * n + k];
+                }
+                for (int c = 0; c < Q; ++c) {
+                    double acc = 0.0;
+                    for (int q = 0; q < Q; ++q) acc += jac[(k * Q + q) * Q + c] * mu[q];
+                    lnext[c * n + k] = acc;
+                }
+                if (s->p.tau1_const > 0.0) continue; /* D does not enter */
+                const double u[2] = {s->ux[k], s->uy[k]};
+                double du[2][2], tau1, tau2, Sn, Snm1;
+                grad_u(s, i, j, du);
+                node_taus(s, k, &tau1, &tau2);
+                /* src_mode 1: the field stays S^n; S^{n-1} is the stored one only at the first step */
+                node_sources(s, i, j, Sstore, Sstore ? (m == 0 ? Sstore + n : Sstore) : NULL, prev_valid, stepm, &Sn,
+                             &Snm1);
+                node_dpost_dtau(&s->L, s->p.dt, g, u, du, tau1, tau2, Sn, Snm1, d1, d2);
+                const double dtau2_dtau1 = s->p.tau2_mode == 1 ? 0.0 : -s->p.magic / ((tau1 - 0.5) * (tau1 - 0.5));
+                double acc = 0.0;
+                for (int q = 0; q < Q; ++q) acc += mu[q] * (d1[q] + dtau2_dtau1 * d2[q]);
+                grad[k] += dtau1_dD * acc;
+            }
+        double* t = lam;
+        lam = lnext;
+        lnext = t;
+    }
+    if (lam0) memcpy(lam0, lam, st * sizeof(double));
+    free(states); free(Sstore); free(jac); free(lam); free(lnext);
+    return 0;
+}
+

@@ -437,6 +437,75 @@ def pin_error_and_mass_definitions(lib):
     sim.close()
 
 
+def pin_adjoint_is_the_transposed_step(lib):
+    """The oracle's adjoint sweep over k steps equals (M^k)^T applied to lambda^N, where M is
+    the brute-force step matrix (forward map applied to unit vectors)."""
+    for nx, ny, seed, steps in ((4, 4, 21, 1), (5, 3, 22, 3)):
+        p, X, Y, ux, uy, D, omega = _tiny_setup(nx, ny, seed)
+        M = _oracle_step_matrix(lib, p, ux, uy, D)
+        n = nx * ny
+        c = _rng(seed).uniform(-1.0, 1.0, size=(ny, nx))
+        sim = oracle.Sim(p, lib)
+        sim.set_fields(ux, uy, D)
+        sim.set_g(W.random_populations(seed, ny, nx))
+        _, lam0 = sim.adjoint(steps, c, want_lam0=True)
+        sim.close()
+        expect = np.tile(c.ravel(), 9)
+        for _ in range(steps):
+            expect = M.T @ expect
+        assert np.allclose(lam0.ravel(), expect, rtol=0, atol=1e-12), np.abs(lam0.ravel() - expect).max()
+
+
+def _fd_gradient_check(lib, p, ux, uy, D, g0, c, steps, S=None, rel=1e-6):
+    sim = oracle.Sim(p, lib)
+    sim.set_fields(ux, uy, D)
+    if S is not None:
+        sim.set_source(S)
+    sim.set_g(g0)
+    grad = sim.adjoint(steps, c)
+    sim.close()
+
+    def J(Dv):
+        sm = oracle.Sim(p, lib)
+        sm.set_fields(ux, uy, Dv)
+        if S is not None:
+            sm.set_source(S)
+        sm.set_g(g0)
+        sm.step(steps)
+        v = float(np.sum(c * sm.phi()))
+        sm.close()
+        return v
+
+    fd = np.zeros_like(D)
+    for j in range(D.shape[0]):
+        for i in range(D.shape[1]):
+            h = 1e-6 * D[j, i]
+            Dp, Dm = D.copy(), D.copy()
+            Dp[j, i] += h
+            Dm[j, i] -= h
+            fd[j, i] = (J(Dp) - J(Dm)) / (2 * h)
+    scale = np.abs(fd).max()
+    assert scale > 0
+    assert np.abs(grad - fd).max() <= rel * scale, (np.abs(grad - fd).max(), scale)
+
+
+def pin_adjoint_gradient_matches_finite_differences(lib):
+    """dJ/dD(x) from the adjoint sweep equals central differences of J = sum c(x) phi^N(x)
+    in D(x) at every node: magic tau2, fixed tau2, a source field, the pulse source."""
+    nx, ny, steps = 5, 4, 5
+    p, X, Y, ux, uy, D, omega = _tiny_setup(nx, ny, 31)
+    g0 = W.random_populations(32, ny, nx)
+    c = _rng(33).uniform(-1.0, 1.0, size=(ny, nx))
+    _fd_gradient_check(lib, p, ux, uy, D, g0, c, steps)
+    p_fixed = oracle.SimParams(**{**p.__dict__, "tau2_mode": 1, "tau2": 0.9})
+    _fd_gradient_check(lib, p_fixed, ux, uy, D, g0, c, steps)
+    p_src = oracle.SimParams(**{**p.__dict__, "src_mode": 1})
+    _fd_gradient_check(lib, p_src, ux, uy, D, g0, c, steps, S=_rng(34).uniform(-1, 1, size=(ny, nx)))
+    p_pulse = oracle.SimParams(**{**p.__dict__, "src_mode": 2, "omega": omega, "xc": 0.2, "yc": -0.1,
+                                  "sigma0": 0.6, "D0": float(D.mean()), "D_amp": 0.5})
+    _fd_gradient_check(lib, p_pulse, ux, uy, D, g0, c, steps)
+
+
 ALL_PINS = [
     pin_error_and_mass_definitions,
     pin_lattice,
@@ -453,4 +522,6 @@ ALL_PINS = [
     pin_manufactured_source,
     pin_pulse_source_time_levels,
     pin_second_order_convergence,
+    pin_adjoint_is_the_transposed_step,
+    pin_adjoint_gradient_matches_finite_differences,
 ]

@@ -22,7 +22,8 @@ MUTANTS = {
                "G[i] = -WEIGHT[i] * ea / L->cs2 * (1.0 - 1.0 / (2.0 * tau1)) * phi;"),
     "G_dropped": ("post[q] = post[q] + dt * G[q] + dt * Fn[q] + dtF;",
                   "post[q] = post[q] + dt * Fn[q] + dtF;"),
-    "G_grad_transposed": ("adv[a] += u[b] * du[a][b];", "adv[a] += u[b] * du[b][a];"),
+    "G_grad_transposed": ("adv[a] += u[b] * du[a][b];\n    }\n    for (int i = 0; i < Q; ++i) {\n        double ea = 0.0;",
+                          "adv[a] += u[b] * du[b][a];\n    }\n    for (int i = 0; i < Q; ++i) {\n        double ea = 0.0;"),
     "G_tau_factor": ("G[i] = WEIGHT[i] * ea / L->cs2 * (1.0 - 1.0 / (2.0 * tau1)) * phi;",
                      "G[i] = WEIGHT[i] * ea / L->cs2 * (1.0 - 1.0 / tau1) * phi;"),
     "F_first_order_dropped": (
@@ -36,8 +37,13 @@ MUTANTS = {
     "third_order_eq_dropped": ("+ t3 / (6.0 * cs6));", ");"),
     "H2_sign": ("L->H2[i][a][b] = L->e[i][a] * L->e[i][b] - L->cs2 * kron(a, b);",
                 "L->H2[i][a][b] = L->e[i][a] * L->e[i][b] + L->cs2 * kron(a, b);"),
-    "push_direction": ("const int it = ((i + EHAT[q][0]) % nx + nx) % nx;",
-                       "const int it = ((i - EHAT[q][0]) % nx + nx) % nx;"),
+    "push_direction": ("post);\n            for (int q = 0; q < Q; ++q) {\n                const int it = ((i + EHAT[q][0]) % nx + nx) % nx;",
+                       "post);\n            for (int q = 0; q < Q; ++q) {\n                const int it = ((i - EHAT[q][0]) % nx + nx) % nx;"),
+    "adjoint_tau2_chain_dropped": ("acc += mu[q] * (d1[q] + dtau2_dtau1 * d2[q]);", "acc += mu[q] * d1[q];"),
+    "adjoint_no_transpose_shift": ("mu[q] = lam[q * n + (size_t)jt * nx + it];", "mu[q] = lam[q * n + k];"),
+    "adjoint_jacobian_not_transposed": ("acc += jac[(k * Q + q) * Q + c] * mu[q];",
+                                        "acc += jac[(k * Q + c) * Q + q] * mu[q];"),
+    "adjoint_dkh": ("dkh = 1.0 / (2.0 * tau1 * tau1)", "dkh = 1.0 / (tau1 * tau1)"),
     "weight_swap": ("static const double WEIGHT[Q] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,\n"
                     "                                 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};",
                     "static const double WEIGHT[Q] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 36.0, 1.0 / 9.0,\n"
