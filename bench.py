@@ -44,6 +44,8 @@ WORKLOADS = {
 DEFAULT_WORKLOAD = "pulse4096_f32_varD_mms"
 # batched workloads: 256 seeded pulses, square grids drawn from {64 ... 1024}, one launch per step
 BATCH_WORKLOADS = {"batch256_f32": ("f32", 4), "batch256_f16": ("f16", 2)}
+# gradient of the L2 misfit w.r.t. D through 2000 steps of a 512^2 pulse (discrete adjoint)
+ADJOINT_WORKLOADS = {"adjoint512_f32": "f32"}
 STEP_SOURCES = ["paper_2312_10316_gb300/csrc/trtr_step.cu", "paper_2312_10316_gb300/csrc/trtr_internal.cuh"]
 
 
@@ -52,7 +54,7 @@ def parse_args():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10000)
     ap.add_argument("--warmup", type=int, default=50)
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) + sorted(ADJOINT_WORKLOADS))
     ap.add_argument("--baseline-steps", type=int, default=50,
                     help="steps of the per-instance-launch comparison (batched workloads)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -378,7 +380,10 @@ def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return None
-    if args.workload in BATCH_WORKLOADS:  # sample the batch's largest instance
+    if args.workload in ADJOINT_WORKLOADS:
+        prec_key = ADJOINT_WORKLOADS[args.workload]
+        pulse = W.C5_ADJ_512
+    elif args.workload in BATCH_WORKLOADS:  # sample the batch's largest instance
         prec_key = BATCH_WORKLOADS[args.workload][0]
         pulse = max((bi.pulse for bi in W.batch_instances(seed=0, count=256)), key=lambda p: p.nx * p.ny)
     else:
@@ -507,12 +512,80 @@ def run_batch(args):
     return line
 
 
+def run_adjoint(args):
+    """Gradient evaluations (forward with sqrt(T) checkpoints + adjoint sweep, through the
+    torch.autograd wrapper) timed against the plain forward run of the same steps."""
+    import numpy as np
+    import torch
+
+    from paper_2312_10316_gb300 import trtr as T
+    from paper_2312_10316_gb300.autograd import misfit_and_gradient
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    prec = T.PRECISIONS[ADJOINT_WORKLOADS[args.workload]]
+    pulse = W.C5_ADJ_512
+    n, steps = pulse.n, pulse.steps
+    evals = max(1, min(args.steps, 10))
+    f = W.fields(pulse)
+    dev = {k: torch.from_numpy(v).cuda() for k, v in f.items()}
+    D_true = torch.from_numpy(W.smooth_random_field(5, n, modes=8, kmax=4, amp=0.3, mean=1e-3)).cuda()
+    D = torch.full((n, n), 1e-3, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.Stream()
+    p = T.Params(nx=n, ny=n, dx=pulse.dx, dt=pulse.dt, precision=prec)
+    with torch.cuda.stream(stream), T.Solver(p, stream.cuda_stream) as s:
+        s.set_fields(dev["ux"], dev["uy"], D_true)
+        s.init_equilibrium(dev["phi0"])
+        s.step(steps)
+        phi_obs = torch.empty((n, n), dtype=torch.float64, device="cuda")
+        s.moments(phi_obs)
+        for _ in range(max(1, min(args.warmup, 2))):
+            misfit_and_gradient(s, dev["ux"], dev["uy"], D, dev["phi0"], phi_obs, steps)
+        torch.cuda.synchronize()
+        launches0 = s.launches
+        t0 = time.perf_counter()
+        for _ in range(evals):
+            J, g = misfit_and_gradient(s, dev["ux"], dev["uy"], D, dev["phi0"], phi_obs, steps)
+        torch.cuda.synchronize()
+        t_grad = (time.perf_counter() - t0) / evals
+        launches_per_gradient = (s.launches - launches0) // evals
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.init_equilibrium(dev["phi0"])
+        e0.record(stream)
+        s.step(steps)
+        e1.record(stream)
+        stream.synchronize()
+        t_fwd = e0.elapsed_time(e1) * 1e-3
+        interval = int(math.ceil(math.sqrt(steps)))
+        state_mb = 9 * (n + 2) * (((n + 64 + 31) // 32) * 32) * (8 if prec == T.TRTR_F64 else 4) / 1e6
+    if rank != 0:
+        return None
+    value = steps * n * n / t_grad / 1e9
+    return {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": evals,
+        "warmup": args.warmup, "ms_per_step": round(t_grad * 1e3 / steps, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": ADJOINT_WORKLOADS[args.workload], "data": "synthetic",
+        "config": {"workload": args.workload, "nx": n, "ny": n, "lbm_steps_per_gradient": steps,
+                   "courant": pulse.courant, "D_true": "1e-3 (1 + 0.3 m/max|m|), m: 8 seeded Fourier modes",
+                   "gradient_at": "D = 1e-3", "value_definition": "forward node-steps per second of one gradient "
+                   "evaluation (forward with checkpoints + adjoint sweep)", "parallelism": "single"},
+        "adjoint": {"gradient_ms": round(t_grad * 1e3, 3), "plain_forward_ms": round(t_fwd * 1e3, 3),
+                    "gradient_over_forward": round(t_grad / t_fwd, 3), "gradients_per_s": round(1.0 / t_grad, 3),
+                    "checkpoint_interval": interval,
+                    "checkpoint_memory_MB": round((interval + (steps + interval - 1) // interval) * state_mb, 1),
+                    "misfit": float(J)},
+        "gpu_launches": launches_per_gradient * evals,
+    }
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         line = run_reference(args)
     elif args.workload in BATCH_WORKLOADS:
         line = run_batch(args)
+    elif args.workload in ADJOINT_WORKLOADS:
+        line = run_adjoint(args)
     else:
         line = run_ours(args)
     if line is not None:

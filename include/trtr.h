@@ -175,6 +175,24 @@ trtr_status trtr_sync(trtr_ctx* ctx);
 /* Number of kernels the library enqueued on this context since creation (launch count). */
 trtr_status trtr_launch_count(const trtr_ctx* ctx, long* launches);
 
+/* ---- Gradients with respect to the diffusivity field (discrete adjoint) ------------------
+ * For J any function of the final phi, dJ/dD(x) through n steps of Eq. (14): the exact
+ * derivative of the discrete step (a discrete adjoint), which the paper does not treat.
+ * D enters each step through tau1 = 1/2 + 3 D dt/dx^2 (Sec. 2.4) and, with the magic
+ * parameter, through tau2 (Eq. (28)).  Scope: S = 0 (src_mode TRTR_SRC_NONE). */
+
+/* Advances n >= 1 steps from the current state, keeping a copy of the state every
+ * `interval` steps (0: ceil(sqrt(n))), and remembers the run for trtr_adjoint.  Allocates
+ * about (n/interval + interval) population arrays of device memory (freed by the next
+ * record or by trtr_destroy). */
+trtr_status trtr_forward_record(trtr_ctx* ctx, long steps, int interval);
+
+/* Backward sweep of the recorded run: dJ_dphi = dJ/dphi(x, t_end) [ny][nx] (host or device);
+ * grad_D receives dJ/dD(x) [ny][nx] in physical units (host or device).  Each segment between
+ * checkpoints is recomputed once from its checkpoint.  The context must still be at the end
+ * of the recorded run (TRTR_ESTATE otherwise); its state is not changed.  Synchronises. */
+trtr_status trtr_adjoint(trtr_ctx* ctx, const double* dJ_dphi, int on_device, double* grad_D, int grad_on_device);
+
 /* ---- Batched instances ----------------------------------------------------------------
  * Many independent problems of uneven sizes advanced together, each by the same step of
  * Eq. (14).  The paper solves one problem at a time; this is a throughput mode of its step.

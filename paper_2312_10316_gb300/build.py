@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtrtr.so")
 
-SOURCES = ["trtr_api.cu", "trtr_step.cu", "trtr_aux.cu", "trtr_noalloc.cu", "trtr_batch.cu"]
+SOURCES = ["trtr_api.cu", "trtr_step.cu", "trtr_aux.cu", "trtr_noalloc.cu", "trtr_batch.cu", "trtr_adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
                      "-I", INCLUDE, "-I", CSRC]

@@ -250,6 +250,7 @@ trtr_status trtr_destroy(trtr_ctx* ctx) {
     if (!ctx) return TRTR_OK;
     cudaStreamSynchronize(ctx->stream);
     cudaGetLastError();
+    trtr::free_adjoint(ctx);
     void* ptrs[] = {ctx->pop[0], ctx->pop[1], ctx->uv,      ctx->Dh,   ctx->S,     ctx->tab_x,
                     ctx->tab_y,  ctx->scratch, ctx->dres, ctx->dflag, ctx->dtmp};
     for (void* q : ptrs)

@@ -126,6 +126,8 @@ enum MapId { kMapPop0 = 0, kMapPop1 = 1, kMapU = 2, kMapD = 3, kMapS = 4, kNumMa
 
 }  // namespace trtr
 
+struct trtr_adjoint_state;  // checkpoints and adjoint buffers (trtr_adjoint.cu)
+
 struct trtr_ctx {
     CUtensorMap maps[trtr::kNumMaps];  // TMA descriptors (64-byte aligned type)
     trtr_params p;
@@ -156,6 +158,7 @@ struct trtr_ctx {
     trtr::Pulse pulse;
     long step;
     long launches;
+    trtr_adjoint_state* adj;  // recorded forward run (trtr_forward_record), or NULL
     char err[512];
 };
 
@@ -165,6 +168,10 @@ namespace trtr {
 // return the cudaGetLastError() of the launch.
 cudaError_t encode_maps(trtr_ctx* ctx);
 cudaError_t launch_step(trtr_ctx* ctx);
+// one step from an arbitrary population buffer (its map from encode_pop_map) into dst, as step `step`
+cudaError_t launch_step_from(trtr_ctx* ctx, const CUtensorMap* src_map, void* dst, long step);
+cudaError_t encode_pop_map(trtr_ctx* ctx, void* buffer, CUtensorMap* out);
+void free_adjoint(trtr_ctx* ctx);
 cudaError_t launch_convert_fields(trtr_ctx* ctx, const double* ux, const double* uy, const double* D);
 cudaError_t launch_pulse_fields(trtr_ctx* ctx);
 cudaError_t launch_convert_source(trtr_ctx* ctx, const double* S, int buffer);

@@ -168,8 +168,10 @@ cudaError_t encode_typed(trtr_ctx* ctx) {
     return ok ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// One step from the population buffer described by src_map into dst, as step `step` (its
+// source terms and first-step rule).
 template <typename S, int SRC>
-cudaError_t launch_typed(trtr_ctx* ctx) {
+cudaError_t launch_typed(trtr_ctx* ctx, const CUtensorMap& src_map, void* dst, long step) {
     using C = typename Store<S>::C;
     using T = Tile<S, SRC, kBX, kBY>;
     constexpr int kStages = stages_for<S, SRC>();
@@ -186,7 +188,7 @@ cudaError_t launch_typed(trtr_ctx* ctx) {
         configured_device = ctx->device;
     }
     StepArgs<C> a;
-    a.dst = ctx->pop[ctx->cur ^ 1];
+    a.dst = dst;
     a.tab_x = static_cast<const C*>(ctx->tab_x);
     a.tab_y = static_cast<const C*>(ctx->tab_y);
     a.flag = ctx->dflag;
@@ -202,10 +204,10 @@ cudaError_t launch_typed(trtr_ctx* ctx) {
     a.y0 = C(ctx->p.y0);
     a.dx = C(ctx->p.dx);
     a.dt = C(ctx->p.dt);
-    a.tf.first_step = ctx->step == 0;
+    a.tf.first_step = step == 0;
     if (SRC == TRTR_SRC_PULSE) {
-        const PulseTime tn = pulse_at(ctx->pulse, (double)ctx->step * ctx->p.dt);
-        const PulseTime tp = pulse_at(ctx->pulse, (double)(ctx->step - 1) * ctx->p.dt);
+        const PulseTime tn = pulse_at(ctx->pulse, (double)step * ctx->p.dt);
+        const PulseTime tp = pulse_at(ctx->pulse, (double)(step - 1) * ctx->p.dt);
         a.dD_amp = C(ctx->pulse.D0 * ctx->pulse.D_amp);
         a.tf.cx_n = C(tn.cx); a.tf.cy_n = C(tn.cy); a.tf.inv_s2_n = C(tn.inv_s2); a.tf.amp_n = C(tn.amp);
         a.tf.cx_p = C(tp.cx); a.tf.cy_p = C(tp.cy); a.tf.inv_s2_p = C(tp.inv_s2); a.tf.amp_p = C(tp.amp);
@@ -217,18 +219,24 @@ cudaError_t launch_typed(trtr_ctx* ctx) {
     const long ntiles = (long)((ctx->lp.nx + kBX - 1) / kBX) * ((ctx->lp.ny + kBY - 1) / kBY);
     const long cap = (long)ctx->num_sms * ctas_per_sm;
     const int grid = (int)(ntiles < cap ? ntiles : cap);
-    kernel<<<grid, kThreads, smem, ctx->stream>>>(ctx->maps[kMapPop0 + ctx->cur], ctx->maps[kMapU], ctx->maps[kMapD],
-                                                  ctx->maps[kMapS], a);
+    kernel<<<grid, kThreads, smem, ctx->stream>>>(src_map, ctx->maps[kMapU], ctx->maps[kMapD], ctx->maps[kMapS], a);
     return cudaGetLastError();
 }
 
 template <typename S>
-cudaError_t launch_src(trtr_ctx* ctx) {
+cudaError_t launch_src(trtr_ctx* ctx, const CUtensorMap& src_map, void* dst, long step) {
     switch (ctx->p.src_mode) {
-        case TRTR_SRC_FIELD: return launch_typed<S, TRTR_SRC_FIELD>(ctx);
-        case TRTR_SRC_PULSE: return launch_typed<S, TRTR_SRC_PULSE>(ctx);
-        default: return launch_typed<S, TRTR_SRC_NONE>(ctx);
+        case TRTR_SRC_FIELD: return launch_typed<S, TRTR_SRC_FIELD>(ctx, src_map, dst, step);
+        case TRTR_SRC_PULSE: return launch_typed<S, TRTR_SRC_PULSE>(ctx, src_map, dst, step);
+        default: return launch_typed<S, TRTR_SRC_NONE>(ctx, src_map, dst, step);
     }
+}
+
+template <typename S>
+cudaError_t encode_pop_typed(trtr_ctx* ctx, void* buffer, CUtensorMap* out) {
+    using T = Tile<S, TRTR_SRC_NONE, kBX, kBY>;
+    return encode(out, tma_type<S>(), sizeof(S), buffer, ctx->lp, kQ, T::PW, kBY, 1) ? cudaSuccess
+                                                                                    : cudaErrorInvalidValue;
 }
 
 }  // namespace
@@ -243,12 +251,26 @@ cudaError_t encode_maps(trtr_ctx* ctx) {
     }
 }
 
-cudaError_t launch_step(trtr_ctx* ctx) {
+cudaError_t launch_step_from(trtr_ctx* ctx, const CUtensorMap* src_map, void* dst, long step) {
     switch (ctx->p.precision) {
-        case TRTR_F64: return launch_src<double>(ctx);
-        case TRTR_F32: return launch_src<float>(ctx);
-        case TRTR_F16_OFS: return launch_src<__half>(ctx);
-        case TRTR_BF16_OFS: return launch_src<__nv_bfloat16>(ctx);
+        case TRTR_F64: return launch_src<double>(ctx, *src_map, dst, step);
+        case TRTR_F32: return launch_src<float>(ctx, *src_map, dst, step);
+        case TRTR_F16_OFS: return launch_src<__half>(ctx, *src_map, dst, step);
+        case TRTR_BF16_OFS: return launch_src<__nv_bfloat16>(ctx, *src_map, dst, step);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_step(trtr_ctx* ctx) {
+    return launch_step_from(ctx, &ctx->maps[kMapPop0 + ctx->cur], ctx->pop[ctx->cur ^ 1], ctx->step);
+}
+
+cudaError_t encode_pop_map(trtr_ctx* ctx, void* buffer, CUtensorMap* out) {
+    switch (ctx->p.precision) {
+        case TRTR_F64: return encode_pop_typed<double>(ctx, buffer, out);
+        case TRTR_F32: return encode_pop_typed<float>(ctx, buffer, out);
+        case TRTR_F16_OFS: return encode_pop_typed<__half>(ctx, buffer, out);
+        case TRTR_BF16_OFS: return encode_pop_typed<__nv_bfloat16>(ctx, buffer, out);
         default: return cudaErrorInvalidValue;
     }
 }

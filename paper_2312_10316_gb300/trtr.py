@@ -75,6 +75,8 @@ _SIGNATURES = {
     "trtr_sync": (_st, [_vp]),
     "trtr_launch_count": (_st, [_vp, ctypes.POINTER(ctypes.c_long)]),
     "trtr_phi_sums_noalloc": (_st, [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]),
+    "trtr_forward_record": (_st, [_vp, ctypes.c_long, ctypes.c_int]),
+    "trtr_adjoint": (_st, [_vp, _vp, ctypes.c_int, _vp, ctypes.c_int]),
     "trtr_batch_create": (_st, [ctypes.POINTER(trtr_instance), ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
     "trtr_batch_destroy": (_st, [_vp]),
     "trtr_batch_config_count": (ctypes.c_int, []),
@@ -281,6 +283,19 @@ def trtr_phi_sums_noalloc(g, nx: int, ny: int, phi_ref, out, cuda_stream: int | 
                                          None if phi_ref is None else phi_ref.data_ptr(), out.data_ptr(), cuda_stream))
 
 
+def trtr_forward_record(ctx, steps: int, interval: int = 0):
+    _check(ctx, lib.trtr_forward_record(ctx, int(steps), int(interval)))
+
+
+def trtr_adjoint(ctx, n: int, dJ_dphi, grad_out):
+    pd, dd, kd = _arr(dJ_dphi, n)
+    pg, dg, kg = _arr(grad_out, n)
+    if dg == 0 and kg is not grad_out:
+        raise ValueError("host output must be a contiguous float64 numpy array")
+    _check(ctx, lib.trtr_adjoint(ctx, pd, dd, pg, dg))
+    return grad_out
+
+
 def trtr_status_str(s: int) -> str:
     return lib.trtr_status_str(s).decode()
 
@@ -403,6 +418,14 @@ class Solver:
 
     def sync(self):
         trtr_sync(self.ctx)
+
+    def forward_record(self, steps: int, interval: int = 0):
+        trtr_forward_record(self.ctx, steps, interval)
+
+    def adjoint(self, dJ_dphi, out=None):
+        if out is None:
+            out = np.zeros((self.params.ny, self.params.nx))
+        return trtr_adjoint(self.ctx, self.n, dJ_dphi, out)
 
     @property
     def launches(self) -> int:
