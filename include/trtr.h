@@ -70,7 +70,9 @@ typedef enum { TRTR_GRAD_PERIODIC = 0, TRTR_GRAD_ONESIDED_EDGE = 1 } trtr_grad_m
 
 /* Source S: none; a field set with trtr_set_source (S^n, the previous step's field kept as
  * S^{n-1}); or the built-in manufactured source of the rotating pulse (trtr_set_pulse).
- * d_t F_i is (F^n - F^{n-1}) / dt with F^{-1} := F^0 at the first step after init. */
+ * d_t F_i is (F^n - F^{n-1}) / dt.  The built-in source is a closed form of t, so its S^{n-1}
+ * is S(t_n - dt) at the first step too; a field source has no predecessor at the first step
+ * after init and takes F^{-1} := F^0. */
 typedef enum { TRTR_SRC_NONE = 0, TRTR_SRC_FIELD = 1, TRTR_SRC_PULSE = 2 } trtr_src_mode;
 
 typedef struct {

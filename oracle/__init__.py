@@ -55,6 +55,11 @@ class Params(ctypes.Structure):
     ]
 
 
+class PaperParams(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("L", ctypes.c_double), ("kappa", ctypes.c_double), ("dt", ctypes.c_double),
+                ("model", ctypes.c_int), ("magic", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -93,6 +98,9 @@ def load(path: str | None = None):
                                     ctypes.c_double, ctypes.c_double, ctypes.c_double, _dbl_p]),
         "oracle_pulse_source_at": (ctypes.c_double, [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
         "oracle_adjoint": (ctypes.c_int, [vp, ctypes.c_long, _dbl_p, _dbl_p, _dbl_p]),
+        "oracle_paper_pulse": (ctypes.c_int, [ctypes.POINTER(PaperParams), ctypes.c_double, _dbl_p]),
+        "oracle_paper_slip": (ctypes.c_long, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                              ctypes.c_double, ctypes.c_long, ctypes.c_double, _dbl_p, _dbl_p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -305,3 +313,28 @@ class Sim:
 
 def num_threads(lib=None) -> int:
     return int((lib or load()).oracle_num_threads())
+
+
+def paper_pulse(N: int, kappa: float, dt: float, model: int = 0, t_end: float = 1.0, magic: float = 1.0 / 12.0,
+                L: float = 4.0 * np.pi, lib=None):
+    """The paper's rotating-pulse benchmark (Sec. 3) to t_end: (RMS error of Eq. (33), blew_up)."""
+    lib = lib or load()
+    pp = PaperParams(N, L, kappa, dt, model, magic)
+    rms = ctypes.c_double()
+    rc = lib.oracle_paper_pulse(ctypes.byref(pp), float(t_end), ctypes.byref(rms))
+    if rc < 0:
+        raise ValueError("bad benchmark parameters")
+    return rms.value, bool(rc)
+
+
+def paper_slip(ny: int, tau1: float, tau2: float, S: float = 1e-3, phi_w: float = 0.0, max_steps: int = 200000,
+               tol: float = 1e-16, lib=None):
+    """Steady wall-bounded diffusion (Sec. 3.2): (RMS error against the parabola, phi [ny], steps)."""
+    lib = lib or load()
+    rms = ctypes.c_double()
+    phi = np.zeros(ny)
+    n = lib.oracle_paper_slip(int(ny), float(tau1), float(tau2), float(S), float(phi_w), int(max_steps), float(tol),
+                              ctypes.byref(rms), _ptr(phi))
+    if n < 0:
+        raise ValueError("bad slip-check parameters")
+    return rms.value, phi, int(n)

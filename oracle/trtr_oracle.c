@@ -24,7 +24,10 @@
  *  - d_beta u_alpha in G_i (Eq. (16) [eq_aux_new]) is a second-order central difference of
  *    the nodal u field; mode 1 uses the one-sided two-point difference on the first and
  *    last column/row instead of wrapping (both are exact for a linear u).
- *  - dt^2/2 d_t F_i is (dt^2/2)(F_i^n - F_i^{n-1})/dt, with F^{-1} := F^0 at the first step
+ *  - dt^2/2 d_t F_i is (dt^2/2)(F_i^n - F_i^{n-1})/dt.  A closed-form source (the built-in pulse,
+ *    the Sec. 3 benchmark) gives S^{n-1} = S(t_n - dt) at the first step too (Table 2's printed
+ *    errors agree with this to their last digit); a source field without a predecessor takes
+ *    F^{-1} := F^0 at the first step
  *    after initialisation (u is time-independent within a step, Sec. 2.3).
  *  - phi = sum_i g_i of the pre-collision populations (B_0^neq = 0, Sec. 2.2).
  *  - tau1 from kappa = (tau1 - 1/2) c_s^2 dt (Sec. 2.4), per node from D(x); tau2 from the
@@ -50,6 +53,7 @@ static const int EHAT[Q][2] = {{0, 0}, {1, 0}, {-1, 0}, {0, 1}, {0, -1},
                                {1, 1}, {-1, -1}, {1, -1}, {-1, 1}};
 static const double WEIGHT[Q] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
                                  1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+static const int OPPOSITE[Q] = {0, 2, 1, 4, 3, 6, 5, 8, 7}; /* e_OPPOSITE[i] = -e_i */
 
 typedef struct {
     int nx, ny;
@@ -399,7 +403,7 @@ static void step_rows(oracle_sim* s, int j0, int j1, double t_n, double t_nm1) {
             } else if (s->p.src_mode == 2) {
                 const double x = node_x(s, i), y = node_y(s, j);
                 Sn = pulse_source(s, x, y, t_n);
-                Snm1 = s->step > 0 ? pulse_source(s, x, y, t_nm1) : Sn;
+                Snm1 = pulse_source(s, x, y, t_nm1); /* closed form: S(t_{-1}) at the first step too */
             }
             node_post(&s->L, s->p.dt, g, u, du, tau1, tau2, Sn, Snm1, post);
             for (int q = 0; q < Q; ++q) {
@@ -559,7 +563,7 @@ static void node_sources(const oracle_sim* s, int i, int j, const double* Scur, 
     } else if (s->p.src_mode == 2) {
         const double x = node_x(s, i), y = node_y(s, j);
         *Sn = pulse_source(s, x, y, (double)step * s->p.dt);
-        *Snm1 = step > 0 ? pulse_source(s, x, y, (double)(step - 1) * s->p.dt) : *Sn;
+        *Snm1 = pulse_source(s, x, y, (double)(step - 1) * s->p.dt);
     }
 }
 
@@ -660,3 +664,226 @@ int oracle_adjoint(oracle_sim* s, long nsteps, const double* lamN, double* grad,
     return 0;
 }
 
+
+/* The paper's benchmark (Sec. 3): a rotating Gaussian pulse with a manufactured source on
+ * [-L/2, L/2]^2, L = 4 pi, with Dirichlet boundaries by non-equilibrium extrapolation.
+ *
+ *   u = (-y, x), kappa constant, phi_a = exp(-(x^2 + 3 y^2 + 2 kappa t)),
+ *   S = [6 kappa - 4 x y - 4 kappa (x^2 + 9 y^2)] exp(-(x^2 + 3 y^2 + 2 kappa t)),
+ *   g = g^eq(phi_0, u) at t = 0; RMS error of Eq. (33) over all nodes at t_end.
+ *
+ * Models (the columns of Table 2):
+ *   0  present: TRT-R (Eq. (12)), G of Eq. (16), F of Eq. (3), dt^2/2 d_t F;
+ *   1  TRT-R with the traditional terms: G of Eq. (15)/(34) with d_t(phi u) taken as
+ *      (phi^n - phi^{n-1}) u / dt (u is steady; 0 at the first step), F = w S (Eq. (35));
+ *   2  BGK (Eq. (4), tau = tau1) with the same traditional terms.
+ * All three take d_t F as (F^n - F^{n-1}) / dt with S^{n-1} = S(t_n - dt), the closed form, at
+ * the first step too.
+ *
+ * Readings: nodes x_i = -L/2 + i L/N, i = 0..N (N + 1 per side; both boundaries are nodes and
+ * dx = L / N); at a boundary node after streaming, g_i = g_i^eq(phi_a, u) + g_i(x_f) -
+ * g_i^eq(phi(x_f), u(x_f)) for every i, x_f the adjacent interior node along the inward normal
+ * (the diagonal one at corners); d_beta u_alpha is exact (u is linear); tau2 from Lambda. */
+
+typedef struct {
+    int N;          /* intervals per side */
+    double L;       /* side length */
+    double kappa;   /* diffusivity */
+    double dt;      /* time step */
+    int model;      /* 0, 1, 2 (above) */
+    double magic;   /* Lambda for tau2 */
+} oracle_paper_params;
+
+static double paper_phi(double x, double y, double kappa, double t) {
+    return exp(-(x * x + 3.0 * y * y + 2.0 * kappa * t));
+}
+
+static double paper_source(double x, double y, double kappa, double t) {
+    return (6.0 * kappa - 4.0 * x * y - 4.0 * kappa * (x * x + 9.0 * y * y)) * exp(-(x * x + 3.0 * y * y + 2.0 * kappa * t));
+}
+
+/* BGK collision, Eq. (4): g^eq + (1 - 1/tau) (g - g^eq). */
+static void collide_bgk(const oracle_lattice* L, const double g[Q], const double u[2], double tau, double out[Q],
+                        double* phi_out) {
+    double phi = 0.0;
+    for (int i = 0; i < Q; ++i) phi += g[i];
+    double geq[Q];
+    equilibrium(L, phi, u, geq);
+    for (int i = 0; i < Q; ++i) out[i] = geq[i] + (1.0 - 1.0 / tau) * (g[i] - geq[i]);
+    *phi_out = phi;
+}
+
+/* Runs the benchmark to t_end (round(t_end / dt) steps).  Writes the RMS error of Eq. (33)
+ * at t_end; returns 0, 1 if the run blew up (non-finite or |phi| > 1e3), -1 on bad input. */
+int oracle_paper_pulse(const oracle_paper_params* pp, double t_end, double* rms_out) {
+    const int N = pp->N, n1 = N + 1;
+    if (N < 2 || !(pp->dt > 0.0) || !(pp->L > 0.0)) return -1;
+    const double dx = pp->L / N, dt = pp->dt, x0 = -pp->L / 2.0;
+    oracle_lattice Lat;
+    lattice_init(&Lat, dx, dt);
+    const size_t n = (size_t)n1 * n1;
+    double* g = (double*)calloc(Q * n, sizeof(double));
+    double* gn = (double*)calloc(Q * n, sizeof(double));
+    double* phi_prev = (double*)calloc(n, sizeof(double));
+    double* phi_cur = (double*)calloc(n, sizeof(double));
+    if (!g || !gn || !phi_prev || !phi_cur) {
+        free(g); free(gn); free(phi_prev); free(phi_cur);
+        return -1;
+    }
+    const double tau1 = 0.5 + pp->kappa / (Lat.cs2 * dt);
+    const double tau2 = 0.5 + pp->magic / (tau1 - 0.5);
+    const double du[2][2] = {{0.0, -1.0}, {1.0, 0.0}}; /* d_b u_a for u = (-y, x) */
+#define PIDX(q, j, i) ((size_t)(q) * n + (size_t)(j) * n1 + (size_t)(i))
+    for (int j = 0; j < n1; ++j)
+        for (int i = 0; i < n1; ++i) {
+            const double x = x0 + i * dx, y = x0 + j * dx, u[2] = {-y, x};
+            double geq[Q];
+            equilibrium(&Lat, paper_phi(x, y, pp->kappa, 0.0), u, geq);
+            for (int q = 0; q < Q; ++q) g[PIDX(q, j, i)] = geq[q];
+            phi_cur[(size_t)j * n1 + i] = paper_phi(x, y, pp->kappa, 0.0);
+            phi_prev[(size_t)j * n1 + i] = phi_cur[(size_t)j * n1 + i];
+        }
+    const long steps = lround(t_end / dt);
+    int blew = 0;
+    for (long s = 0; s < steps && !blew; ++s) {
+        const double tn = s * dt, tnm1 = (s - 1) * dt;
+        memset(gn, 0, Q * n * sizeof(double));
+        for (int j = 0; j < n1; ++j)
+            for (int i = 0; i < n1; ++i) {
+                const double x = x0 + i * dx, y = x0 + j * dx, u[2] = {-y, x};
+                const size_t k = (size_t)j * n1 + i;
+                double gl[Q], post[Q], G[Q], Fn[Q], Fp[Q], phi;
+                for (int q = 0; q < Q; ++q) gl[q] = g[PIDX(q, j, i)];
+                const double Sn = paper_source(x, y, pp->kappa, tn);
+                const double Sp = paper_source(x, y, pp->kappa, tnm1); /* S(-dt) at the first step */
+                if (pp->model == 2) collide_bgk(&Lat, gl, u, tau1, post, &phi);
+                else collide_trtr(&Lat, gl, u, tau1, tau2, post, &phi);
+                phi_cur[k] = phi;
+                if (pp->model == 0) {
+                    aux_G(&Lat, phi, u, du, tau1, G);
+                    source_F(&Lat, Sn, u, tau1, Fn);
+                    source_F(&Lat, Sp, u, tau1, Fp);
+                } else {
+                    /* G_i = w_i e_ia / cs^2 (1 - 1/(2 tau1)) d_t(phi u_a), Eq. (15) */
+                    const double dphidt = s > 0 ? (phi - phi_prev[k]) / dt : 0.0;
+                    for (int q = 0; q < Q; ++q) {
+                        const double eu = Lat.e[q][0] * u[0] + Lat.e[q][1] * u[1];
+                        G[q] = WEIGHT[q] * eu / Lat.cs2 * (1.0 - 1.0 / (2.0 * tau1)) * dphidt;
+                        Fn[q] = WEIGHT[q] * Sn; /* Eq. (35) */
+                        Fp[q] = WEIGHT[q] * Sp;
+                    }
+                }
+                for (int q = 0; q < Q; ++q) {
+                    const double v = post[q] + dt * G[q] + dt * Fn[q] + (dt * dt / 2.0) * (Fn[q] - Fp[q]) / dt;
+                    const int it = i + EHAT[q][0], jt = j + EHAT[q][1];
+                    if (it >= 0 && it < n1 && jt >= 0 && jt < n1) gn[PIDX(q, jt, it)] = v;
+                }
+            }
+        memcpy(phi_prev, phi_cur, n * sizeof(double));
+        /* non-equilibrium extrapolation at the boundary nodes */
+        const double t1 = (s + 1) * dt;
+        for (int j = 0; j < n1; ++j)
+            for (int i = 0; i < n1; ++i) {
+                if (i != 0 && i != N && j != 0 && j != N) continue;
+                const int fi = i == 0 ? 1 : (i == N ? N - 1 : i);
+                const int fj = j == 0 ? 1 : (j == N ? N - 1 : j);
+                const double xb = x0 + i * dx, yb = x0 + j * dx, ub[2] = {-yb, xb};
+                const double xf = x0 + fi * dx, yf = x0 + fj * dx, uf[2] = {-yf, xf};
+                double phif = 0.0, geqb[Q], geqf[Q];
+                for (int q = 0; q < Q; ++q) phif += gn[PIDX(q, fj, fi)];
+                equilibrium(&Lat, paper_phi(xb, yb, pp->kappa, t1), ub, geqb);
+                equilibrium(&Lat, phif, uf, geqf);
+                for (int q = 0; q < Q; ++q) gn[PIDX(q, j, i)] = geqb[q] + gn[PIDX(q, fj, fi)] - geqf[q];
+            }
+        double* t = g;
+        g = gn;
+        gn = t;
+        for (size_t k = 0; k < n && !blew; ++k) {
+            double phi = 0.0;
+            for (int q = 0; q < Q; ++q) phi += g[(size_t)q * n + k];
+            if (!isfinite(phi) || fabs(phi) > 1e3) blew = 1;
+        }
+    }
+    double num = 0.0;
+    const double tf = steps * dt;
+    for (int j = 0; j < n1; ++j)
+        for (int i = 0; i < n1; ++i) {
+            double phi = 0.0;
+            for (int q = 0; q < Q; ++q) phi += g[PIDX(q, j, i)];
+            const double d = phi - paper_phi(x0 + i * dx, x0 + j * dx, pp->kappa, tf);
+            num += d * d;
+        }
+#undef PIDX
+    *rms_out = sqrt(num / (double)n);
+    free(g); free(gn); free(phi_prev); free(phi_cur);
+    return blew;
+}
+
+/* The slip check of Sec. 3.2: steady diffusion with a uniform source S between two walls at
+ * y = 0 and y = H = ny dx held at phi_w, in lattice units (dx = dt = 1, u = 0), one column
+ * periodic in x.  Nodes sit at y_j = j + 1/2 (halfway walls); a population that would stream
+ * through a wall returns to its node reversed by the Dirichlet bounce-back rule
+ * g_ibar(x_f, t + 1) = -P_i(x_f, t) + 2 w_i phi_w.  The exact solution of kappa phi'' = -S is
+ * the parabola phi_w + S/(2 kappa) y (H - y), kappa = (tau1 - 1/2) / 3; Eq. (37) names the
+ * tau2 for which the scheme has no slip at the wall.  Steps until max |phi^{n+1} - phi^n| <=
+ * tol (or max_steps); writes the RMS error of Eq. (33) against the parabola and, if phi_out
+ * is not NULL, the ny values of phi.  Returns the number of steps, or -1 on bad input. */
+long oracle_paper_slip(int ny, double tau1, double tau2, double S, double phi_w, long max_steps, double tol,
+                       double* rms_out, double* phi_out) {
+    if (ny < 2 || !(tau1 > 0.5) || !(tau2 > 0.5) || max_steps < 1) return -1;
+    oracle_lattice Lat;
+    lattice_init(&Lat, 1.0, 1.0);
+    const double kappa = (tau1 - 0.5) * Lat.cs2;
+    double* g = (double*)calloc((size_t)Q * ny, sizeof(double));
+    double* post = (double*)calloc((size_t)Q * ny, sizeof(double));
+    double* phi = (double*)calloc((size_t)ny, sizeof(double));
+    if (!g || !post || !phi) {
+        free(g); free(post); free(phi);
+        return -1;
+    }
+    const double u[2] = {0.0, 0.0};
+    for (int j = 0; j < ny; ++j) {
+        double geq[Q];
+        equilibrium(&Lat, phi_w, u, geq);
+        for (int q = 0; q < Q; ++q) g[(size_t)q * ny + j] = geq[q];
+        phi[j] = phi_w;
+    }
+    long s = 0;
+    for (; s < max_steps; ++s) {
+        for (int j = 0; j < ny; ++j) {
+            double gl[Q], pl[Q], p;
+            for (int q = 0; q < Q; ++q) gl[q] = g[(size_t)q * ny + j];
+            collide_trtr(&Lat, gl, u, tau1, tau2, pl, &p);
+            /* u = 0: G = 0 and F_i = w_i S (Eq. (3)); S is steady, so d_t F = 0 */
+            for (int q = 0; q < Q; ++q) post[(size_t)q * ny + j] = pl[q] + WEIGHT[q] * S;
+        }
+        double change = 0.0;
+        for (int j = 0; j < ny; ++j) {
+            double p = 0.0;
+            for (int q = 0; q < Q; ++q) {
+                const int js = j - EHAT[q][1];
+                double v;
+                if (js >= 0 && js < ny) v = post[(size_t)q * ny + js];
+                else v = -post[(size_t)OPPOSITE[q] * ny + j] + 2.0 * WEIGHT[q] * phi_w;
+                g[(size_t)q * ny + j] = v;
+                p += v;
+            }
+            change = fmax(change, fabs(p - phi[j]));
+            phi[j] = p;
+        }
+        if (change <= tol) {
+            ++s;
+            break;
+        }
+    }
+    double num = 0.0;
+    const double H = (double)ny;
+    for (int j = 0; j < ny; ++j) {
+        const double y = j + 0.5, d = phi[j] - (phi_w + S / (2.0 * kappa) * y * (H - y));
+        num += d * d;
+        if (phi_out) phi_out[j] = phi[j];
+    }
+    *rms_out = sqrt(num / ny);
+    free(g); free(post); free(phi);
+    return s;
+}

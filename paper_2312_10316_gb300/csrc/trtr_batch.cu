@@ -71,7 +71,6 @@ __host__ __device__ inline TimeFields<float> time_fields(const Pulse& p, double 
     u.cy_p = (float)(p.xc * sp + p.yc * cp);
     u.inv_s2_p = (float)(1.0 / s2p);
     u.amp_p = (float)(p.sigma0 * p.sigma0 / s2p);
-    u.first_step = n == 0;
     return u;
 }
 

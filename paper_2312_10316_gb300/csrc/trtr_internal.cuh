@@ -96,8 +96,7 @@ struct Store<__nv_bfloat16> {
 template <typename C>
 struct alignas(16) TimeFields {
     C cx_n, cy_n, inv_s2_n, amp_n;     // at t_n
-    C cx_p, cy_p, inv_s2_p, amp_p;     // at t_{n-1}
-    int first_step;         // F^{-1} := F^0
+    C cx_p, cy_p, inv_s2_p, amp_p;     // at t_{n-1} (t = -dt at the first step: the closed form)
 };
 
 // Uniform arguments of the fused step kernel (one launch per time step).  The static part

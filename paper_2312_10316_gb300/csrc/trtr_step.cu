@@ -204,7 +204,6 @@ cudaError_t launch_typed(trtr_ctx* ctx, const CUtensorMap& src_map, void* dst, l
     a.y0 = C(ctx->p.y0);
     a.dx = C(ctx->p.dx);
     a.dt = C(ctx->p.dt);
-    a.tf.first_step = step == 0;
     if (SRC == TRTR_SRC_PULSE) {
         const PulseTime tn = pulse_at(ctx->pulse, (double)step * ctx->p.dt);
         const PulseTime tp = pulse_at(ctx->pulse, (double)(step - 1) * ctx->p.dt);

@@ -333,9 +333,7 @@ __device__ __forceinline__ void tile_row_pairs(const unsigned char* st, int r, i
             const F2 dDx = F2(a.dD_amp * 3.14159265358979323846f * sy) * cxm;
             const F2 dDy = F2(a.dD_amp * 3.14159265358979323846f * cy) * sxm;
             const F2 Sn = pulse_source(x, y, F2(a.tf.cx_n), F2(a.tf.cy_n), F2(a.tf.inv_s2_n), F2(a.tf.amp_n), dD, dDx, dDy);
-            const F2 Sp = a.tf.first_step
-                              ? Sn
-                              : pulse_source(x, y, F2(a.tf.cx_p), F2(a.tf.cy_p), F2(a.tf.inv_s2_p), F2(a.tf.amp_p), dD, dDx, dDy);
+            const F2 Sp = pulse_source(x, y, F2(a.tf.cx_p), F2(a.tf.cy_p), F2(a.tf.inv_s2_p), F2(a.tf.amp_p), dD, dDx, dDy);
             src = F2(a.dt) * vfma(F2(1.5f), Sn, F2(-0.5f) * Sp);
         }
 
@@ -403,8 +401,7 @@ __device__ __forceinline__ void tile_row_f64(const unsigned char* st, int r, int
             const double dDx = a.dD_amp * 3.14159265358979323846 * cx * sy;
             const double dDy = a.dD_amp * 3.14159265358979323846 * sx * cy;
             const double Sn = pulse_source(x, y, a.tf.cx_n, a.tf.cy_n, a.tf.inv_s2_n, a.tf.amp_n, dD, dDx, dDy);
-            const double Sp =
-                a.tf.first_step ? Sn : pulse_source(x, y, a.tf.cx_p, a.tf.cy_p, a.tf.inv_s2_p, a.tf.amp_p, dD, dDx, dDy);
+            const double Sp = pulse_source(x, y, a.tf.cx_p, a.tf.cy_p, a.tf.inv_s2_p, a.tf.amp_p, dD, dDx, dDy);
             src = a.dt * fma(1.5, Sn, -0.5 * Sp);
         }
         double out[kQ];

@@ -51,8 +51,18 @@ MUTANTS = {
     "tau1_cs2_missing": ("return 0.5 + kappa / (L->cs2 * dt);", "return 0.5 + kappa / dt;"),
     "grad_one_sided_wrong": ("du[a][0] = (u[(size_t)j * nx + 1] - u[(size_t)j * nx]) / s->p.dx;",
                              "du[a][0] = (u[(size_t)j * nx + 1] - u[(size_t)j * nx]) / (2.0 * s->p.dx);"),
-    "source_prev_time": ("Snm1 = s->step > 0 ? pulse_source(s, x, y, t_nm1) : Sn;",
-                         "Snm1 = s->step > 0 ? pulse_source(s, x, y, t_n) : Sn;"),
+    "source_prev_time": ("Snm1 = pulse_source(s, x, y, t_nm1); /* closed form",
+                         "Snm1 = pulse_source(s, x, y, t_n); /* closed form"),
+    "nee_interior_phi_exact": ("equilibrium(&Lat, phif, uf, geqf);",
+                               "equilibrium(&Lat, paper_phi(xf, yf, pp->kappa, t1), uf, geqf);"),
+    "bounce_back_sign": ("else v = -post[(size_t)OPPOSITE[q] * ny + j] + 2.0 * WEIGHT[q] * phi_w;",
+                         "else v = post[(size_t)OPPOSITE[q] * ny + j] + 2.0 * WEIGHT[q] * phi_w;"),
+    "bgk_relaxation": ("out[i] = geq[i] + (1.0 - 1.0 / tau) * (g[i] - geq[i]);",
+                       "out[i] = geq[i] + (1.0 - 0.5 / tau) * (g[i] - geq[i]);"),
+    "traditional_G_factor": ("G[q] = WEIGHT[q] * eu / Lat.cs2 * (1.0 - 1.0 / (2.0 * tau1)) * dphidt;",
+                             "G[q] = WEIGHT[q] * eu / Lat.cs2 * dphidt;"),
+    "paper_source_sign": ("return (6.0 * kappa - 4.0 * x * y - 4.0 * kappa",
+                          "return (6.0 * kappa + 4.0 * x * y - 4.0 * kappa"),
     "source_laplacian_sign": ("return -(dDx * gx + dDy * gy + dD * lap);",
                               "return -(dDx * gx + dDy * gy - dD * lap);"),
 }
