@@ -75,6 +75,15 @@ typedef enum { TRTR_GRAD_PERIODIC = 0, TRTR_GRAD_ONESIDED_EDGE = 1 } trtr_grad_m
  * after init and takes F^{-1} := F^0. */
 typedef enum { TRTR_SRC_NONE = 0, TRTR_SRC_FIELD = 1, TRTR_SRC_PULSE = 2 } trtr_src_mode;
 
+/* Boundaries: periodic, or Dirichlet values phi_b held by non-equilibrium extrapolation (the
+ * scheme of the paper's Sec. 3 runs).  With TRTR_BC_DIRICHLET_NEE the edge nodes (i = 0,
+ * nx - 1; j = 0, ny - 1) are boundary nodes: after each step's streaming every population of
+ * edge node b is replaced by g_i^eq(phi_b(b), u(b)) + g_i(f) - g_i^eq(phi(f), u(f)), f the next
+ * node inward along the normal (diagonally at corners), g^eq the third-order Hermite
+ * equilibrium of Eq. (6).  Needs nx, ny >= 3 and trtr_set_dirichlet before stepping; use
+ * TRTR_GRAD_ONESIDED_EDGE for the velocity gradient at the edges. */
+typedef enum { TRTR_BC_PERIODIC = 0, TRTR_BC_DIRICHLET_NEE = 1 } trtr_bc_mode;
+
 typedef struct {
     int nx, ny;         /* nodes, >= 1 each; ny * round_up(nx, 32) < 2^31              */
     double x0, y0;      /* coordinates of node (0, 0)                                  */
@@ -89,6 +98,7 @@ typedef struct {
     int src_mode;       /* trtr_src_mode                                                */
     int check_every;    /* > 0: trtr_step checks every k steps that all populations are
                            finite and returns TRTR_EUNSTABLE if not (synchronises)      */
+    int bc_mode;        /* trtr_bc_mode                                                 */
 } trtr_params;
 
 typedef struct trtr_ctx trtr_ctx; /* opaque, library-owned */
@@ -112,8 +122,22 @@ trtr_status trtr_set_fields(trtr_ctx* ctx, const double* ux, const double* uy, c
                             const double* S, int on_device);
 
 /* TRTR_SRC_FIELD: sets S^n, the source of the next step (Eq. (3)); the source used by the
- * previous step becomes S^{n-1}.  Before the first step after init, S^{n-1} := S^n. */
+ * previous step becomes S^{n-1}.  Before the first step after init, S^{n-1} := S^n unless
+ * trtr_set_source_prev gives it. */
 trtr_status trtr_set_source(trtr_ctx* ctx, const double* S, int on_device);
+
+/* TRTR_SRC_FIELD: sets S^{n-1} of the next step explicitly, for a source known in closed form
+ * at t_n - dt (the d_t F term of Eq. (14) at the first step).  Needs a current source
+ * (trtr_set_source) and is undone by trtr_init_equilibrium / trtr_set_populations, so call it
+ * after those.  S: [ny][nx], host or device. */
+trtr_status trtr_set_source_prev(trtr_ctx* ctx, const double* S, int on_device);
+
+/* TRTR_BC_DIRICHLET_NEE: the boundary values phi_b imposed after each following step's
+ * streaming, i.e. phi at t_{n+1} for the step from t_n.  phi_b: [ny][nx] (host or device);
+ * only the edge nodes are read (copied, so the caller may reuse the array at once; host input
+ * synchronises the stream).  Values stay until set again: call it before every
+ * trtr_step(ctx, 1) for time-dependent values. */
+trtr_status trtr_set_dirichlet(trtr_ctx* ctx, const double* phi_b, int on_device);
 
 /* Rotating, spreading Gaussian pulse (the benchmark family of Sec. 3 on this periodic box):
  * u = omega (-y, x); D = D0 (1 + D_amp sin(pi x) sin(pi y)); phi_a(x, t) =
@@ -181,7 +205,8 @@ trtr_status trtr_launch_count(const trtr_ctx* ctx, long* launches);
  * For J any function of the final phi, dJ/dD(x) through n steps of Eq. (14): the exact
  * derivative of the discrete step (a discrete adjoint), which the paper does not treat.
  * D enters each step through tau1 = 1/2 + 3 D dt/dx^2 (Sec. 2.4) and, with the magic
- * parameter, through tau2 (Eq. (28)).  Scope: S = 0 (src_mode TRTR_SRC_NONE). */
+ * parameter, through tau2 (Eq. (28)).  Scope: S = 0 (src_mode TRTR_SRC_NONE) and periodic
+ * boundaries (TRTR_EINVAL otherwise). */
 
 /* Advances n >= 1 steps from the current state, keeping a copy of the state every
  * `interval` steps (0: ceil(sqrt(n))), and remembers the run for trtr_adjoint.  Allocates
@@ -204,7 +229,7 @@ trtr_status trtr_adjoint(trtr_ctx* ctx, const double* dJ_dphi, int on_device, do
 typedef struct {
     trtr_params p;  /* the instance's lattice and options.  precision: the same for every
                        instance, TRTR_F32, TRTR_F16_OFS or TRTR_BF16_OFS; src_mode: NONE or
-                       PULSE (the manufactured source of its pulse)                        */
+                       PULSE (the manufactured source of its pulse); bc_mode: PERIODIC     */
     double omega, xc, yc, sigma0, D0, D_amp; /* its pulse, as for trtr_set_pulse          */
 } trtr_instance;
 

@@ -52,6 +52,7 @@ class Params(ctypes.Structure):
         ("grad_mode", ctypes.c_int), ("src_mode", ctypes.c_int),
         ("omega", ctypes.c_double), ("xc", ctypes.c_double), ("yc", ctypes.c_double),
         ("sigma0", ctypes.c_double), ("D0", ctypes.c_double), ("D_amp", ctypes.c_double),
+        ("bc_mode", ctypes.c_int),
     ]
 
 
@@ -83,6 +84,8 @@ def load(path: str | None = None):
         "oracle_destroy": (None, [vp]),
         "oracle_set_fields": (None, [vp, _dbl_p, _dbl_p, _dbl_p]),
         "oracle_set_source": (None, [vp, _dbl_p]),
+        "oracle_set_source_prev": (None, [vp, _dbl_p]),
+        "oracle_set_dirichlet": (None, [vp, _dbl_p]),
         "oracle_pulse_source": (None, [vp, ctypes.c_double, _dbl_p]),
         "oracle_init_equilibrium": (None, [vp, _dbl_p]),
         "oracle_step": (None, [vp, ctypes.c_long]),
@@ -98,7 +101,7 @@ def load(path: str | None = None):
                                     ctypes.c_double, ctypes.c_double, ctypes.c_double, _dbl_p]),
         "oracle_pulse_source_at": (ctypes.c_double, [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
         "oracle_adjoint": (ctypes.c_int, [vp, ctypes.c_long, _dbl_p, _dbl_p, _dbl_p]),
-        "oracle_paper_pulse": (ctypes.c_int, [ctypes.POINTER(PaperParams), ctypes.c_double, _dbl_p]),
+        "oracle_paper_pulse": (ctypes.c_int, [ctypes.POINTER(PaperParams), ctypes.c_double, _dbl_p, _dbl_p]),
         "oracle_paper_slip": (ctypes.c_long, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                               ctypes.c_double, ctypes.c_long, ctypes.c_double, _dbl_p, _dbl_p]),
     }
@@ -208,6 +211,7 @@ class SimParams:
     sigma0: float = 0.1
     D0: float = 0.0
     D_amp: float = 0.0
+    bc_mode: int = 0         # 0 periodic, 1 Dirichlet by non-equilibrium extrapolation
 
     def to_c(self) -> Params:
         return Params(**{k: getattr(self, k) for k, _ in Params._fields_})
@@ -249,6 +253,14 @@ class Sim:
     def set_source(self, S):
         S = self._field(S)
         self.lib.oracle_set_source(self.h, _ptr(S))
+
+    def set_source_prev(self, S):
+        S = self._field(S)
+        self.lib.oracle_set_source_prev(self.h, _ptr(S))
+
+    def set_dirichlet(self, phi_b):
+        phi_b = self._field(phi_b)
+        self.lib.oracle_set_dirichlet(self.h, _ptr(phi_b))
 
     def pulse_source(self, t) -> np.ndarray:
         out = np.zeros(self.shape)
@@ -297,7 +309,7 @@ class Sim:
         rc = self.lib.oracle_adjoint(self.h, int(nsteps), _ptr(lamN), _ptr(grad),
                                      _ptr(lam0) if want_lam0 else None)
         if rc != 0:
-            raise MemoryError("oracle_adjoint: out of memory")
+            raise RuntimeError("oracle_adjoint: out of memory, or the boundaries are not periodic")
         return (grad, lam0) if want_lam0 else grad
 
     def mass(self) -> float:
@@ -316,14 +328,19 @@ def num_threads(lib=None) -> int:
 
 
 def paper_pulse(N: int, kappa: float, dt: float, model: int = 0, t_end: float = 1.0, magic: float = 1.0 / 12.0,
-                L: float = 4.0 * np.pi, lib=None):
-    """The paper's rotating-pulse benchmark (Sec. 3) to t_end: (RMS error of Eq. (33), blew_up)."""
+                L: float = 4.0 * np.pi, lib=None, want_phi: bool = False):
+    """The paper's rotating-pulse benchmark (Sec. 3) to t_end: (RMS error of Eq. (33), blew_up)
+    and, with want_phi, phi at t_end ([N + 1][N + 1])."""
     lib = lib or load()
     pp = PaperParams(N, L, kappa, dt, model, magic)
     rms = ctypes.c_double()
-    rc = lib.oracle_paper_pulse(ctypes.byref(pp), float(t_end), ctypes.byref(rms))
+    phi = np.zeros((N + 1, N + 1)) if want_phi else None
+    rc = lib.oracle_paper_pulse(ctypes.byref(pp), float(t_end), ctypes.byref(rms),
+                                _ptr(phi) if want_phi else None)
     if rc < 0:
         raise ValueError("bad benchmark parameters")
+    if want_phi:
+        return rms.value, bool(rc), phi
     return rms.value, bool(rc)
 
 

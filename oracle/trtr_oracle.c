@@ -64,6 +64,7 @@ typedef struct {
     int grad_mode;      /* 0: periodic central differences, 1: one-sided at the edges */
     int src_mode;       /* 0: S = 0, 1: given field, 2: manufactured pulse source */
     double omega, xc, yc, sigma0, D0, D_amp; /* pulse parameters (src_mode 2) */
+    int bc_mode;        /* 0: periodic, 1: Dirichlet by non-equilibrium extrapolation (Sec. 3) */
 } oracle_params;
 
 /* Lattice constants and Hermite tensors in physical units (Sec. 2.2, text after Eq. (10)):
@@ -242,6 +243,7 @@ typedef struct {
     double *ux, *uy, *D;       /* physical fields */
     double *S_cur, *S_prev;    /* src_mode 1: S used at this step and at the previous one */
     int S_prev_valid;          /* 0 right after init: F^{-1} := F^0 */
+    double* phi_b;             /* bc_mode 1: Dirichlet values; only the edge nodes are read */
     long step;
 } oracle_sim;
 
@@ -249,6 +251,7 @@ typedef struct {
 
 oracle_sim* oracle_create(const oracle_params* p) {
     if (p->nx < 1 || p->ny < 1 || !(p->dx > 0.0) || !(p->dt > 0.0)) return NULL;
+    if (p->bc_mode == 1 && (p->nx < 3 || p->ny < 3)) return NULL;
     oracle_sim* s = (oracle_sim*)calloc(1, sizeof(oracle_sim));
     if (!s) return NULL;
     s->p = *p;
@@ -261,8 +264,10 @@ oracle_sim* oracle_create(const oracle_params* p) {
     s->D = (double*)calloc(s->n, sizeof(double));
     s->S_cur = (double*)calloc(s->n, sizeof(double));
     s->S_prev = (double*)calloc(s->n, sizeof(double));
-    if (!s->g || !s->gnext || !s->ux || !s->uy || !s->D || !s->S_cur || !s->S_prev) {
+    s->phi_b = (double*)calloc(s->n, sizeof(double));
+    if (!s->g || !s->gnext || !s->ux || !s->uy || !s->D || !s->S_cur || !s->S_prev || !s->phi_b) {
         free(s->g); free(s->gnext); free(s->ux); free(s->uy); free(s->D); free(s->S_cur); free(s->S_prev);
+        free(s->phi_b);
         free(s);
         return NULL;
     }
@@ -272,6 +277,7 @@ oracle_sim* oracle_create(const oracle_params* p) {
 void oracle_destroy(oracle_sim* s) {
     if (!s) return;
     free(s->g); free(s->gnext); free(s->ux); free(s->uy); free(s->D); free(s->S_cur); free(s->S_prev);
+    free(s->phi_b);
     free(s);
 }
 
@@ -284,6 +290,16 @@ void oracle_set_fields(oracle_sim* s, const double* ux, const double* uy, const 
 
 /* src_mode 1: S for the next step.  The previous step's S stays as S^{n-1}. */
 void oracle_set_source(oracle_sim* s, const double* S) { memcpy(s->S_cur, S, s->n * sizeof(double)); }
+
+/* src_mode 1: S^{n-1} for the next step (a closed-form source known at t_n - dt). */
+void oracle_set_source_prev(oracle_sim* s, const double* S) {
+    memcpy(s->S_prev, S, s->n * sizeof(double));
+    s->S_prev_valid = 1;
+}
+
+/* bc_mode 1: the Dirichlet values phi_b(x) imposed after the next step's streaming ([ny][nx];
+ * only the edge nodes are read). */
+void oracle_set_dirichlet(oracle_sim* s, const double* phi_b) { memcpy(s->phi_b, phi_b, s->n * sizeof(double)); }
 
 static double node_x(const oracle_sim* s, int i) { return s->p.x0 + (double)i * s->p.dx; }
 static double node_y(const oracle_sim* s, int j) { return s->p.y0 + (double)j * s->p.dx; }
@@ -431,6 +447,26 @@ void oracle_node_post(const oracle_params* p, const double* g, double ux, double
 /* Manufactured pulse source at one point (src_mode 2 closed form). */
 double oracle_pulse_source_at(const oracle_sim* s, double x, double y, double t) { return pulse_source(s, x, y, t); }
 
+/* bc_mode 1 (Sec. 3): at every edge node x_b the streamed populations are replaced by
+ * g_i(x_b) = g_i^eq(phi_b(x_b), u(x_b)) + g_i(x_f) - g_i^eq(phi(x_f), u(x_f)), x_f the next node
+ * inward along the normal (diagonally at corners); every edge node takes all nine. */
+static void dirichlet_nee(oracle_sim* s) {
+    const int nx = s->p.nx, ny = s->p.ny;
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            if (i != 0 && i != nx - 1 && j != 0 && j != ny - 1) continue;
+            const int fi = i == 0 ? 1 : (i == nx - 1 ? nx - 2 : i);
+            const int fj = j == 0 ? 1 : (j == ny - 1 ? ny - 2 : j);
+            const size_t kb = (size_t)j * nx + i, kf = (size_t)fj * nx + fi;
+            const double ub[2] = {s->ux[kb], s->uy[kb]}, uf[2] = {s->ux[kf], s->uy[kf]};
+            double phif = 0.0, geqb[Q], geqf[Q];
+            for (int q = 0; q < Q; ++q) phif += s->g[AT(s, q, fj, fi)];
+            equilibrium(&s->L, s->phi_b[kb], ub, geqb);
+            equilibrium(&s->L, phif, uf, geqf);
+            for (int q = 0; q < Q; ++q) s->g[AT(s, q, j, i)] = geqb[q] + s->g[AT(s, q, fj, fi)] - geqf[q];
+        }
+}
+
 void oracle_step(oracle_sim* s, long nsteps) {
     for (long n = 0; n < nsteps; ++n) {
         const double t_n = (double)s->step * s->p.dt;
@@ -439,6 +475,7 @@ void oracle_step(oracle_sim* s, long nsteps) {
         double* tmp = s->g;
         s->g = s->gnext;
         s->gnext = tmp;
+        if (s->p.bc_mode == 1) dirichlet_nee(s);
         if (s->p.src_mode == 1) {
             memcpy(s->S_prev, s->S_cur, s->n * sizeof(double));
             s->S_prev_valid = 1;
@@ -578,8 +615,9 @@ static void node_sources(const oracle_sim* s, int i, int j, const double* Scur, 
  * A(x) is built column by column from the node map applied to unit vectors minus its value
  * at zero (the map is affine in g).  src_mode 1 keeps one source field for every step.
  * Outputs grad [ny][nx] (dJ/dD) and, if lam0 is not NULL, lam0 [9][ny][nx] = dJ/dg^0.
- * Returns 0, or -1 if memory runs out. */
+ * Returns 0, or -1 if memory runs out or the boundaries are not periodic (bc_mode 1). */
 int oracle_adjoint(oracle_sim* s, long nsteps, const double* lamN, double* grad, double* lam0) {
+    if (s->p.bc_mode != 0) return -1;
     const int nx = s->p.nx, ny = s->p.ny;
     const size_t n = s->n, st = Q * n;
     double* states = (double*)malloc((size_t)(nsteps + 1) * st * sizeof(double));
@@ -714,8 +752,9 @@ static void collide_bgk(const oracle_lattice* L, const double g[Q], const double
 }
 
 /* Runs the benchmark to t_end (round(t_end / dt) steps).  Writes the RMS error of Eq. (33)
- * at t_end; returns 0, 1 if the run blew up (non-finite or |phi| > 1e3), -1 on bad input. */
-int oracle_paper_pulse(const oracle_paper_params* pp, double t_end, double* rms_out) {
+ * at t_end and, if phi_out is not NULL, phi there ([N + 1][N + 1], x fastest); returns 0, 1 if
+ * the run blew up (non-finite or |phi| > 1e3), -1 on bad input. */
+int oracle_paper_pulse(const oracle_paper_params* pp, double t_end, double* rms_out, double* phi_out) {
     const int N = pp->N, n1 = N + 1;
     if (N < 2 || !(pp->dt > 0.0) || !(pp->L > 0.0)) return -1;
     const double dx = pp->L / N, dt = pp->dt, x0 = -pp->L / 2.0;
@@ -812,6 +851,7 @@ int oracle_paper_pulse(const oracle_paper_params* pp, double t_end, double* rms_
             for (int q = 0; q < Q; ++q) phi += g[PIDX(q, j, i)];
             const double d = phi - paper_phi(x0 + i * dx, x0 + j * dx, pp->kappa, tf);
             num += d * d;
+            if (phi_out) phi_out[(size_t)j * n1 + i] = phi;
         }
 #undef PIDX
     *rms_out = sqrt(num / (double)n);

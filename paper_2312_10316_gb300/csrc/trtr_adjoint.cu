@@ -204,6 +204,8 @@ trtr_status trtr_forward_record(trtr_ctx* ctx, long steps, int interval) {
     if (steps < 1 || interval < 0) return adj_fail(ctx, TRTR_EINVAL, "steps >= 1 and interval >= 0 required");
     if (!ctx->initialized) return adj_fail(ctx, TRTR_ESTATE, "populations not initialised");
     if (ctx->p.src_mode != TRTR_SRC_NONE) return adj_fail(ctx, TRTR_EINVAL, "the adjoint supports S = 0 only");
+    if (ctx->p.bc_mode != TRTR_BC_PERIODIC)
+        return adj_fail(ctx, TRTR_EINVAL, "the adjoint supports periodic boundaries only");
     trtr::free_adjoint(ctx);
     trtr_adjoint_state* a = new (std::nothrow) trtr_adjoint_state();
     if (!a) return TRTR_ENOMEM;

@@ -13,7 +13,7 @@
 
 namespace {
 
-constexpr int kAbiVersion = 1;
+constexpr int kAbiVersion = 2;
 constexpr uint64_t kSaveMagic = 0x3152545254ULL;  // "TRTR1"
 
 struct SaveHeader {
@@ -175,6 +175,8 @@ trtr_status trtr_create(const trtr_params* p, void* cuda_stream, trtr_ctx** out)
     if (p->grad_mode != TRTR_GRAD_PERIODIC && p->grad_mode != TRTR_GRAD_ONESIDED_EDGE) return TRTR_EINVAL;
     if (p->src_mode < TRTR_SRC_NONE || p->src_mode > TRTR_SRC_PULSE) return TRTR_EINVAL;
     if (p->check_every < 0 || !isfinite(p->phi_ref)) return TRTR_EINVAL;
+    if (p->bc_mode != TRTR_BC_PERIODIC && p->bc_mode != TRTR_BC_DIRICHLET_NEE) return TRTR_EINVAL;
+    if (p->bc_mode == TRTR_BC_DIRICHLET_NEE && (p->nx < 3 || p->ny < 3)) return TRTR_EINVAL;
     const trtr::PlaneLayout lp = trtr::make_layout(p->nx, p->ny, (int)es);
     const trtr::PlaneLayout lf = trtr::make_layout(p->nx, p->ny, p->precision == TRTR_F64 ? 8 : 4);
     if ((long long)trtr::kQ * (long long)lp.plane >= (1LL << 31) || 2LL * (long long)lf.plane >= (1LL << 31))
@@ -217,6 +219,8 @@ trtr_status trtr_create(const trtr_params* p, void* cuda_stream, trtr_ctx** out)
         {(void**)&ctx->scratch, 2 * (size_t)ctx->red_blocks * sizeof(double), false},
         {(void**)&ctx->dres, 4 * sizeof(double), false},
         {(void**)&ctx->dflag, sizeof(int), true},
+        {(void**)&ctx->phib,
+         p->bc_mode == TRTR_BC_DIRICHLET_NEE ? (size_t)trtr::edge_count(p->nx, p->ny) * sizeof(double) : 0, true},
     };
     for (auto& a : allocs) {
         if (a.bytes == 0) continue;
@@ -251,8 +255,8 @@ trtr_status trtr_destroy(trtr_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     cudaGetLastError();
     trtr::free_adjoint(ctx);
-    void* ptrs[] = {ctx->pop[0], ctx->pop[1], ctx->uv,      ctx->Dh,   ctx->S,     ctx->tab_x,
-                    ctx->tab_y,  ctx->scratch, ctx->dres, ctx->dflag, ctx->dtmp};
+    void* ptrs[] = {ctx->pop[0], ctx->pop[1],  ctx->uv,   ctx->Dh,    ctx->S,    ctx->tab_x,
+                    ctx->tab_y,  ctx->scratch, ctx->dres, ctx->dflag, ctx->dtmp, ctx->phib};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (ctx->hres) cudaFreeHost(ctx->hres);
@@ -275,6 +279,49 @@ static trtr_status set_source_impl(trtr_ctx* ctx, const double* S, int on_device
     s = check_launch(ctx, trtr::launch_convert_source(ctx, dev, dst), "source conversion");
     if (s != TRTR_OK) return s;
     ctx->S_cur = dst;
+    return TRTR_OK;
+}
+
+trtr_status trtr_set_source_prev(trtr_ctx* ctx, const double* S, int on_device) {
+    if (!ctx) return TRTR_EINVAL;
+    if (!S) return fail(ctx, TRTR_EINVAL, "S is NULL");
+    if (ctx->p.src_mode != TRTR_SRC_FIELD) return fail(ctx, TRTR_EINVAL, "src_mode is not FIELD");
+    if (ctx->S_cur < 0) return fail(ctx, TRTR_ESTATE, "set the current source (trtr_set_source) first");
+    const size_t n = n_nodes(ctx);
+    const int dst = ctx->S_cur ^ 1;
+    const double* dev = nullptr;
+    trtr_status s = on_device ? TRTR_OK : ensure_tmp(ctx, n);
+    if (s == TRTR_OK) s = stage_in(ctx, S, n, on_device, 0, &dev);
+    if (s != TRTR_OK) return s;
+    s = check_launch(ctx, trtr::launch_convert_source(ctx, dev, dst), "source conversion");
+    if (s != TRTR_OK) return s;
+    ctx->S_prev = dst;
+    return TRTR_OK;
+}
+
+trtr_status trtr_set_dirichlet(trtr_ctx* ctx, const double* phi_b, int on_device) {
+    if (!ctx) return TRTR_EINVAL;
+    if (!phi_b) return fail(ctx, TRTR_EINVAL, "phi_b is NULL");
+    if (ctx->p.bc_mode != TRTR_BC_DIRICHLET_NEE) return fail(ctx, TRTR_EINVAL, "bc_mode is not DIRICHLET_NEE");
+    const int nx = ctx->p.nx, ny = ctx->p.ny, nb = trtr::edge_count(nx, ny);
+    if (on_device) {
+        trtr_status s = check_launch(ctx, trtr::launch_gather_edges(ctx, phi_b), "edge gather");
+        if (s != TRTR_OK) return s;
+    } else {
+        // gathered on the host; the copy is ordered after the kernels already on the stream
+        double* edge = (double*)malloc((size_t)nb * sizeof(double));
+        if (!edge) return fail(ctx, TRTR_ENOMEM, "host memory");
+        for (int k = 0; k < nb; ++k) {
+            int i, j;
+            trtr::edge_node(k, nx, ny, &i, &j);
+            edge[k] = phi_b[(size_t)j * nx + i];
+        }
+        cudaError_t e = cudaMemcpyAsync(ctx->phib, edge, (size_t)nb * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        free(edge);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "edge values copy");
+    }
+    ctx->dirichlet_set = true;
     return TRTR_OK;
 }
 
@@ -360,10 +407,17 @@ trtr_status trtr_step(trtr_ctx* ctx, long n) {
         return fail(ctx, TRTR_ESTATE, "src_mode FIELD needs a source (trtr_set_source)");
     if (ctx->p.src_mode == TRTR_SRC_PULSE && !ctx->pulse_set)
         return fail(ctx, TRTR_ESTATE, "src_mode PULSE needs trtr_set_pulse");
+    const bool nee = ctx->p.bc_mode == TRTR_BC_DIRICHLET_NEE;
+    if (nee && !ctx->dirichlet_set)
+        return fail(ctx, TRTR_ESTATE, "bc_mode DIRICHLET_NEE needs boundary values (trtr_set_dirichlet)");
     for (long k = 0; k < n; ++k) {
         cudaError_t e = trtr::launch_step(ctx);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "step launch");
         ctx->launches += 1;
+        if (nee) {
+            e = trtr::launch_dirichlet(ctx, ctx->pop[ctx->cur ^ 1]);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "boundary launch");
+        }
         ctx->cur ^= 1;
         ctx->step += 1;
         if (ctx->p.src_mode == TRTR_SRC_FIELD) ctx->S_prev = ctx->S_cur;

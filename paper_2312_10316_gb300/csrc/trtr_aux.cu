@@ -119,9 +119,16 @@ __device__ __forceinline__ double pulse_phi(const PulseTime& pt, double x, doubl
     return pt.amp * exp(-0.5 * (rx * rx + ry * ry) * pt.inv_s2);
 }
 
-// Initial condition g_i(x) = g_i^eq(phi0(x), u(x)) stored in the pull layout:
-// P_i(x) = g_i(x + e_i).  Third-order Hermite equilibrium (Eq. (6)) in lattice units:
+// Third-order Hermite equilibrium (Eq. (6)) in lattice units, in FP64:
 // w_i phi [1 + 3 eu + 4.5 ((eu)^2 - |u|^2/3) + 4.5 ((eu)^3 - eu |u|^2)], eu = e_i . uhat.
+__device__ __forceinline__ double equilibrium(int q, double phi, double u, double v) {
+    const double eu = c_ex[q] * u + c_ey[q] * v;
+    const double uu = u * u + v * v;
+    return c_w[q] * phi * (1.0 + 3.0 * eu + 4.5 * (eu * eu - uu / 3.0) + 4.5 * (eu * eu * eu - eu * uu));
+}
+
+// Initial condition g_i(x) = g_i^eq(phi0(x), u(x)) stored in the pull layout:
+// P_i(x) = g_i(x + e_i).
 template <typename S, typename C>
 __global__ void init_eq_kernel(S* P, const C* uv, const double* phi0, PlaneLayout lp, PlaneLayout lf, double x0,
                                double y0, double dx, PulseTime pt, C phi_ref) {
@@ -132,22 +139,59 @@ __global__ void init_eq_kernel(S* P, const C* uv, const double* phi0, PlaneLayou
         for (int q = 0; q < kQ; ++q) {
             const int si = wrap(i + c_ex[q], nx), sj = wrap(j + c_ey[q], ny);
             const double phi = phi0 ? phi0[(size_t)sj * nx + si] : pulse_phi(pt, x0 + si * dx, y0 + sj * dx);
-            const double u = (double)uv[lf.at(si, sj)];
-            const double v = (double)uv[lf.plane + lf.at(si, sj)];
-            const double eu = c_ex[q] * u + c_ey[q] * v;
-            const double uu = u * u + v * v;
-            const double geq =
-                c_w[q] * phi * (1.0 + 3.0 * eu + 4.5 * (eu * eu - uu / 3.0) + 4.5 * (eu * eu * eu - eu * uu));
+            const double geq = equilibrium(q, phi, (double)uv[lf.at(si, sj)], (double)uv[lf.plane + lf.at(si, sj)]);
             store_with_ghosts(P + q * lp.plane, lp, i, j, Store<S>::encode((C)geq, (C)(c_w[q]) * phi_ref));
         }
     }
 }
 
-// g_i(x, t_n) = P_i(x - e_i), decoded to the compute type.
+// Dirichlet boundary by non-equilibrium extrapolation (Sec. 3) over the buffer P that a step
+// has just written.  For edge node b and its inward neighbour f (diagonal at corners):
+//   g_i(b) = g_i^eq(phi_b, u_b) + g_i(f) - g_i^eq(phi(f), u_f),  g_i(f) = P_i(f - e_i),
+// stored where b pulls it, P_i(b - e_i) (a ghost cell when b - e_i is outside the grid).  A
+// slot P_i(y) is pulled by the node y + e_i alone, so the slots written here (pulled by edge
+// nodes) and the slots read (pulled by interior nodes f) are disjoint: no thread ordering.
+template <typename S, typename C>
+__global__ void dirichlet_nee_kernel(S* P, const C* uv, const double* phib, PlaneLayout lp, PlaneLayout lf,
+                                     C phi_ref) {
+    const int nx = lp.nx, ny = lp.ny, nb = edge_count(nx, ny);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+        int i, j;
+        edge_node(k, nx, ny, &i, &j);
+        const int fi = i == 0 ? 1 : (i == nx - 1 ? nx - 2 : i);
+        const int fj = j == 0 ? 1 : (j == ny - 1 ? ny - 2 : j);
+        double gf[kQ], phif = 0.0;
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            gf[q] = (double)Store<S>::decode(P[q * lp.plane + lp.at(fi - c_ex[q], fj - c_ey[q])],
+                                             (C)(c_w[q]) * phi_ref);
+            phif += gf[q];
+        }
+        const double ub = (double)uv[lf.at(i, j)], vb = (double)uv[lf.plane + lf.at(i, j)];
+        const double uf = (double)uv[lf.at(fi, fj)], vf = (double)uv[lf.plane + lf.at(fi, fj)];
+        const double phi_b = phib[k];
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            const double g = equilibrium(q, phi_b, ub, vb) + gf[q] - equilibrium(q, phif, uf, vf);
+            P[q * lp.plane + lp.at(i - c_ex[q], j - c_ey[q])] = Store<S>::encode((C)g, (C)(c_w[q]) * phi_ref);
+        }
+    }
+}
+
+__global__ void gather_edges_kernel(double* phib, const double* phi, int nx, int ny) {
+    const int nb = edge_count(nx, ny);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+        int i, j;
+        edge_node(k, nx, ny, &i, &j);
+        phib[k] = phi[(size_t)j * nx + i];
+    }
+}
+
+// g_i(x, t_n) = P_i(x - e_i), decoded to the compute type.  x - e_i may be a ghost cell: it
+// holds the periodic image, or the Dirichlet pass's value (TRTR_BC_DIRICHLET_NEE).
 template <typename S, typename C>
 __device__ __forceinline__ C pulled(const S* P, int q, int i, int j, const PlaneLayout& L, C phi_ref) {
-    const int si = wrap(i - c_ex[q], L.nx), sj = wrap(j - c_ey[q], L.ny);
-    return Store<S>::decode(P[q * L.plane + L.at(si, sj)], (C)(c_w[q]) * phi_ref);
+    return Store<S>::decode(P[q * L.plane + L.at(i - c_ex[q], j - c_ey[q])], (C)(c_w[q]) * phi_ref);
 }
 
 template <typename S, typename C>
@@ -397,6 +441,25 @@ cudaError_t launch_sample(trtr_ctx* ctx, const long* nodes, int count, double* o
         using C = std::remove_pointer_t<decltype(cp)>;
         sample_kernel<S, C><<<(total + kThreads - 1) / kThreads, kThreads, 0, ctx->stream>>>(
             out, nodes, count, (const S*)ctx->pop[ctx->cur], ctx->lp, (C)ctx->p.phi_ref);
+    });
+}
+
+cudaError_t launch_gather_edges(trtr_ctx* ctx, const double* phi_b) {
+    const int nb = edge_count(ctx->p.nx, ctx->p.ny);
+    ctx->launches += 1;
+    gather_edges_kernel<<<(nb + kThreads - 1) / kThreads, kThreads, 0, ctx->stream>>>(ctx->phib, phi_b, ctx->p.nx,
+                                                                                      ctx->p.ny);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dirichlet(trtr_ctx* ctx, void* P) {
+    const int nb = edge_count(ctx->p.nx, ctx->p.ny);
+    ctx->launches += 1;
+    return dispatch(ctx, [&](auto* sp, auto* cp) {
+        using S = std::remove_pointer_t<decltype(sp)>;
+        using C = std::remove_pointer_t<decltype(cp)>;
+        dirichlet_nee_kernel<S, C><<<(nb + kThreads - 1) / kThreads, kThreads, 0, ctx->stream>>>(
+            (S*)P, (const C*)ctx->uv, ctx->phib, ctx->lp, ctx->lf, (C)ctx->p.phi_ref);
     });
 }
 

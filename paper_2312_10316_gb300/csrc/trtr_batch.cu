@@ -475,7 +475,7 @@ trtr_status trtr_batch_create(const trtr_instance* inst, int count, void* cuda_s
     int src = TRTR_SRC_NONE;
     for (int k = 0; k < count; ++k) {
         if (inst[k].p.precision != prec) return TRTR_EINVAL;
-        if (inst[k].p.src_mode == TRTR_SRC_FIELD) return TRTR_EINVAL;
+        if (inst[k].p.src_mode == TRTR_SRC_FIELD || inst[k].p.bc_mode != TRTR_BC_PERIODIC) return TRTR_EINVAL;
         if (inst[k].p.src_mode == TRTR_SRC_PULSE) src = TRTR_SRC_PULSE;
     }
     trtr_batch* b = new (std::nothrow) trtr_batch();

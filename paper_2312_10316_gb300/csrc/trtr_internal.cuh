@@ -17,6 +17,8 @@
 //                central difference at the edge node equals the one-sided difference.
 //   source       [2][rows][pitch] dt*S in the compute type (TRTR_SRC_FIELD only)
 //   pulse tab    [2][nx] sin(pi x_i), cos(pi x_i) and [2][ny] sin(pi y_j), cos(pi y_j)
+//   edge values  [2 nx + 2 (ny - 2)] FP64 Dirichlet values of the edge nodes
+//                (TRTR_BC_DIRICHLET_NEE), in the order of edge_node()
 //   scratch      FP64 partial sums of the reductions, one pair per reduction block
 //   flag         device int set by a kernel whose bounded wait gave up
 // rows >= ny + 2 and pitch >= nx + 2 gx are padded so that every TMA box fits inside the
@@ -153,7 +155,8 @@ struct trtr_ctx {
     int* dflag;       // device timeout flag
     double* dtmp;     // device staging for double I/O
     size_t dtmp_len;  // in doubles
-    bool fields_set, pulse_set, initialized, maps_ready;
+    double* phib;     // Dirichlet values of the edge nodes (TRTR_BC_DIRICHLET_NEE)
+    bool fields_set, pulse_set, initialized, maps_ready, dirichlet_set;
     trtr::Pulse pulse;
     long step;
     long launches;
@@ -180,10 +183,24 @@ cudaError_t launch_reduce(trtr_ctx* ctx, int kind, const double* phi_ref_dev);
 cudaError_t launch_get_populations(trtr_ctx* ctx, double* g_dev);
 cudaError_t launch_set_populations(trtr_ctx* ctx, const double* g_dev);
 cudaError_t launch_sample(trtr_ctx* ctx, const long* nodes_dev, int count, double* out_dev);
+// TRTR_BC_DIRICHLET_NEE: edge values from a device [ny][nx] array, and the boundary pass over
+// the population buffer P that a step has just written
+cudaError_t launch_gather_edges(trtr_ctx* ctx, const double* phi_b_dev);
+cudaError_t launch_dirichlet(trtr_ctx* ctx, void* P);
 
 enum ReduceKind { kReduceMass = 0, kReducePulse = 1, kReduceField = 2, kReduceNonFinite = 3 };
 
 PulseTime pulse_at(const Pulse& p, double t);
+
+// Edge nodes of an nx x ny grid (nx, ny >= 3), k in [0, 2 nx + 2 (ny - 2)): the bottom row,
+// the top row, then the left and right columns without their corners.
+__host__ __device__ inline int edge_count(int nx, int ny) { return 2 * nx + 2 * (ny - 2); }
+__host__ __device__ inline void edge_node(int k, int nx, int ny, int* i, int* j) {
+    if (k < nx) { *i = k; *j = 0; }
+    else if (k < 2 * nx) { *i = k - nx; *j = ny - 1; }
+    else if (k < 2 * nx + ny - 2) { *i = 0; *j = 1 + (k - 2 * nx); }
+    else { *i = nx - 1; *j = 1 + (k - 2 * nx - (ny - 2)); }
+}
 
 // D2Q9 in the library's order: 0:(0,0) 1:(1,0) 2:(-1,0) 3:(0,1) 4:(0,-1) 5:(1,1) 6:(-1,-1)
 // 7:(1,-1) 8:(-1,1).

@@ -22,6 +22,7 @@ TRTR_F64, TRTR_F32, TRTR_F16_OFS, TRTR_BF16_OFS = range(4)
 TRTR_TAU2_MAGIC, TRTR_TAU2_FIXED = range(2)
 TRTR_GRAD_PERIODIC, TRTR_GRAD_ONESIDED_EDGE = range(2)
 TRTR_SRC_NONE, TRTR_SRC_FIELD, TRTR_SRC_PULSE = range(3)
+TRTR_BC_PERIODIC, TRTR_BC_DIRICHLET_NEE = range(2)
 
 PRECISIONS = {"f64": TRTR_F64, "f32": TRTR_F32, "f16": TRTR_F16_OFS, "bf16": TRTR_BF16_OFS}
 
@@ -42,6 +43,7 @@ class trtr_params(ctypes.Structure):
         ("tau1_const", ctypes.c_double),
         ("grad_mode", ctypes.c_int), ("src_mode", ctypes.c_int),
         ("check_every", ctypes.c_int),
+        ("bc_mode", ctypes.c_int),
     ]
 
 
@@ -59,6 +61,8 @@ _SIGNATURES = {
     "trtr_destroy": (_st, [_vp]),
     "trtr_set_fields": (_st, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int]),
     "trtr_set_source": (_st, [_vp, _vp, ctypes.c_int]),
+    "trtr_set_source_prev": (_st, [_vp, _vp, ctypes.c_int]),
+    "trtr_set_dirichlet": (_st, [_vp, _vp, ctypes.c_int]),
     "trtr_set_pulse": (_st, [_vp] + [ctypes.c_double] * 6),
     "trtr_init_equilibrium": (_st, [_vp, _vp, ctypes.c_int]),
     "trtr_step": (_st, [_vp, ctypes.c_long]),
@@ -175,6 +179,16 @@ def trtr_set_fields(ctx, n: int, ux, uy, D=None, S=None):
 def trtr_set_source(ctx, n: int, S):
     p, d, k = _arr(S, n)
     _check(ctx, lib.trtr_set_source(ctx, p, d))
+
+
+def trtr_set_source_prev(ctx, n: int, S):
+    p, d, k = _arr(S, n)
+    _check(ctx, lib.trtr_set_source_prev(ctx, p, d))
+
+
+def trtr_set_dirichlet(ctx, n: int, phi_b):
+    p, d, k = _arr(phi_b, n)
+    _check(ctx, lib.trtr_set_dirichlet(ctx, p, d))
 
 
 def trtr_set_pulse(ctx, omega, xc, yc, sigma0, D0, D_amp):
@@ -337,6 +351,7 @@ class Params:
     grad_mode: int = TRTR_GRAD_ONESIDED_EDGE
     src_mode: int = TRTR_SRC_NONE
     check_every: int = 0
+    bc_mode: int = TRTR_BC_PERIODIC
 
     def to_c(self) -> trtr_params:
         return trtr_params(**{f.name: getattr(self, f.name) for f in dc_fields(self)})
@@ -372,6 +387,12 @@ class Solver:
 
     def set_source(self, S):
         trtr_set_source(self.ctx, self.n, S)
+
+    def set_source_prev(self, S):
+        trtr_set_source_prev(self.ctx, self.n, S)
+
+    def set_dirichlet(self, phi_b):
+        trtr_set_dirichlet(self.ctx, self.n, phi_b)
 
     def set_pulse(self, omega, xc, yc, sigma0, D0, D_amp=0.0):
         trtr_set_pulse(self.ctx, omega, xc, yc, sigma0, D0, D_amp)

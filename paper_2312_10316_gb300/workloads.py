@@ -194,3 +194,72 @@ def batch_instances(seed: int = 0, count: int = 256, sizes=(64, 128, 256, 512, 1
         out.append(BatchInstance(p, off))
         off += n * n
     return out
+
+
+# --- The paper's own benchmark (Sec. 3, Table 2) -------------------------------------------
+#
+# Rigid rotation u = (-y, x) on [-2 pi, 2 pi]^2 with constant kappa; Table 2 reports t = 1.
+# The closed form
+#     phi_a(x, y, t) = exp(-(x^2 + 3 y^2 + 2 kappa t)),
+#     S(x, y, t) = [6 kappa - 4 x y - 4 kappa (x^2 + 9 y^2)] exp(-(x^2 + 3 y^2 + 2 kappa t)),
+# held on the boundary by Dirichlet conditions.  Nodes: N intervals per side, N + 1 nodes
+# including both edges, dx = L / N; Table 2's diffusive scaling is (dx)^2 / dt = 0.16 pi^2.
+
+
+@dataclass(frozen=True)
+class PaperPulse:
+    N: int                      # intervals per side
+    kappa: float
+    L: float = 4.0 * math.pi
+    dt: float | None = None     # None: Table 2's scaling (dx)^2 / dt = 0.16 pi^2
+    t_end: float = 1.0
+
+    @property
+    def nx(self) -> int:
+        return self.N + 1
+
+    @property
+    def ny(self) -> int:
+        return self.N + 1
+
+    @property
+    def x0(self) -> float:
+        return -self.L / 2.0
+
+    @property
+    def y0(self) -> float:
+        return -self.L / 2.0
+
+    @property
+    def dx(self) -> float:
+        return self.L / self.N
+
+    @property
+    def time_step(self) -> float:
+        return self.dt if self.dt is not None else self.dx**2 / (0.16 * math.pi**2)
+
+    @property
+    def steps(self) -> int:
+        return int(round(self.t_end / self.time_step))
+
+
+def paper_coords(p: PaperPulse) -> tuple[np.ndarray, np.ndarray]:
+    x = p.x0 + np.arange(p.nx) * p.dx
+    y = p.y0 + np.arange(p.ny) * p.dx
+    return np.meshgrid(x, y, indexing="xy")
+
+
+def paper_fields(p: PaperPulse) -> dict[str, np.ndarray]:
+    X, Y = paper_coords(p)
+    return {"ux": -Y, "uy": X.copy(), "D": np.full_like(X, p.kappa), "phi0": paper_phi(p, 0.0)}
+
+
+def paper_phi(p: PaperPulse, t: float) -> np.ndarray:
+    X, Y = paper_coords(p)
+    return np.exp(-(X * X + 3.0 * Y * Y + 2.0 * p.kappa * t))
+
+
+def paper_source(p: PaperPulse, t: float) -> np.ndarray:
+    X, Y = paper_coords(p)
+    k = p.kappa
+    return (6.0 * k - 4.0 * X * Y - 4.0 * k * (X * X + 9.0 * Y * Y)) * np.exp(-(X * X + 3.0 * Y * Y + 2.0 * k * t))

@@ -600,6 +600,29 @@ def pin_table2_comparison_models(lib):
             assert not blew and e2 < 0.05, (model, N, e2)
 
 
+def pin_dirichlet_field_path_matches_benchmark(lib):
+    """The simulator's Dirichlet mode (non-equilibrium extrapolation at the edge nodes, bc_mode
+    1), fed the benchmark's closed forms step by step (source field with S^{-1} = S(-dt), edge
+    values phi_a(t_{n+1}), finite-difference velocity gradients), reproduces the Sec. 3
+    benchmark run, whose RMS errors are pinned to Table 2, node by node."""
+    for N in (20, 40):
+        pp = W.PaperPulse(N=N, kappa=0.01)
+        _, _, phi_ref = oracle.paper_pulse(N, pp.kappa, pp.time_step, 0, lib=lib, want_phi=True)
+        f = W.paper_fields(pp)
+        sim = oracle.Sim(oracle.SimParams(nx=pp.nx, ny=pp.ny, x0=pp.x0, y0=pp.y0, dx=pp.dx, dt=pp.time_step,
+                                          grad_mode=1, src_mode=1, bc_mode=1), lib)
+        sim.set_fields(f["ux"], f["uy"], f["D"])
+        sim.init_equilibrium(f["phi0"])
+        sim.set_source(W.paper_source(pp, 0.0))
+        sim.set_source_prev(W.paper_source(pp, -pp.time_step))
+        for n in range(pp.steps):
+            sim.set_dirichlet(W.paper_phi(pp, (n + 1) * pp.time_step))
+            sim.step(1)
+            sim.set_source(W.paper_source(pp, (n + 1) * pp.time_step))
+        assert np.abs(sim.phi() - phi_ref).max() <= 1e-13
+        sim.close()
+
+
 def pin_slip_free_tau2(lib):
     """Sec. 3.2, Eq. (37): with halfway bounce-back walls, steady diffusion under a uniform
     source shows no numerical slip exactly when tau2 = 3(1 - 4 tau1) / (8 (1 - 2 tau1)) (1.375 at
@@ -636,5 +659,6 @@ ALL_PINS = [
     pin_adjoint_gradient_matches_finite_differences,
     pin_slip_free_tau2,
     pin_table2_present_model,
+    pin_dirichlet_field_path_matches_benchmark,
     pin_table2_comparison_models,
 ]

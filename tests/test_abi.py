@@ -55,7 +55,7 @@ def test_binding_covers_the_header(T):
 
 
 def test_host_only_calls(T):
-    assert T.trtr_abi_version() == 1
+    assert T.trtr_abi_version() == 2
     ex, ey, w = T.trtr_d2q9()
     assert np.isclose(w.sum(), 1.0)
     assert np.array_equal(ex + 0, [0, 1, -1, 0, 0, 1, -1, 1, -1])
@@ -79,7 +79,7 @@ BAD = [
     dict(nx=0), dict(ny=-3), dict(dx=0.0), dict(dt=-1.0), dict(dx=float("nan")), dict(precision=7),
     dict(tau2_mode=2), dict(magic=0.0), dict(tau2_mode=1, tau2=0.5), dict(tau1_const=0.4),
     dict(grad_mode=5), dict(src_mode=3), dict(check_every=-1), dict(phi_ref=float("inf")),
-    dict(nx=70000, ny=40000),
+    dict(nx=70000, ny=40000), dict(bc_mode=2), dict(bc_mode=1, nx=2), dict(bc_mode=1, ny=1),
 ]
 
 
@@ -99,6 +99,8 @@ def test_null_arguments(T):
     assert lib.trtr_destroy(None) == T.TRTR_OK
     assert lib.trtr_step(None, 1) == T.TRTR_EINVAL
     assert lib.trtr_sync(None) == T.TRTR_EINVAL
+    assert lib.trtr_set_dirichlet(None, None, 0) == T.TRTR_EINVAL
+    assert lib.trtr_set_source_prev(None, None, 0) == T.TRTR_EINVAL
 
 
 def test_batch_rejects_bad_instances_before_touching_cuda(T):
@@ -106,7 +108,9 @@ def test_batch_rejects_bad_instances_before_touching_cuda(T):
 
     a = T.pulse_instance(W.Pulse(n=32), T.TRTR_F32)
     b = T.pulse_instance(W.Pulse(n=40), T.TRTR_F16_OFS)
-    for bad in ([a, b], [T.pulse_instance(W.Pulse(n=32), T.TRTR_F64)], []):
+    c = T.pulse_instance(W.Pulse(n=32), T.TRTR_F32)
+    c.p.bc_mode = T.TRTR_BC_DIRICHLET_NEE
+    for bad in ([a, b], [T.pulse_instance(W.Pulse(n=32), T.TRTR_F64)], [], [a, c]):
         with pytest.raises(T.TrtrError) as e:
             T.trtr_batch_create(bad)
         assert e.value.status == T.TRTR_EINVAL
