@@ -15,8 +15,8 @@
 // where a_a = u_b d_b u_a (Eq. (16)) comes from central differences of the staged u tile,
 // and the nine populations are rebuilt pairwise from their even and odd halves.
 //
-// Data movement (sm_103a): a persistent kernel, two CTAs per SM, walks 128 x 8-node
-// tiles.  For each tile one thread issues TMA loads (cp.async.bulk.tensor) of the nine
+// Data movement (sm_103a): a persistent kernel walks 128 x 16-node tiles (FP64: 128 x 8),
+// with the CTAs per SM and stages of Geom below.  For each tile one thread issues TMA loads (cp.async.bulk.tensor) of the nine
 // shifted population tiles, the u tile with its one-node halo and the D tile into a
 // shared-memory stage and arms an mbarrier with the expected byte count; the stages form a
 // ring so the loads of the next tiles are in flight while the current one is computed.
@@ -33,29 +33,67 @@ namespace {
 
 using namespace core;
 
-constexpr int kBX = 128;            // nodes per tile along x (4 per lane)
-constexpr int kBY = 8;              // tile rows = warps per CTA
-constexpr int kThreads = 32 * kBY;
-constexpr int kMinBlocks = 2;  // two CTAs per SM: at most 128 registers per thread
+constexpr int kBX = 128;  // nodes per tile along x
 
-// Tile order across the persistent CTAs: 0 = interleaved row-major (tile = CTA + k * grid,
-// so the CTAs sweep the grid together row band by row band and neighbouring tiles are
-// fetched at the same time), 1 = contiguous column-major chunk per CTA, 2 = contiguous
-// row-major chunk per CTA (x-neighbour tiles follow each other in one CTA, so the 16-byte
-// x over-fetch of the shifted planes is still in L2).  Measured on GB300: 4-byte and 8-byte
-// storage run fastest with 2, 2-byte storage with 0.
-#ifndef TRTR_TILE_ORDER_WIDE
-#define TRTR_TILE_ORDER_WIDE 2
+// Pipeline geometry per storage type.  A CTA owns STAGES tile buffers of BY x 128 nodes: while
+// its warps work on one, the TMA loads of the next STAGES - 1 are in flight.  WPR warps share a
+// tile row (a lane takes 128 / (64 WPR) node pairs); CTAS CTAs per SM set the register budget
+// (65536 / (threads x CTAS) per thread).  ORDER is the order in which the persistent CTAs take
+// the tiles: 0 = interleaved row-major (tile = CTA + k * grid, so the CTAs sweep the grid
+// together row band by row band and neighbouring tiles are fetched at the same time), 1 =
+// contiguous column-major chunk per CTA, 2 = contiguous row-major chunk per CTA.  Chosen by
+// sweeps on GB300 (4096^2 FP32 and 8192^2 FP16 pulse steps): one CTA of 16 warps per SM on
+// 128 x 16 tiles (a lane takes two node pairs of its row), two stages for FP32 and three for
+// the 2-byte storages (as many as fit in shared memory).  Larger tiles halve the share of the
+// velocity halo rows; one CTA per SM gives each SM one tile computing and one or two loading.
+// The TRTR_STEP_* macros override the geometry of the storages of TRTR_STEP_SIZE bytes (sweeps).
+template <typename S>
+struct Geom {  // FP64
+    static constexpr int BY = 8, WPR = 1, CTAS = 2, STAGES = 2, ORDER = 2;
+};
+template <>
+struct Geom<float> {
+    static constexpr int BY = 16, WPR = 1, CTAS = 1, STAGES = 2, ORDER = 0;
+};
+template <>
+struct Geom<__half> {
+    static constexpr int BY = 16, WPR = 1, CTAS = 1, STAGES = 3, ORDER = 0;
+};
+template <>
+struct Geom<__nv_bfloat16> : Geom<__half> {};
+
+#ifdef TRTR_STEP_ROWS
+template <typename S>
+struct Sweep {
+    static constexpr bool on = sizeof(S) == TRTR_STEP_SIZE;
+    static constexpr int BY = on ? TRTR_STEP_ROWS : Geom<S>::BY;
+    static constexpr int WPR = on ? TRTR_STEP_WARPS_PER_ROW : Geom<S>::WPR;
+    static constexpr int CTAS = on ? TRTR_STEP_CTAS_PER_SM : Geom<S>::CTAS;
+    static constexpr int STAGES = on ? TRTR_STEP_STAGES : Geom<S>::STAGES;
+    static constexpr int ORDER = on ? TRTR_STEP_ORDER : Geom<S>::ORDER;
+};
+#else
+template <typename S>
+using Sweep = Geom<S>;
 #endif
-#ifndef TRTR_TILE_ORDER_HALF
-#define TRTR_TILE_ORDER_HALF 0
-#endif
+
+template <typename S>
+struct Pipe {
+    static constexpr int BY = Sweep<S>::BY, WPR = Sweep<S>::WPR, CTAS = Sweep<S>::CTAS, STAGES = Sweep<S>::STAGES,
+                         ORDER = Sweep<S>::ORDER;
+    static constexpr int THREADS = 32 * BY * WPR;
+    static constexpr int PAIRS = kBX / 64 / WPR;  // node pairs per lane (FP64: 2 PAIRS nodes)
+    static_assert(BY >= 1 && CTAS >= 1 && STAGES >= 1 && THREADS <= 1024, "pipeline geometry");
+    static_assert((WPR == 1 || WPR == 2) && PAIRS >= 1, "warps per row");
+};
+
 
 template <typename S, int SRC, int STAGES>
-__global__ void __launch_bounds__(kThreads, kMinBlocks)
+__global__ void __launch_bounds__(Pipe<S>::THREADS, Pipe<S>::CTAS)
     step_kernel(const __grid_constant__ CUtensorMap mp, const __grid_constant__ CUtensorMap mu,
                 const __grid_constant__ CUtensorMap md, const __grid_constant__ CUtensorMap ms,
                 const StepArgs<typename Store<S>::C> a) {
+    constexpr int kBY = Pipe<S>::BY, kWPR = Pipe<S>::WPR, kPairsPerLane = Pipe<S>::PAIRS;
     using T = Tile<S, SRC, kBX, kBY>;
     constexpr bool kPairs = !std::is_same<S, double>::value;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -65,11 +103,13 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
                                                            ~static_cast<uintptr_t>(127));
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * T::STAGE);
 
-    const int tid = threadIdx.x, lane = tid & 31, r = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int r = w / kWPR;                // tile row of this warp
+    const int c0 = (w % kWPR) * 64 * kPairsPerLane;  // its first column in the row
     const int nx = a.lp.nx, ny = a.lp.ny;
     const int ntx = (nx + kBX - 1) / kBX, nty = (ny + kBY - 1) / kBY;
     const int ntiles = ntx * nty;
-    constexpr int kOrder = sizeof(S) == 2 ? TRTR_TILE_ORDER_HALF : TRTR_TILE_ORDER_WIDE;
+    constexpr int kOrder = Pipe<S>::ORDER;
     const int chunk = (ntiles + gridDim.x - 1) / gridDim.x;
     const int first = kOrder == 0 ? blockIdx.x : blockIdx.x * chunk;
     const int stride = kOrder == 0 ? gridDim.x : 1;
@@ -101,12 +141,12 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
         const int j = j0 + r;
 
         // per-column / per-row pulse tables, loaded before the wait so their latency hides
-        F2 sx[2], cx[2];
+        F2 sx[kPairsPerLane], cx[kPairsPerLane];
         float sy = 0.f, cy = 0.f;
         if (kPairs && SRC == TRTR_SRC_PULSE) {
 #pragma unroll
-            for (int m = 0; m < 2; ++m) {
-                const int i = i0 + 64 * m + 2 * lane;
+            for (int m = 0; m < kPairsPerLane; ++m) {
+                const int i = i0 + c0 + 64 * m + 2 * lane;
                 const float* tx = reinterpret_cast<const float*>(a.tab_x);
                 const float s0 = i < nx ? __ldg(tx + i) : 0.f, s1 = i + 1 < nx ? __ldg(tx + i + 1) : 0.f;
                 const float c0 = i < nx ? __ldg(tx + nx + i) : 0.f, c1 = i + 1 < nx ? __ldg(tx + nx + i + 1) : 0.f;
@@ -125,9 +165,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
         if (ok && j < ny) {
             const unsigned char* st = smem + s * T::STAGE;
             if constexpr (kPairs)
-                tile_row_pairs<S, SRC, kBX, kBY>(st, r, lane, i0, j, a, sx, cx, sy, cy);
+                tile_row_pairs<S, SRC, kBX, kBY, kPairsPerLane>(st, r, lane, i0, j, a, sx, cx, sy, cy, c0);
             else
-                tile_row_f64<SRC, kBX, kBY>(st, r, lane, i0, j, a);
+                tile_row_f64<SRC, kBX, kBY, 2 * kPairsPerLane>(st, r, lane, i0, j, a, c0);
         }
         __syncthreads();  // stage s fully read (and s_abort visible)
         if (s_abort) {
@@ -145,10 +185,14 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
     }
 }
 
-// Stages per CTA: two when they fit in the 227 KB a CTA may use, else one.
+// Stages per CTA: Pipe<S>::STAGES, or fewer while they do not fit in the 227 KB a CTA may use.
 template <typename S, int SRC>
 constexpr int stages_for() {
-    return 2 * Tile<S, SRC, kBX, kBY>::STAGE + 256 <= 227 * 1024 ? 2 : 1;
+    constexpr int kStage = Tile<S, SRC, kBX, Pipe<S>::BY>::STAGE;
+    static_assert(kStage + 256 <= 227 * 1024, "one tile stage must fit in shared memory");
+    int s = Pipe<S>::STAGES;
+    while (s > 1 && s * kStage + 256 > 227 * 1024) --s;
+    return s;
 }
 
 // ------------------------------------------------------------------------------ host side
@@ -156,6 +200,7 @@ constexpr int stages_for() {
 template <typename S>
 cudaError_t encode_typed(trtr_ctx* ctx) {
     using C = typename Store<S>::C;
+    constexpr int kBY = Pipe<S>::BY;
     // The box shapes do not depend on the source mode (TX bytes do).
     using T = Tile<S, TRTR_SRC_NONE, kBX, kBY>;
     bool ok = true;
@@ -173,6 +218,7 @@ cudaError_t encode_typed(trtr_ctx* ctx) {
 template <typename S, int SRC>
 cudaError_t launch_typed(trtr_ctx* ctx, const CUtensorMap& src_map, void* dst, long step) {
     using C = typename Store<S>::C;
+    constexpr int kBY = Pipe<S>::BY, kThreads = Pipe<S>::THREADS;
     using T = Tile<S, SRC, kBX, kBY>;
     constexpr int kStages = stages_for<S, SRC>();
     auto kernel = step_kernel<S, SRC, kStages>;
@@ -233,8 +279,8 @@ cudaError_t launch_src(trtr_ctx* ctx, const CUtensorMap& src_map, void* dst, lon
 
 template <typename S>
 cudaError_t encode_pop_typed(trtr_ctx* ctx, void* buffer, CUtensorMap* out) {
-    using T = Tile<S, TRTR_SRC_NONE, kBX, kBY>;
-    return encode(out, tma_type<S>(), sizeof(S), buffer, ctx->lp, kQ, T::PW, kBY, 1) ? cudaSuccess
+    using T = Tile<S, TRTR_SRC_NONE, kBX, Pipe<S>::BY>;
+    return encode(out, tma_type<S>(), sizeof(S), buffer, ctx->lp, kQ, T::PW, Pipe<S>::BY, 1) ? cudaSuccess
                                                                                     : cudaErrorInvalidValue;
 }
 

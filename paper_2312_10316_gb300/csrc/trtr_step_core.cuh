@@ -263,13 +263,12 @@ __device__ __forceinline__ void issue_tile(unsigned char* stage, uint64_t* bar, 
     }
 }
 
-// One tile row (warp r) of the FP32-computing storages: lane handles the node pairs
-// (i0 + 64 m + 2 lane, + 1), m = 0, 1.
-template <typename S, int SRC, int BX, int BY>
+// One tile row r of the FP32-computing storages, or NM * 64 columns of it from column c0: lane
+// handles the node pairs (i0 + c0 + 64 m + 2 lane, + 1), m = 0 .. NM - 1.
+template <typename S, int SRC, int BX, int BY, int NM = BX / 64>
 __device__ __forceinline__ void tile_row_pairs(const unsigned char* st, int r, int lane, int i0, int j,
                                                const StepArgs<float>& a, const F2* sx, const F2* cx, float sy,
-                                               float cy) {
-    constexpr int NM = BX / 64;  // node pairs per lane
+                                               float cy, int c0 = 0) {
     using T = Tile<S, SRC, BX, BY>;
     using P = Pair<S>;
     using S2 = typename P::type;
@@ -285,7 +284,7 @@ __device__ __forceinline__ void tile_row_pairs(const unsigned char* st, int r, i
     const F2 magic(a.magic), w2f(a.omega2_fixed);
 #pragma unroll 1
     for (int m = 0; m < NM; ++m) {
-        const int c = 64 * m + 2 * lane;  // column of the pair inside the tile
+        const int c = c0 + 64 * m + 2 * lane;  // column of the pair inside the tile
         const int i = i0 + c;
         if (i >= nx) break;
         // a1: pull-streaming from the shifted tiles
@@ -358,10 +357,11 @@ __device__ __forceinline__ void tile_row_pairs(const unsigned char* st, int r, i
     }
 }
 
-// One tile row of the FP64 path: lane handles nodes i0 + 32 m + lane, m = 0..3.
-template <int SRC, int BX, int BY>
+// One tile row of the FP64 path, or NMF * 32 columns of it from column c0: lane handles nodes
+// i0 + c0 + 32 m + lane, m = 0 .. NMF - 1.
+template <int SRC, int BX, int BY, int NMF = BX / 32>
 __device__ __forceinline__ void tile_row_f64(const unsigned char* st, int r, int lane, int i0, int j,
-                                             const StepArgs<double>& a) {
+                                             const StepArgs<double>& a, int c0 = 0) {
     using T = Tile<double, SRC, BX, BY>;
     const int nx = a.lp.nx, ny = a.lp.ny;
     const double* sp = reinterpret_cast<const double*>(st) + r * T::PW;
@@ -377,8 +377,8 @@ __device__ __forceinline__ void tile_row_f64(const unsigned char* st, int r, int
         cy = __ldg(a.tab_y + ny + j);
     }
 #pragma unroll 1
-    for (int m = 0; m < BX / 32; ++m) {
-        const int c = 32 * m + lane;
+    for (int m = 0; m < NMF; ++m) {
+        const int c = c0 + 32 * m + lane;
         const int i = i0 + c;
         if (i >= nx) break;
         double g[kQ];
