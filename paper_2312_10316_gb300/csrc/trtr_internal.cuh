@@ -207,11 +207,10 @@ __host__ __device__ inline void edge_node(int k, int nx, int ny, int* i, int* j)
 __host__ __device__ constexpr int lattice_ex(int q) { return q == 1 || q == 5 || q == 7 ? 1 : (q == 2 || q == 6 || q == 8 ? -1 : 0); }
 __host__ __device__ constexpr int lattice_ey(int q) { return q == 3 || q == 5 || q == 8 ? 1 : (q == 4 || q == 6 || q == 7 ? -1 : 0); }
 
-// Stores one population value at interior node (i, j) and at every ghost cell that repeats
-// it (the periodic images just outside the interior).
+// Stores one population value at every ghost cell that repeats interior node (i, j) (the
+// periodic images just outside the interior); nothing for nodes off the edges.
 template <typename T>
-__device__ __forceinline__ void store_with_ghosts(T* plane, const PlaneLayout& L, int i, int j, T v) {
-    plane[L.at(i, j)] = v;
+__device__ __forceinline__ void store_ghosts(T* plane, const PlaneLayout& L, int i, int j, T v) {
     const bool xl = i == 0, xr = i == L.nx - 1, yl = j == 0, yr = j == L.ny - 1;
     if (!(xl || xr || yl || yr)) return;
     if (xl) plane[L.at(L.nx, j)] = v;
@@ -222,6 +221,13 @@ __device__ __forceinline__ void store_with_ghosts(T* plane, const PlaneLayout& L
     if (xl && yr) plane[L.at(L.nx, -1)] = v;
     if (xr && yl) plane[L.at(-1, L.ny)] = v;
     if (xr && yr) plane[L.at(-1, -1)] = v;
+}
+
+// Stores one population value at interior node (i, j) and at its ghost cells.
+template <typename T>
+__device__ __forceinline__ void store_with_ghosts(T* plane, const PlaneLayout& L, int i, int j, T v) {
+    plane[L.at(i, j)] = v;
+    store_ghosts(plane, L, i, j, v);
 }
 
 }  // namespace trtr

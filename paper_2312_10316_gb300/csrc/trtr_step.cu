@@ -15,17 +15,18 @@
 // where a_a = u_b d_b u_a (Eq. (16)) comes from central differences of the staged u tile,
 // and the nine populations are rebuilt pairwise from their even and odd halves.
 //
-// Data movement (sm_103a): a persistent kernel walks 128 x 16-node tiles (FP64: 128 x 8),
-// with the CTAs per SM and stages of Geom below.  For each tile one thread issues TMA loads (cp.async.bulk.tensor) of the nine
-// shifted population tiles, the u tile with its one-node halo and the D tile into a
-// shared-memory stage and arms an mbarrier with the expected byte count; the stages form a
+// Data movement (sm_103a): a persistent kernel walks 128 x BY-node tiles with the CTAs per SM
+// and stages of Geom below.  For each tile one thread issues TMA loads (cp.async.bulk.tensor)
+// of the nine shifted population tiles, the u tile with its one-node halo and the D tile into
+// a shared-memory stage and arms an mbarrier with the expected byte count; the stages form a
 // ring so the loads of the next tiles are in flight while the current one is computed.
 // The pull shift of plane i is a tile origin moved by -e_i; TMA needs 16-byte aligned x
 // origins, so the planes with e_x = +1 start one 16-byte chunk early and are read from
 // shared memory with a column offset.  Ghost cells of the layout make the periodic wrap a
-// plain tile read.  Results go to global memory with coalesced stores (one warp = one
-// 128-node row), ghost copies included.  Every mbarrier wait is bounded: on timeout the
-// kernel raises the context's flag and returns.
+// plain tile read.  Results leave one warp = one 128-node row at a time: coalesced lane stores,
+// or (FP32 pulse) one bulk copy per plane of the row staged in shared memory; edge nodes also
+// store their ghost copies.  Every mbarrier wait is bounded: on timeout the kernel raises the
+// context's flag and returns.
 #include "trtr_step_core.cuh"
 
 namespace trtr {
@@ -35,65 +36,84 @@ using namespace core;
 
 constexpr int kBX = 128;  // nodes per tile along x
 
-// Pipeline geometry per storage type.  A CTA owns STAGES tile buffers of BY x 128 nodes: while
-// its warps work on one, the TMA loads of the next STAGES - 1 are in flight.  WPR warps share a
-// tile row (a lane takes 128 / (64 WPR) node pairs); CTAS CTAs per SM set the register budget
-// (65536 / (threads x CTAS) per thread).  ORDER is the order in which the persistent CTAs take
-// the tiles: 0 = interleaved row-major (tile = CTA + k * grid, so the CTAs sweep the grid
-// together row band by row band and neighbouring tiles are fetched at the same time), 1 =
-// contiguous column-major chunk per CTA, 2 = contiguous row-major chunk per CTA.  Chosen by
-// sweeps on GB300 (4096^2 FP32 and 8192^2 FP16 pulse steps): one CTA of 16 warps per SM on
-// 128 x 16 tiles (a lane takes two node pairs of its row), two stages for FP32 and three for
-// the 2-byte storages (as many as fit in shared memory).  Larger tiles halve the share of the
-// velocity halo rows; one CTA per SM gives each SM one tile computing and one or two loading.
-// The TRTR_STEP_* macros override the geometry of the storages of TRTR_STEP_SIZE bytes (sweeps).
-template <typename S>
+// Pipeline geometry per storage type and source mode.  A CTA owns STAGES tile buffers of
+// BY x 128 nodes: while its warps work on one, the TMA loads of the next STAGES - 1 are in
+// flight.  WPR warps share a tile row (a lane takes 128 / (64 WPR) node pairs); CTAS CTAs per SM
+// set the register budget (65536 / (threads x CTAS) per thread).  ORDER is the order in which
+// the persistent CTAs take the tiles: 0 = interleaved row-major (tile = CTA + k * grid, so the
+// CTAs sweep the grid together and neighbouring tiles' halos are fetched at the same time),
+// 1 = contiguous column-major chunk per CTA, 2 = contiguous row-major chunk per CTA.  TST = 1:
+// results leave through bulk copies of whole tile rows from shared memory (one warp per row),
+// 0: lane stores.  Chosen by sweeps on GB300 (4096^2 FP32 and 8192^2 FP16 steps in each source
+// mode): one CTA of 16 warps per SM on 128 x 16 tiles, two stages for FP32 and three for the
+// 2-byte storages (as many as fit), bulk row stores for the FP32 pulse; the FP32 source-field
+// mode, whose stages carry two more planes, runs two CTAs per SM on 128 x 8 tiles so that each
+// still has two stages.  The TRTR_STEP_* macros override the geometry of the storages of
+// TRTR_STEP_SIZE bytes in source mode TRTR_STEP_SRC (sweeps).
+template <typename S, int SRC>
 struct Geom {  // FP64
-    static constexpr int BY = 8, WPR = 1, CTAS = 2, STAGES = 2, ORDER = 2;
+    static constexpr int BY = 8, WPR = 1, CTAS = 2, STAGES = 2, ORDER = 2, TST = 0;
+};
+template <int SRC>
+struct Geom<float, SRC> {  // pulse source
+    static constexpr int BY = 16, WPR = 1, CTAS = 1, STAGES = 2, ORDER = 0, TST = 1;
 };
 template <>
-struct Geom<float> {
-    static constexpr int BY = 16, WPR = 1, CTAS = 1, STAGES = 2, ORDER = 0;
+struct Geom<float, TRTR_SRC_NONE> {
+    static constexpr int BY = 16, WPR = 1, CTAS = 1, STAGES = 2, ORDER = 2, TST = 0;
 };
 template <>
-struct Geom<__half> {
-    static constexpr int BY = 16, WPR = 1, CTAS = 1, STAGES = 3, ORDER = 0;
+struct Geom<float, TRTR_SRC_FIELD> {
+    static constexpr int BY = 8, WPR = 1, CTAS = 2, STAGES = 2, ORDER = 0, TST = 0;
 };
-template <>
-struct Geom<__nv_bfloat16> : Geom<__half> {};
+template <int SRC>
+struct Geom<__half, SRC> {
+    static constexpr int BY = 16, WPR = 1, CTAS = 1, STAGES = 3, ORDER = 0, TST = 0;
+};
+template <int SRC>
+struct Geom<__nv_bfloat16, SRC> : Geom<__half, SRC> {};
 
 #ifdef TRTR_STEP_ROWS
-template <typename S>
+#ifndef TRTR_STEP_SRC
+#define TRTR_STEP_SRC -1
+#endif
+#ifndef TRTR_STEP_TMA_STORE
+#define TRTR_STEP_TMA_STORE 0
+#endif
+template <typename S, int SRC>
 struct Sweep {
-    static constexpr bool on = sizeof(S) == TRTR_STEP_SIZE;
-    static constexpr int BY = on ? TRTR_STEP_ROWS : Geom<S>::BY;
-    static constexpr int WPR = on ? TRTR_STEP_WARPS_PER_ROW : Geom<S>::WPR;
-    static constexpr int CTAS = on ? TRTR_STEP_CTAS_PER_SM : Geom<S>::CTAS;
-    static constexpr int STAGES = on ? TRTR_STEP_STAGES : Geom<S>::STAGES;
-    static constexpr int ORDER = on ? TRTR_STEP_ORDER : Geom<S>::ORDER;
+    static constexpr bool on = sizeof(S) == TRTR_STEP_SIZE && (TRTR_STEP_SRC < 0 || SRC == TRTR_STEP_SRC);
+    static constexpr int BY = on ? TRTR_STEP_ROWS : Geom<S, SRC>::BY;
+    static constexpr int WPR = on ? TRTR_STEP_WARPS_PER_ROW : Geom<S, SRC>::WPR;
+    static constexpr int CTAS = on ? TRTR_STEP_CTAS_PER_SM : Geom<S, SRC>::CTAS;
+    static constexpr int STAGES = on ? TRTR_STEP_STAGES : Geom<S, SRC>::STAGES;
+    static constexpr int ORDER = on ? TRTR_STEP_ORDER : Geom<S, SRC>::ORDER;
+    static constexpr int TST = on ? TRTR_STEP_TMA_STORE : Geom<S, SRC>::TST;
 };
 #else
-template <typename S>
-using Sweep = Geom<S>;
+template <typename S, int SRC>
+using Sweep = Geom<S, SRC>;
 #endif
 
-template <typename S>
+template <typename S, int SRC>
 struct Pipe {
-    static constexpr int BY = Sweep<S>::BY, WPR = Sweep<S>::WPR, CTAS = Sweep<S>::CTAS, STAGES = Sweep<S>::STAGES,
-                         ORDER = Sweep<S>::ORDER;
+    static constexpr int BY = Sweep<S, SRC>::BY, WPR = Sweep<S, SRC>::WPR, CTAS = Sweep<S, SRC>::CTAS,
+                         STAGES = Sweep<S, SRC>::STAGES, ORDER = Sweep<S, SRC>::ORDER;
+    static constexpr bool TST = Sweep<S, SRC>::TST != 0 && WPR == 1;
     static constexpr int THREADS = 32 * BY * WPR;
     static constexpr int PAIRS = kBX / 64 / WPR;  // node pairs per lane (FP64: 2 PAIRS nodes)
     static_assert(BY >= 1 && CTAS >= 1 && STAGES >= 1 && THREADS <= 1024, "pipeline geometry");
     static_assert((WPR == 1 || WPR == 2) && PAIRS >= 1, "warps per row");
 };
 
-
 template <typename S, int SRC, int STAGES>
-__global__ void __launch_bounds__(Pipe<S>::THREADS, Pipe<S>::CTAS)
+__global__ void __launch_bounds__(Pipe<S, SRC>::THREADS, Pipe<S, SRC>::CTAS)
     step_kernel(const __grid_constant__ CUtensorMap mp, const __grid_constant__ CUtensorMap mu,
                 const __grid_constant__ CUtensorMap md, const __grid_constant__ CUtensorMap ms,
                 const StepArgs<typename Store<S>::C> a) {
-    constexpr int kBY = Pipe<S>::BY, kWPR = Pipe<S>::WPR, kPairsPerLane = Pipe<S>::PAIRS;
+    using G = Pipe<S, SRC>;
+    constexpr int kBY = G::BY, kWPR = G::WPR, kPairsPerLane = G::PAIRS;
+    constexpr bool kTST = G::TST;
     using T = Tile<S, SRC, kBX, kBY>;
     constexpr bool kPairs = !std::is_same<S, double>::value;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -109,7 +129,7 @@ __global__ void __launch_bounds__(Pipe<S>::THREADS, Pipe<S>::CTAS)
     const int nx = a.lp.nx, ny = a.lp.ny;
     const int ntx = (nx + kBX - 1) / kBX, nty = (ny + kBY - 1) / kBY;
     const int ntiles = ntx * nty;
-    constexpr int kOrder = Pipe<S>::ORDER;
+    constexpr int kOrder = G::ORDER;
     const int chunk = (ntiles + gridDim.x - 1) / gridDim.x;
     const int first = kOrder == 0 ? blockIdx.x : blockIdx.x * chunk;
     const int stride = kOrder == 0 ? gridDim.x : 1;
@@ -165,9 +185,9 @@ __global__ void __launch_bounds__(Pipe<S>::THREADS, Pipe<S>::CTAS)
         if (ok && j < ny) {
             const unsigned char* st = smem + s * T::STAGE;
             if constexpr (kPairs)
-                tile_row_pairs<S, SRC, kBX, kBY, kPairsPerLane>(st, r, lane, i0, j, a, sx, cx, sy, cy, c0);
+                tile_row_pairs<S, SRC, kBX, kBY, kPairsPerLane, kTST>(st, r, lane, i0, j, a, sx, cx, sy, cy, c0);
             else
-                tile_row_f64<SRC, kBX, kBY, 2 * kPairsPerLane>(st, r, lane, i0, j, a, c0);
+                tile_row_f64<SRC, kBX, kBY, 2 * kPairsPerLane, kTST>(st, r, lane, i0, j, a, c0);
         }
         __syncthreads();  // stage s fully read (and s_abort visible)
         if (s_abort) {
@@ -177,30 +197,32 @@ __global__ void __launch_bounds__(Pipe<S>::THREADS, Pipe<S>::CTAS)
                 for (int kk = k + 1; kk < my_tiles && kk < k + STAGES; ++kk)
                     mbar_wait_bounded(&full[kk % STAGES], (kk / STAGES) & 1);
             }
+            if (kTST && lane == 0) bulk_wait_all();
             return;
         }
         if (tid == 0 && k + STAGES < my_tiles)
             issue_tile<S, SRC, kBX, kBY>(smem + s * T::STAGE, &full[s], &mp, &mu, &md, &ms, tile_x0(k + STAGES),
                                tile_y0(k + STAGES), a);
     }
+    if (kTST && lane == 0) bulk_wait_all();  // this warp's row copies have completed
 }
 
-// Stages per CTA: Pipe<S>::STAGES, or fewer while they do not fit in the 227 KB a CTA may use.
+// Stages per CTA: Pipe<S, SRC>::STAGES, or fewer while they do not fit in the 227 KB a CTA may use.
 template <typename S, int SRC>
 constexpr int stages_for() {
-    constexpr int kStage = Tile<S, SRC, kBX, Pipe<S>::BY>::STAGE;
+    constexpr int kStage = Tile<S, SRC, kBX, Pipe<S, SRC>::BY>::STAGE;
     static_assert(kStage + 256 <= 227 * 1024, "one tile stage must fit in shared memory");
-    int s = Pipe<S>::STAGES;
+    int s = Pipe<S, SRC>::STAGES;
     while (s > 1 && s * kStage + 256 > 227 * 1024) --s;
     return s;
 }
 
 // ------------------------------------------------------------------------------ host side
 
-template <typename S>
+template <typename S, int SRC>
 cudaError_t encode_typed(trtr_ctx* ctx) {
     using C = typename Store<S>::C;
-    constexpr int kBY = Pipe<S>::BY;
+    constexpr int kBY = Pipe<S, SRC>::BY;
     // The box shapes do not depend on the source mode (TX bytes do).
     using T = Tile<S, TRTR_SRC_NONE, kBX, kBY>;
     bool ok = true;
@@ -218,7 +240,7 @@ cudaError_t encode_typed(trtr_ctx* ctx) {
 template <typename S, int SRC>
 cudaError_t launch_typed(trtr_ctx* ctx, const CUtensorMap& src_map, void* dst, long step) {
     using C = typename Store<S>::C;
-    constexpr int kBY = Pipe<S>::BY, kThreads = Pipe<S>::THREADS;
+    constexpr int kBY = Pipe<S, SRC>::BY, kThreads = Pipe<S, SRC>::THREADS;
     using T = Tile<S, SRC, kBX, kBY>;
     constexpr int kStages = stages_for<S, SRC>();
     auto kernel = step_kernel<S, SRC, kStages>;
@@ -279,19 +301,29 @@ cudaError_t launch_src(trtr_ctx* ctx, const CUtensorMap& src_map, void* dst, lon
 
 template <typename S>
 cudaError_t encode_pop_typed(trtr_ctx* ctx, void* buffer, CUtensorMap* out) {
-    using T = Tile<S, TRTR_SRC_NONE, kBX, Pipe<S>::BY>;
-    return encode(out, tma_type<S>(), sizeof(S), buffer, ctx->lp, kQ, T::PW, Pipe<S>::BY, 1) ? cudaSuccess
+    // population maps of the source-free kernel (the adjoint's recomputation)
+    using T = Tile<S, TRTR_SRC_NONE, kBX, Pipe<S, TRTR_SRC_NONE>::BY>;
+    return encode(out, tma_type<S>(), sizeof(S), buffer, ctx->lp, kQ, T::PW, Pipe<S, TRTR_SRC_NONE>::BY, 1) ? cudaSuccess
                                                                                     : cudaErrorInvalidValue;
 }
 
 }  // namespace
 
+template <typename S>
+cudaError_t encode_src(trtr_ctx* ctx) {
+    switch (ctx->p.src_mode) {
+        case TRTR_SRC_FIELD: return encode_typed<S, TRTR_SRC_FIELD>(ctx);
+        case TRTR_SRC_PULSE: return encode_typed<S, TRTR_SRC_PULSE>(ctx);
+        default: return encode_typed<S, TRTR_SRC_NONE>(ctx);
+    }
+}
+
 cudaError_t encode_maps(trtr_ctx* ctx) {
     switch (ctx->p.precision) {
-        case TRTR_F64: return encode_typed<double>(ctx);
-        case TRTR_F32: return encode_typed<float>(ctx);
-        case TRTR_F16_OFS: return encode_typed<__half>(ctx);
-        case TRTR_BF16_OFS: return encode_typed<__nv_bfloat16>(ctx);
+        case TRTR_F64: return encode_src<double>(ctx);
+        case TRTR_F32: return encode_src<float>(ctx);
+        case TRTR_F16_OFS: return encode_src<__half>(ctx);
+        case TRTR_BF16_OFS: return encode_src<__nv_bfloat16>(ctx);
         default: return cudaErrorInvalidValue;
     }
 }

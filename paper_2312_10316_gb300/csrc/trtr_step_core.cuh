@@ -90,6 +90,24 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
+// Bulk copy of `bytes` (a multiple of 16) from shared to global memory, both addresses 16-byte
+// aligned; the async proxy reads the source, completion is tracked per thread in bulk
+// async-groups.
+__device__ __forceinline__ void bulk_store(void* gdst, const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(smem_addr(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the shared-memory sources of this thread's bulk stores have been read (may be overwritten)
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// this thread's bulk stores are complete
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// generic-proxy writes to shared memory become visible to the async proxy (bulk stores)
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // ---- arithmetic types --------------------------------------------------------------------
 // FP32-computing storages work on pairs of adjacent nodes with the packed FP32 instructions
 // of sm_100-family SMs (two lanes of FP32 per FADD2 / FMUL2 / FFMA2); FP64 works per node.
@@ -197,6 +215,15 @@ __device__ __forceinline__ C weight(int q) {
     return q == 0 ? C(4.0 / 9.0) : (q < 5 ? C(1.0 / 9.0) : C(1.0 / 36.0));
 }
 
+// Columns of a tile row (of `valid` interior columns, at most 128) that one bulk copy writes: a
+// whole number of 16-byte chunks.
+template <typename S>
+__device__ __forceinline__ int bulk_cols(int valid) {
+    constexpr int kChunk = 16 / (int)sizeof(S);
+    const int v = valid < 128 ? valid : 128;
+    return v / kChunk * kChunk;
+}
+
 // Shared-memory column offset of plane q's tile (see the TMA origin in issue_tile).
 template <int A>
 __device__ __forceinline__ constexpr int plane_offset(int q) {
@@ -265,10 +292,19 @@ __device__ __forceinline__ void issue_tile(unsigned char* stage, uint64_t* bar, 
 
 // One tile row r of the FP32-computing storages, or NM * 64 columns of it from column c0: lane
 // handles the node pairs (i0 + c0 + 64 m + 2 lane, + 1), m = 0 .. NM - 1.
-template <typename S, int SRC, int BX, int BY, int NM = BX / 64>
+//
+// Stores: TST = false writes every value to global memory from the lanes.  TST = true (one warp
+// per whole row) writes the row's nine result rows into shared memory over the row's own input
+// rows (only this warp reads them; the results of pair m cover columns 64 m .. 64 m + 63, which
+// no later pair reads), and lane 0 then copies each plane's row to global memory with one bulk
+// copy of the row's first `bulk_cols(nx - i0)` columns (16-byte multiples: the row starts are
+// 16-byte aligned in both memories).  The lanes store the few columns past those, and the ghost
+// copies of edge nodes, directly.
+template <typename S, int SRC, int BX, int BY, int NM = BX / 64, bool TST = false>
 __device__ __forceinline__ void tile_row_pairs(const unsigned char* st, int r, int lane, int i0, int j,
                                                const StepArgs<float>& a, const F2* sx, const F2* cx, float sy,
                                                float cy, int c0 = 0) {
+    static_assert(!TST || NM == BX / 64, "bulk row stores need one warp per tile row");
     using T = Tile<S, SRC, BX, BY>;
     using P = Pair<S>;
     using S2 = typename P::type;
@@ -286,7 +322,7 @@ __device__ __forceinline__ void tile_row_pairs(const unsigned char* st, int r, i
     for (int m = 0; m < NM; ++m) {
         const int c = c0 + 64 * m + 2 * lane;  // column of the pair inside the tile
         const int i = i0 + c;
-        if (i >= nx) break;
+        if (!TST && i >= nx) break;  // (TST: pairs past nx are computed; their columns are not stored)
         // a1: pull-streaming from the shifted tiles
         F2 g[kQ];
 #pragma unroll
@@ -341,7 +377,25 @@ __device__ __forceinline__ void tile_row_pairs(const unsigned char* st, int r, i
 
         // a8: store P_i(x); edge nodes also write their periodic ghost copies
         const bool edge = j == 0 || j == ny - 1 || i == 0 || i + 1 >= nx - 1;
-        if (!edge) {
+        if constexpr (TST) {
+            __syncwarp();  // every lane has read its inputs of pair m
+            S* srow = const_cast<S*>(sp);
+#pragma unroll
+            for (int q = 0; q < kQ; ++q)
+                *reinterpret_cast<S2*>(srow + q * T::PLANE_ELEMS + c) = P::encode(out[q], weight<float>(q) * phi_ref);
+            const int nb = bulk_cols<S>(nx - i0);
+            if ((edge || c + 1 >= nb) && i < nx) {  // ghost copies, and the columns past the bulk copy
+#pragma unroll
+                for (int q = 0; q < kQ; ++q) {
+                    const float off = weight<float>(q) * phi_ref;
+                    const S v0 = Store<S>::encode(out[q].v.x, off), v1 = Store<S>::encode(out[q].v.y, off);
+                    if (c >= nb) dst[q * pl + a.lp.at(i, j)] = v0;
+                    if (c + 1 >= nb && i + 1 < nx) dst[q * pl + a.lp.at(i + 1, j)] = v1;
+                    store_ghosts(dst + q * pl, a.lp, i, j, v0);
+                    if (i + 1 < nx) store_ghosts(dst + q * pl, a.lp, i + 1, j, v1);
+                }
+            }
+        } else if (!edge) {
             S* d0 = dst + a.lp.at(i, j);
 #pragma unroll
             for (int q = 0; q < kQ; ++q)
@@ -355,13 +409,26 @@ __device__ __forceinline__ void tile_row_pairs(const unsigned char* st, int r, i
             }
         }
     }
+    if constexpr (TST) {
+        fence_proxy_async_smem();  // the result rows, for the bulk copies
+        __syncwarp();
+        const int nb = bulk_cols<S>(nx - i0);
+        if (lane == 0 && nb > 0) {
+#pragma unroll
+            for (int q = 0; q < kQ; ++q)
+                bulk_store(dst + q * pl + a.lp.at(i0, j), sp + q * T::PLANE_ELEMS, (uint32_t)(nb * sizeof(S)));
+            bulk_commit();
+            bulk_wait_read();  // the stage may be refilled after the CTA barrier
+        }
+    }
 }
 
 // One tile row of the FP64 path, or NMF * 32 columns of it from column c0: lane handles nodes
-// i0 + c0 + 32 m + lane, m = 0 .. NMF - 1.
-template <int SRC, int BX, int BY, int NMF = BX / 32>
+// i0 + c0 + 32 m + lane, m = 0 .. NMF - 1.  TST: bulk row stores as in tile_row_pairs.
+template <int SRC, int BX, int BY, int NMF = BX / 32, bool TST = false>
 __device__ __forceinline__ void tile_row_f64(const unsigned char* st, int r, int lane, int i0, int j,
                                              const StepArgs<double>& a, int c0 = 0) {
+    static_assert(!TST || NMF == BX / 32, "bulk row stores need one warp per tile row");
     using T = Tile<double, SRC, BX, BY>;
     const int nx = a.lp.nx, ny = a.lp.ny;
     const double* sp = reinterpret_cast<const double*>(st) + r * T::PW;
@@ -380,7 +447,7 @@ __device__ __forceinline__ void tile_row_f64(const unsigned char* st, int r, int
     for (int m = 0; m < NMF; ++m) {
         const int c = c0 + 32 * m + lane;
         const int i = i0 + c;
-        if (i >= nx) break;
+        if (!TST && i >= nx) break;
         double g[kQ];
 #pragma unroll
         for (int q = 0; q < kQ; ++q) g[q] = sp[q * T::PLANE_ELEMS + c + plane_offset<T::A>(q)];
@@ -406,8 +473,35 @@ __device__ __forceinline__ void tile_row_f64(const unsigned char* st, int r, int
         }
         double out[kQ];
         collide_node<double>(g, ux, uy, ax, ay, sd[c], src, a.magic, a.omega2_fixed, a.tau2_fixed, out);
+        if constexpr (TST) {
+            __syncwarp();  // every lane has read its inputs of node m
+            double* srow = const_cast<double*>(sp);
 #pragma unroll
-        for (int q = 0; q < kQ; ++q) store_with_ghosts(dst + q * pl, a.lp, i, j, out[q]);
+            for (int q = 0; q < kQ; ++q) srow[q * T::PLANE_ELEMS + c] = out[q];
+            if (i < nx) {
+                const bool tail = c >= bulk_cols<double>(nx - i0);
+#pragma unroll
+                for (int q = 0; q < kQ; ++q) {
+                    if (tail) dst[q * pl + a.lp.at(i, j)] = out[q];
+                    store_ghosts(dst + q * pl, a.lp, i, j, out[q]);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) store_with_ghosts(dst + q * pl, a.lp, i, j, out[q]);
+        }
+    }
+    if constexpr (TST) {
+        fence_proxy_async_smem();
+        __syncwarp();
+        const int nb = bulk_cols<double>(nx - i0);
+        if (lane == 0 && nb > 0) {
+#pragma unroll
+            for (int q = 0; q < kQ; ++q)
+                bulk_store(dst + q * pl + a.lp.at(i0, j), sp + q * T::PLANE_ELEMS, (uint32_t)(nb * sizeof(double)));
+            bulk_commit();
+            bulk_wait_read();
+        }
     }
 }
 
