@@ -50,8 +50,10 @@ static_assert(offsetof(InstanceDesc<float>, base) % 16 == 0, "16-byte aligned ar
 struct Geometry {
     int bx, by;
 };
-constexpr Geometry kGeoms[] = {{128, 8}, {64, 8}, {128, 4}};
-constexpr int kNumGeoms = 3;
+// 8-row tiles: two 256-thread CTAs per SM; 4-row: four 128-thread CTAs; 16-row: one 512-thread CTA
+// (the single-grid step's geometry).
+constexpr Geometry kGeoms[] = {{128, 8}, {64, 8}, {128, 4}, {128, 16}, {64, 16}};
+constexpr int kNumGeoms = 5;
 constexpr int kNumSchedules = 3;  // 0 interleaved, 1 chunked, 2 chunked with the largest instances first
 constexpr int kNumConfigs = kNumGeoms * kNumSchedules;
 constexpr int kDefaultConfig = 1;  // 128 x 8 tiles, chunked
@@ -86,7 +88,7 @@ __device__ __forceinline__ void cp_async_16(void* sdst, const void* gsrc, int by
 
 template <int BY>
 constexpr int min_blocks() {
-    return BY == 8 ? 2 : 4;  // keeps the register budget at 128 per thread
+    return BY >= 16 ? 1 : (BY == 8 ? 2 : 4);  // keeps the register budget at 128 per thread
 }
 
 template <typename S, int SRC, int BX, int BY, int STAGES>
@@ -141,9 +143,13 @@ __global__ void __launch_bounds__(32 * BY, min_blocks<BY>())
     if (tid == 0)
         for (int k = 0; k < STAGES && k < my_tiles; ++k) issue(k, k);
 
+    // the work-list entry of the next tile is fetched one iteration ahead (its latency hides
+    // behind the current tile)
+    int4 t_next = my_tiles > 0 ? tiles[first] : make_int4(0, 0, 0, 0);
     for (int k = 0; k < my_tiles; ++k) {
         const int s = k % STAGES;
-        const int4 t = tiles[first + k * stride];
+        const int4 t = t_next;
+        if (k + 1 < my_tiles) t_next = tiles[first + (k + 1) * stride];
         const int i0 = t.y, j0 = t.z, j = j0 + r;
 
         F2 sx[BX / 64 > 0 ? BX / 64 : 1], cx[BX / 64 > 0 ? BX / 64 : 1];
@@ -169,8 +175,11 @@ __global__ void __launch_bounds__(32 * BY, min_blocks<BY>())
 
         const bool ok = mbar_wait_bounded(&full[s], (k / STAGES) & 1);
         if (!ok) s_abort = 1;
-        if (ok && j < sargs[s].lp.ny)
-            tile_row_pairs<S, SRC, BX, BY>(smem + s * T::STAGE, r, lane, i0, j, sargs[s], sx, cx, sy, cy);
+        if (ok && j < sargs[s].lp.ny) {
+            // a private copy: the row's global stores cannot alias it, so its fields are read once
+            const StepArgs<C> args = sargs[s];
+            tile_row_pairs<S, SRC, BX, BY>(smem + s * T::STAGE, r, lane, i0, j, args, sx, cx, sy, cy);
+        }
         __syncthreads();
         if (s_abort) {
             if (tid == 0) {
@@ -240,7 +249,14 @@ template <typename S, int SRC, int BX, int BY>
 struct BatchLaunch {
     using C = typename Store<S>::C;
     using T = Tile<S, SRC, BX, BY>;
-    static constexpr int kStages = 2 * T::STAGE + 256 <= 227 * 1024 ? 2 : 1;
+    // two stages, or (one CTA per SM: 16-row tiles) as many as fit, up to three
+    static constexpr int kMaxStages = BY >= 16 ? 3 : 2;
+    static constexpr int stages() {
+        int s = kMaxStages;
+        while (s > 1 && s * T::STAGE + 256 > 227 * 1024) --s;
+        return s;
+    }
+    static constexpr int kStages = stages();
     static size_t smem() { return (size_t)kStages * T::STAGE + 128 + kStages * sizeof(uint64_t); }
     static cudaError_t configure(int device, int num_sms, int* grid_cap) {
         auto kernel = batch_kernel<S, SRC, BX, BY, kStages>;
@@ -296,41 +312,35 @@ struct BatchLaunch {
     }
 };
 
+// Calls f with the BatchLaunch of tile geometry `geom`.
+template <typename S, int SRC, typename F>
+cudaError_t with_geom(int geom, F&& f) {
+    switch (geom) {
+        case 0: return f(BatchLaunch<S, SRC, 128, 8>());
+        case 1: return f(BatchLaunch<S, SRC, 64, 8>());
+        case 2: return f(BatchLaunch<S, SRC, 128, 4>());
+        case 3: return f(BatchLaunch<S, SRC, 128, 16>());
+        case 4: return f(BatchLaunch<S, SRC, 64, 16>());
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 template <typename S, int SRC>
 cudaError_t dispatch_geom(trtr_batch* b, int geom, int what, int parity, int interleaved, bool* enc_ok) {
-    // what: 0 configure, 1 launch, 2 encode descriptors
-    switch (geom) {
-        case 0: {
-            using L = BatchLaunch<S, SRC, 128, 8>;
-            if (what == 0) return L::configure(b->ctx[0]->device, b->ctx[0]->num_sms, &b->grid);
-            if (what == 1) return L::launch(b, parity, interleaved);
-            break;
-        }
-        case 1: {
-            using L = BatchLaunch<S, SRC, 64, 8>;
-            if (what == 0) return L::configure(b->ctx[0]->device, b->ctx[0]->num_sms, &b->grid);
-            if (what == 1) return L::launch(b, parity, interleaved);
-            break;
-        }
-        default: {
-            using L = BatchLaunch<S, SRC, 128, 4>;
-            if (what == 0) return L::configure(b->ctx[0]->device, b->ctx[0]->num_sms, &b->grid);
-            if (what == 1) return L::launch(b, parity, interleaved);
-            break;
-        }
-    }
-    // what == 2: descriptors are built host-side
+    // what: 0 configure, 1 launch, 2 encode descriptors (built host-side, then copied)
     using C = typename Store<S>::C;
-    std::vector<InstanceDesc<C>> h(b->count);
-    bool ok = geom == 0   ? BatchLaunch<S, SRC, 128, 8>::encode_desc(b, h.data())
-              : geom == 1 ? BatchLaunch<S, SRC, 64, 8>::encode_desc(b, h.data())
-                          : BatchLaunch<S, SRC, 128, 4>::encode_desc(b, h.data());
-    *enc_ok = ok;
-    if (!ok) return cudaErrorInvalidValue;
-    cudaError_t e = cudaMemcpyAsync(b->d_desc, h.data(), sizeof(InstanceDesc<C>) * b->count, cudaMemcpyHostToDevice,
-                                    b->stream);
-    if (e != cudaSuccess) return e;
-    return cudaStreamSynchronize(b->stream);  // h goes out of scope
+    return with_geom<S, SRC>(geom, [&](auto L) -> cudaError_t {
+        using Launch = decltype(L);
+        if (what == 0) return Launch::configure(b->ctx[0]->device, b->ctx[0]->num_sms, &b->grid);
+        if (what == 1) return Launch::launch(b, parity, interleaved);
+        std::vector<InstanceDesc<C>> h(b->count);
+        *enc_ok = Launch::encode_desc(b, h.data());
+        if (!*enc_ok) return cudaErrorInvalidValue;
+        cudaError_t e = cudaMemcpyAsync(b->d_desc, h.data(), sizeof(InstanceDesc<C>) * b->count,
+                                        cudaMemcpyHostToDevice, b->stream);
+        if (e != cudaSuccess) return e;
+        return cudaStreamSynchronize(b->stream);  // h goes out of scope
+    });
 }
 
 cudaError_t dispatch(trtr_batch* b, int geom, int what, int parity = 0, int interleaved = 0) {
@@ -552,7 +562,9 @@ const char* trtr_batch_config_name(int config) {
     static const char* names[trtr::kNumConfigs] = {
         "tile 128x8, interleaved",  "tile 128x8, chunked", "tile 128x8, chunked largest-first",
         "tile 64x8, interleaved",   "tile 64x8, chunked",  "tile 64x8, chunked largest-first",
-        "tile 128x4, interleaved",  "tile 128x4, chunked", "tile 128x4, chunked largest-first"};
+        "tile 128x4, interleaved",  "tile 128x4, chunked", "tile 128x4, chunked largest-first",
+        "tile 128x16, interleaved", "tile 128x16, chunked", "tile 128x16, chunked largest-first",
+        "tile 64x16, interleaved",  "tile 64x16, chunked",  "tile 64x16, chunked largest-first"};
     return config >= 0 && config < trtr::kNumConfigs ? names[config] : "invalid";
 }
 
