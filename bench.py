@@ -46,7 +46,8 @@ DEFAULT_WORKLOAD = "pulse4096_f32_varD_mms"
 BATCH_WORKLOADS = {"batch256_f32": ("f32", 4), "batch256_f16": ("f16", 2)}
 # gradient of the L2 misfit w.r.t. D through 2000 steps of a 512^2 pulse (discrete adjoint)
 ADJOINT_WORKLOADS = {"adjoint512_f32": "f32"}
-STEP_SOURCES = ["paper_2312_10316_gb300/csrc/trtr_step.cu", "paper_2312_10316_gb300/csrc/trtr_internal.cuh"]
+STEP_SOURCES = ["paper_2312_10316_gb300/csrc/trtr_step.cu", "paper_2312_10316_gb300/csrc/trtr_step_core.cuh",
+                "paper_2312_10316_gb300/csrc/trtr_internal.cuh"]
 
 
 def parse_args():

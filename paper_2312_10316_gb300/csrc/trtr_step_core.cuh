@@ -152,9 +152,15 @@ __device__ __forceinline__ V pulse_source(V x, V y, V cx, V cy, V inv_s2, V amp,
 }
 
 // The node update of Eq. (14) in moment space; g: pre-collision populations, out: P_i(x).
-template <class V>
+//
+// OFS: g and out are the offsets h_i = g_i - w_i phi_ref of the 2-byte storages.  The offset
+// folds into the moments: sum w_i = 1 gives phi = sum h_i + phi_ref; sum w_i e_i = 0 leaves the
+// first moments alone; sum w_i (e_ia e_ib - d_ab/3) = 0 leaves B_ab alone when its trace part
+// uses sum h_i / 3; and the rebuild is linear in m0 with weight w_i, so rebuilding from
+// sum h_i + s (in place of phi + s) gives the offsets of the results.
+template <typename V, bool OFS = false>
 __device__ __forceinline__ void collide_node(const V g[kQ], V ux, V uy, V ax, V ay, V Dh, V s, V magic, V w2_fixed,
-                                             bool tau2_fixed, V out[kQ]) {
+                                             bool tau2_fixed, V out[kQ], V phi_ref = V(0.f)) {
     using T = typename ScalarOf<V>::type;
     // relaxation rates: tau1 - 1/2 = 3 Dh (Sec. 2.4); tau2 from Lambda (Eq. (28)) or fixed
     const V t1m = V(T(3)) * Dh;
@@ -167,7 +173,9 @@ __device__ __forceinline__ void collide_node(const V g[kQ], V ux, V uy, V ax, V 
     const V p12 = g[1] + g[2], p34 = g[3] + g[4], p56 = g[5] + g[6], p78 = g[7] + g[8];
     const V d12 = g[1] - g[2], d34 = g[3] - g[4], d56 = g[5] - g[6], d78 = g[7] - g[8];
     const V pdiag = p56 + p78;
-    const V phi = (g[0] + p12) + (p34 + pdiag);
+    const V phis = (g[0] + p12) + (p34 + pdiag);  // sum of the inputs (phi, or phi - phi_ref)
+    V phi = phis;
+    if constexpr (OFS) phi = phis + phi_ref;
     const V jx = d12 + (d56 + d78);
     const V jy = d34 + (d56 - d78);
     const V pxx = p12 + pdiag;
@@ -177,10 +185,10 @@ __device__ __forceinline__ void collide_node(const V g[kQ], V ux, V uy, V ax, V 
     // a5 + a6 + a7: post-collision Hermite coefficients
     const V phux = phi * ux, phuy = phi * uy;
     const V euxx = phux * ux, euyy = phuy * uy, euxy = phux * uy;
-    const V m0 = phi + s;
+    const V m0 = phis + s;  // (OFS: its rebuild gives offsets)
     const V m1x = vfma(kh, vfma(phi, ax, ux * s), vfma(k1, jx - phux, phux));
     const V m1y = vfma(kh, vfma(phi, ay, uy * s), vfma(k1, jy - phuy, phuy));
-    const V third = phi * V(T(1.0 / 3.0));
+    const V third = phis * V(T(1.0 / 3.0));  // pairs with the input sums pxx, pyy
     const V Axx = vfma(k2, (pxx - third) - euxx, euxx);
     const V Ayy = vfma(k2, (pyy - third) - euyy, euyy);
     const V Axy = vfma(k2, pxy - euxy, euxy);
@@ -239,6 +247,9 @@ struct Pair<float> {
     static __device__ __forceinline__ F2 decode(float2 v, float) { return F2(v); }
     static __device__ __forceinline__ F2 decode(float a, float b, float) { return F2(a, b); }
     static __device__ __forceinline__ float2 encode(F2 v, float) { return v.v; }
+    static __device__ __forceinline__ F2 raw(float2 v) { return F2(v); }
+    static __device__ __forceinline__ F2 raw(float a, float b) { return F2(a, b); }
+    static __device__ __forceinline__ float2 encode_raw(F2 v) { return v.v; }
 };
 template <>
 struct Pair<__half> {
@@ -253,6 +264,10 @@ struct Pair<__half> {
     static __device__ __forceinline__ __half2 encode(F2 v, float off) {
         return __floats2half2_rn(v.v.x - off, v.v.y - off);
     }
+    // the stored offsets themselves (their w_i phi_ref is folded into the moments)
+    static __device__ __forceinline__ F2 raw(__half2 v) { return F2(__half22float2(v)); }
+    static __device__ __forceinline__ F2 raw(__half a, __half b) { return F2(__half2float(a), __half2float(b)); }
+    static __device__ __forceinline__ __half2 encode_raw(F2 v) { return __floats2half2_rn(v.v.x, v.v.y); }
 };
 template <>
 struct Pair<__nv_bfloat16> {
@@ -267,6 +282,11 @@ struct Pair<__nv_bfloat16> {
     static __device__ __forceinline__ __nv_bfloat162 encode(F2 v, float off) {
         return __floats2bfloat162_rn(v.v.x - off, v.v.y - off);
     }
+    static __device__ __forceinline__ F2 raw(__nv_bfloat162 v) { return F2(__bfloat1622float2(v)); }
+    static __device__ __forceinline__ F2 raw(__nv_bfloat16 a, __nv_bfloat16 b) {
+        return F2(__bfloat162float(a), __bfloat162float(b));
+    }
+    static __device__ __forceinline__ __nv_bfloat162 encode_raw(F2 v) { return __floats2bfloat162_rn(v.v.x, v.v.y); }
 };
 
 template <typename S, int SRC, int BX, int BY>
@@ -315,6 +335,7 @@ __device__ __forceinline__ void tile_row_pairs(const unsigned char* st, int r, i
     const float* sd = reinterpret_cast<const float*>(st + T::POP + T::U) + r * BX;
     const float* ss = reinterpret_cast<const float*>(st + T::POP + T::U + T::D) + r * BX;
     const float phi_ref = a.phi_ref;
+    constexpr bool kOfs = sizeof(S) == 2;  // offset storages: h_i = g_i - w_i phi_ref, folded into the moments
     S* dst = static_cast<S*>(a.dst);
     const size_t pl = a.lp.plane;
     const F2 magic(a.magic), w2f(a.omega2_fixed);
@@ -328,11 +349,10 @@ __device__ __forceinline__ void tile_row_pairs(const unsigned char* st, int r, i
 #pragma unroll
         for (int q = 0; q < kQ; ++q) {
             const S* pq = sp + q * T::PLANE_ELEMS + c + plane_offset<T::A>(q);
-            const float off = weight<float>(q) * phi_ref;
             if (plane_offset<T::A>(q) % 2 == 0)
-                g[q] = P::decode(*reinterpret_cast<const S2*>(pq), off);
+                g[q] = P::raw(*reinterpret_cast<const S2*>(pq));
             else
-                g[q] = P::decode(pq[0], pq[1], off);
+                g[q] = P::raw(pq[0], pq[1]);
         }
         // u, its central differences (ghosts make edges one-sided or periodic), D
         const float2 uc = *reinterpret_cast<const float2*>(su + c);
@@ -373,7 +393,8 @@ __device__ __forceinline__ void tile_row_pairs(const unsigned char* st, int r, i
         }
 
         F2 out[kQ];
-        collide_node<F2>(g, ux, uy, ax, ay, Dh, src, magic, w2f, a.tau2_fixed, out);
+        // 2-byte storages: g and out stay offsets (the offset is folded into the moments)
+        collide_node<F2, kOfs>(g, ux, uy, ax, ay, Dh, src, magic, w2f, a.tau2_fixed, out, F2(phi_ref));
 
         // a8: store P_i(x); edge nodes also write their periodic ghost copies
         const bool edge = j == 0 || j == ny - 1 || i == 0 || i + 1 >= nx - 1;
@@ -382,13 +403,13 @@ __device__ __forceinline__ void tile_row_pairs(const unsigned char* st, int r, i
             S* srow = const_cast<S*>(sp);
 #pragma unroll
             for (int q = 0; q < kQ; ++q)
-                *reinterpret_cast<S2*>(srow + q * T::PLANE_ELEMS + c) = P::encode(out[q], weight<float>(q) * phi_ref);
+                *reinterpret_cast<S2*>(srow + q * T::PLANE_ELEMS + c) = P::encode_raw(out[q]);
             const int nb = bulk_cols<S>(nx - i0);
             if ((edge || c + 1 >= nb) && i < nx) {  // ghost copies, and the columns past the bulk copy
 #pragma unroll
                 for (int q = 0; q < kQ; ++q) {
-                    const float off = weight<float>(q) * phi_ref;
-                    const S v0 = Store<S>::encode(out[q].v.x, off), v1 = Store<S>::encode(out[q].v.y, off);
+                    const S2 v = P::encode_raw(out[q]);
+                    const S v0 = reinterpret_cast<const S*>(&v)[0], v1 = reinterpret_cast<const S*>(&v)[1];
                     if (c >= nb) dst[q * pl + a.lp.at(i, j)] = v0;
                     if (c + 1 >= nb && i + 1 < nx) dst[q * pl + a.lp.at(i + 1, j)] = v1;
                     store_ghosts(dst + q * pl, a.lp, i, j, v0);
@@ -399,13 +420,13 @@ __device__ __forceinline__ void tile_row_pairs(const unsigned char* st, int r, i
             S* d0 = dst + a.lp.at(i, j);
 #pragma unroll
             for (int q = 0; q < kQ; ++q)
-                *reinterpret_cast<S2*>(d0 + q * pl) = P::encode(out[q], weight<float>(q) * phi_ref);
+                *reinterpret_cast<S2*>(d0 + q * pl) = P::encode_raw(out[q]);
         } else {
 #pragma unroll
             for (int q = 0; q < kQ; ++q) {
-                const float off = weight<float>(q) * phi_ref;
-                store_with_ghosts(dst + q * pl, a.lp, i, j, Store<S>::encode(out[q].v.x, off));
-                if (i + 1 < nx) store_with_ghosts(dst + q * pl, a.lp, i + 1, j, Store<S>::encode(out[q].v.y, off));
+                const S2 v = P::encode_raw(out[q]);
+                store_with_ghosts(dst + q * pl, a.lp, i, j, reinterpret_cast<const S*>(&v)[0]);
+                if (i + 1 < nx) store_with_ghosts(dst + q * pl, a.lp, i + 1, j, reinterpret_cast<const S*>(&v)[1]);
             }
         }
     }
