@@ -121,14 +121,17 @@ __device__ __forceinline__ double pulse_phi(const PulseTime& pt, double x, doubl
 
 // Third-order Hermite equilibrium (Eq. (6)) in lattice units, in FP64:
 // w_i phi [1 + 3 eu + 4.5 ((eu)^2 - |u|^2/3) + 4.5 ((eu)^3 - eu |u|^2)], eu = e_i . uhat.
-__device__ __forceinline__ double equilibrium(int q, double phi, double u, double v) {
-    const double eu = c_ex[q] * u + c_ey[q] * v;
-    const double uu = u * u + v * v;
-    return c_w[q] * phi * (1.0 + 3.0 * eu + 4.5 * (eu * eu - uu / 3.0) + 4.5 * (eu * eu * eu - eu * uu));
+template <typename T>
+__device__ __forceinline__ T equilibrium(int q, T phi, T u, T v) {
+    const T eu = T(c_ex[q]) * u + T(c_ey[q]) * v;
+    const T uu = u * u + v * v;
+    return T(c_w[q]) * phi *
+           (T(1) + T(3) * eu + T(4.5) * (eu * eu - uu / T(3)) + T(4.5) * (eu * eu * eu - eu * uu));
 }
 
-// Initial condition g_i(x) = g_i^eq(phi0(x), u(x)) stored in the pull layout:
-// P_i(x) = g_i(x + e_i).
+// Initial condition g_i(x) = g_i^eq(phi0(x), u(x)) in the pull layout: node x evaluates phi0
+// once (FP64) and its nine equilibria in the compute type, and stores g_i(x) where x pulls it,
+// P_i(x - e_i), periodic images included (each slot has exactly one writer).
 template <typename S, typename C>
 __global__ void init_eq_kernel(S* P, const C* uv, const double* phi0, PlaneLayout lp, PlaneLayout lf, double x0,
                                double y0, double dx, PulseTime pt, C phi_ref) {
@@ -136,11 +139,13 @@ __global__ void init_eq_kernel(S* P, const C* uv, const double* phi0, PlaneLayou
     const size_t n = (size_t)nx * ny;
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
         const int j = (int)(k / nx), i = (int)(k - (size_t)j * nx);
+        const C phi = (C)(phi0 ? phi0[k] : pulse_phi(pt, x0 + i * dx, y0 + j * dx));
+        const C u = uv[lf.at(i, j)], v = uv[lf.plane + lf.at(i, j)];
+#pragma unroll
         for (int q = 0; q < kQ; ++q) {
-            const int si = wrap(i + c_ex[q], nx), sj = wrap(j + c_ey[q], ny);
-            const double phi = phi0 ? phi0[(size_t)sj * nx + si] : pulse_phi(pt, x0 + si * dx, y0 + sj * dx);
-            const double geq = equilibrium(q, phi, (double)uv[lf.at(si, sj)], (double)uv[lf.plane + lf.at(si, sj)]);
-            store_with_ghosts(P + q * lp.plane, lp, i, j, Store<S>::encode((C)geq, (C)(c_w[q]) * phi_ref));
+            const int ti = wrap(i - c_ex[q], nx), tj = wrap(j - c_ey[q], ny);
+            store_with_ghosts(P + q * lp.plane, lp, ti, tj,
+                              Store<S>::encode(equilibrium<C>(q, phi, u, v), (C)(c_w[q]) * phi_ref));
         }
     }
 }
