@@ -157,6 +157,7 @@ struct trtr_ctx {
     size_t dtmp_len;  // in doubles
     double* phib;     // Dirichlet values of the edge nodes (TRTR_BC_DIRICHLET_NEE)
     bool fields_set, pulse_set, initialized, maps_ready, dirichlet_set;
+    bool small_tiles;  // step kernel geometry for small grids (chosen by encode_maps)
     trtr::Pulse pulse;
     long step;
     long launches;

@@ -97,22 +97,37 @@ using Sweep = Geom<S, SRC>;
 
 template <typename S, int SRC>
 struct Pipe {
+    static constexpr int BX = kBX;
     static constexpr int BY = Sweep<S, SRC>::BY, WPR = Sweep<S, SRC>::WPR, CTAS = Sweep<S, SRC>::CTAS,
                          STAGES = Sweep<S, SRC>::STAGES, ORDER = Sweep<S, SRC>::ORDER;
     static constexpr bool TST = Sweep<S, SRC>::TST != 0 && WPR == 1;
     static constexpr int THREADS = 32 * BY * WPR;
-    static constexpr int PAIRS = kBX / 64 / WPR;  // node pairs per lane (FP64: 2 PAIRS nodes)
+    static constexpr int PAIRS = BX / 64 / WPR;  // node pairs per lane (FP64: 2 PAIRS nodes)
     static_assert(BY >= 1 && CTAS >= 1 && STAGES >= 1 && THREADS <= 1024, "pipeline geometry");
     static_assert((WPR == 1 || WPR == 2) && PAIRS >= 1, "warps per row");
 };
 
-template <typename S, int SRC, int STAGES>
-__global__ void __launch_bounds__(Pipe<S, SRC>::THREADS, Pipe<S, SRC>::CTAS)
+// Small grids: with the geometry above a grid of a few hundred nodes per side has fewer tiles
+// than SMs, and each step is one tile's load-compute-store latency.  64 x 8 tiles, two
+// 256-thread CTAs per SM, one node pair per lane, spread such a grid over the whole GPU.
+// Chosen when the geometry above would give fewer than TRTR_SMALL_TILES_PER_SM tiles per SM.
+#ifndef TRTR_SMALL_TILES_PER_SM
+#define TRTR_SMALL_TILES_PER_SM 2
+#endif
+template <typename S, int SRC>
+struct SmallPipe {
+    static constexpr int BX = 64, BY = 8, WPR = 1, CTAS = 2, STAGES = 2, ORDER = 0;
+    static constexpr bool TST = false;
+    static constexpr int THREADS = 32 * BY * WPR;
+    static constexpr int PAIRS = BX / 64 / WPR;
+};
+
+template <typename S, int SRC, int STAGES, class G>
+__global__ void __launch_bounds__(G::THREADS, G::CTAS)
     step_kernel(const __grid_constant__ CUtensorMap mp, const __grid_constant__ CUtensorMap mu,
                 const __grid_constant__ CUtensorMap md, const __grid_constant__ CUtensorMap ms,
                 const StepArgs<typename Store<S>::C> a) {
-    using G = Pipe<S, SRC>;
-    constexpr int kBY = G::BY, kWPR = G::WPR, kPairsPerLane = G::PAIRS;
+    constexpr int kBX = G::BX, kBY = G::BY, kWPR = G::WPR, kPairsPerLane = G::PAIRS;
     constexpr bool kTST = G::TST;
     using T = Tile<S, SRC, kBX, kBY>;
     constexpr bool kPairs = !std::is_same<S, double>::value;
@@ -207,22 +222,22 @@ __global__ void __launch_bounds__(Pipe<S, SRC>::THREADS, Pipe<S, SRC>::CTAS)
     if (kTST && lane == 0) bulk_wait_all();  // this warp's row copies have completed
 }
 
-// Stages per CTA: Pipe<S, SRC>::STAGES, or fewer while they do not fit in the 227 KB a CTA may use.
-template <typename S, int SRC>
+// Stages per CTA: G::STAGES, or fewer while they do not fit in the 227 KB a CTA may use.
+template <typename S, int SRC, class G>
 constexpr int stages_for() {
-    constexpr int kStage = Tile<S, SRC, kBX, Pipe<S, SRC>::BY>::STAGE;
+    constexpr int kStage = Tile<S, SRC, G::BX, G::BY>::STAGE;
     static_assert(kStage + 256 <= 227 * 1024, "one tile stage must fit in shared memory");
-    int s = Pipe<S, SRC>::STAGES;
+    int s = G::STAGES;
     while (s > 1 && s * kStage + 256 > 227 * 1024) --s;
     return s;
 }
 
 // ------------------------------------------------------------------------------ host side
 
-template <typename S, int SRC>
+template <typename S, int SRC, class G>
 cudaError_t encode_typed(trtr_ctx* ctx) {
     using C = typename Store<S>::C;
-    constexpr int kBY = Pipe<S, SRC>::BY;
+    constexpr int kBX = G::BX, kBY = G::BY;
     // The box shapes do not depend on the source mode (TX bytes do).
     using T = Tile<S, TRTR_SRC_NONE, kBX, kBY>;
     bool ok = true;
@@ -237,13 +252,13 @@ cudaError_t encode_typed(trtr_ctx* ctx) {
 
 // One step from the population buffer described by src_map into dst, as step `step` (its
 // source terms and first-step rule).
-template <typename S, int SRC>
+template <typename S, int SRC, class G>
 cudaError_t launch_typed(trtr_ctx* ctx, const CUtensorMap& src_map, void* dst, long step) {
     using C = typename Store<S>::C;
-    constexpr int kBY = Pipe<S, SRC>::BY, kThreads = Pipe<S, SRC>::THREADS;
+    constexpr int kBX = G::BX, kBY = G::BY, kThreads = G::THREADS;
     using T = Tile<S, SRC, kBX, kBY>;
-    constexpr int kStages = stages_for<S, SRC>();
-    auto kernel = step_kernel<S, SRC, kStages>;
+    constexpr int kStages = stages_for<S, SRC, G>();
+    auto kernel = step_kernel<S, SRC, kStages, G>;
     const size_t smem = (size_t)kStages * T::STAGE + 128 + kStages * sizeof(uint64_t);
     static int configured_device = -1;
     static int ctas_per_sm = 1;
@@ -290,21 +305,42 @@ cudaError_t launch_typed(trtr_ctx* ctx, const CUtensorMap& src_map, void* dst, l
     return cudaGetLastError();
 }
 
-template <typename S>
-cudaError_t launch_src(trtr_ctx* ctx, const CUtensorMap& src_map, void* dst, long step) {
-    switch (ctx->p.src_mode) {
-        case TRTR_SRC_FIELD: return launch_typed<S, TRTR_SRC_FIELD>(ctx, src_map, dst, step);
-        case TRTR_SRC_PULSE: return launch_typed<S, TRTR_SRC_PULSE>(ctx, src_map, dst, step);
-        default: return launch_typed<S, TRTR_SRC_NONE>(ctx, src_map, dst, step);
-    }
+template <typename S, int SRC>
+cudaError_t launch_geom(trtr_ctx* ctx, const CUtensorMap& src_map, void* dst, long step) {
+    return ctx->small_tiles ? launch_typed<S, SRC, SmallPipe<S, SRC>>(ctx, src_map, dst, step)
+                            : launch_typed<S, SRC, Pipe<S, SRC>>(ctx, src_map, dst, step);
 }
 
 template <typename S>
+cudaError_t launch_src(trtr_ctx* ctx, const CUtensorMap& src_map, void* dst, long step) {
+    switch (ctx->p.src_mode) {
+        case TRTR_SRC_FIELD: return launch_geom<S, TRTR_SRC_FIELD>(ctx, src_map, dst, step);
+        case TRTR_SRC_PULSE: return launch_geom<S, TRTR_SRC_PULSE>(ctx, src_map, dst, step);
+        default: return launch_geom<S, TRTR_SRC_NONE>(ctx, src_map, dst, step);
+    }
+}
+
+template <typename S, class G>
+cudaError_t encode_pop_geom(trtr_ctx* ctx, void* buffer, CUtensorMap* out) {
+    using T = Tile<S, TRTR_SRC_NONE, G::BX, G::BY>;
+    return encode(out, tma_type<S>(), sizeof(S), buffer, ctx->lp, kQ, T::PW, G::BY, 1) ? cudaSuccess
+                                                                                      : cudaErrorInvalidValue;
+}
+
+// population maps of the source-free kernel (the adjoint's recomputation)
+template <typename S>
 cudaError_t encode_pop_typed(trtr_ctx* ctx, void* buffer, CUtensorMap* out) {
-    // population maps of the source-free kernel (the adjoint's recomputation)
-    using T = Tile<S, TRTR_SRC_NONE, kBX, Pipe<S, TRTR_SRC_NONE>::BY>;
-    return encode(out, tma_type<S>(), sizeof(S), buffer, ctx->lp, kQ, T::PW, Pipe<S, TRTR_SRC_NONE>::BY, 1) ? cudaSuccess
-                                                                                    : cudaErrorInvalidValue;
+    return ctx->small_tiles ? encode_pop_geom<S, SmallPipe<S, TRTR_SRC_NONE>>(ctx, buffer, out)
+                            : encode_pop_geom<S, Pipe<S, TRTR_SRC_NONE>>(ctx, buffer, out);
+}
+
+template <typename S, int SRC>
+cudaError_t encode_geom(trtr_ctx* ctx) {
+    // the small-grid geometry when the large one leaves most SMs without a second tile
+    using G = Pipe<S, SRC>;
+    const long tiles = (long)((ctx->lp.nx + G::BX - 1) / G::BX) * ((ctx->lp.ny + G::BY - 1) / G::BY);
+    ctx->small_tiles = tiles < (long)TRTR_SMALL_TILES_PER_SM * ctx->num_sms;
+    return ctx->small_tiles ? encode_typed<S, SRC, SmallPipe<S, SRC>>(ctx) : encode_typed<S, SRC, G>(ctx);
 }
 
 }  // namespace
@@ -312,12 +348,13 @@ cudaError_t encode_pop_typed(trtr_ctx* ctx, void* buffer, CUtensorMap* out) {
 template <typename S>
 cudaError_t encode_src(trtr_ctx* ctx) {
     switch (ctx->p.src_mode) {
-        case TRTR_SRC_FIELD: return encode_typed<S, TRTR_SRC_FIELD>(ctx);
-        case TRTR_SRC_PULSE: return encode_typed<S, TRTR_SRC_PULSE>(ctx);
-        default: return encode_typed<S, TRTR_SRC_NONE>(ctx);
+        case TRTR_SRC_FIELD: return encode_geom<S, TRTR_SRC_FIELD>(ctx);
+        case TRTR_SRC_PULSE: return encode_geom<S, TRTR_SRC_PULSE>(ctx);
+        default: return encode_geom<S, TRTR_SRC_NONE>(ctx);
     }
 }
 
+// Encodes the context's TMA descriptors and picks its tile geometry (ctx->small_tiles).
 cudaError_t encode_maps(trtr_ctx* ctx) {
     switch (ctx->p.precision) {
         case TRTR_F64: return encode_src<double>(ctx);

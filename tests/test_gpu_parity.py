@@ -101,6 +101,40 @@ def test_random_state_steps(nx, ny, prec, src_mode):
         assert abs(s.mass() - o.mass()) <= 10 * ONE_STEP_TOL[prec] * abs(o.mass())
 
 
+@pytest.mark.parametrize("prec,src_mode", [("f64", 0), ("f64", 1), ("f64", 2), ("f32", 0), ("f32", 1), ("f32", 2),
+                                           ("f16", 0), ("f16", 2), ("bf16", 2)])
+def test_large_geometry_ragged_grid(prec, src_mode):
+    """1101 x 700 nodes: enough tiles for the large-grid step geometry (128 x 16 tiles, or 128 x 8
+    for FP64 and the FP32 source fields; at least two per SM on a 152-SM GPU), with a ragged last
+    tile column (77 nodes: the FP32 pulse path's bulk row copies leave its last column, the
+    2-byte storages' its last five, to the lanes) and a ragged last tile row.  Two steps from
+    random populations against the oracle; the 2-byte storages use phi_ref = 1."""
+    nx, ny = 1101, 700
+    case = random_case(900 + src_mode, nx, ny)
+    pulse = (0.0, -0.1, 0.05, 0.2, 5e-3, 0.5) if src_mode == 2 else None
+    phi_ref = 1.0 if prec in ("f16", "bf16") else 0.0
+    o, s = _pair(case, nx, ny, PREC[prec], src_mode, 1, 0, phi_ref=phi_ref, pulse=pulse)
+    with s:
+        S1 = case["S1"] if src_mode == 1 else None
+        o.set_fields(case["ux"], case["uy"], case["D"])
+        s.set_fields(case["ux"], case["uy"], case["D"], S1)
+        if src_mode == 1:
+            o.set_source(S1)
+        if src_mode == 2:
+            s.set_pulse(*pulse)
+            s.set_fields(case["ux"], case["uy"], case["D"])
+        o.set_g(case["g"], step=5)
+        s.set_populations(case["g"], step=5)
+        for k in range(2):
+            o.step(1)
+            s.step(1)
+            assert rel_l2(s.get_populations(), o.get_g()) <= ONE_STEP_TOL[prec], (k, prec)
+            if src_mode == 1:
+                o.set_source(case["S2"])
+                s.set_source(case["S2"])
+        assert rel_l2(s.moments(), o.phi()) <= ONE_STEP_TOL[prec]
+
+
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_tau1_const_and_fixed_tau2(prec):
     nx, ny = 45, 38
