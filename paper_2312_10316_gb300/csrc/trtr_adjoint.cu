@@ -73,6 +73,10 @@ __global__ void __launch_bounds__(kThreads)
                     const typename Store<S>::C* __restrict__ uv, const typename Store<S>::C* __restrict__ Dh,
                     PlaneLayout lp, PlaneLayout lf,
                     PlaneLayout lq, C phi_ref, int tau2_fixed, C magic, C w2_fixed, double dtau1_dD, int d_enters) {
+    // programmatic dependent launch (as the step kernel): let the next launch be set up, then
+    // wait for the kernels before this one
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const size_t n = (size_t)lp.nx * lp.ny;
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
         const int j = (int)(k / lp.nx), i = (int)(k - (size_t)j * lp.nx);
@@ -289,16 +293,28 @@ trtr_status trtr_adjoint(trtr_ctx* ctx, const double* dJ_dphi, int on_device, do
         for (long k = 0; k + 1 < len && e == cudaSuccess; ++k)
             e = trtr::launch_step_from(ctx, &a->pool_maps[k], a->pool[k + 1], a->n0 + s0 + k);
         for (long k = len - 1; k >= 0 && e == cudaSuccess; --k) {
+            cudaError_t le = cudaSuccess;
             e = trtr::dispatch(ctx, [&](auto* sp, auto* cp) {
                 using S = std::remove_pointer_t<decltype(sp)>;
                 using C = std::remove_pointer_t<decltype(cp)>;
                 using F = typename trtr::Store<S>::C;
-                trtr::adj_step_kernel<S, C><<<grid, trtr::kThreads, 0, st>>>(
-                    (const S*)a->pool[k], (const C*)a->Q[qc], (C*)a->Q[qc ^ 1], a->grad, (const F*)ctx->uv,
-                    (const F*)ctx->Dh, ctx->lp, ctx->lf, a->lq, (C)ctx->p.phi_ref,
-                    ctx->p.tau2_mode == TRTR_TAU2_FIXED, (C)ctx->p.magic,
-                    (C)(ctx->p.tau2_mode == TRTR_TAU2_FIXED ? 1.0 / ctx->p.tau2 : 0.0), dtau1_dD, d_enters);
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3(grid);
+                cfg.blockDim = dim3(trtr::kThreads);
+                cfg.stream = st;
+                cudaLaunchAttribute attr[1];
+                attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+                attr[0].val.programmaticStreamSerializationAllowed = 1;
+                cfg.attrs = attr;
+                cfg.numAttrs = 1;
+                le = cudaLaunchKernelEx(&cfg, trtr::adj_step_kernel<S, C>, (const S*)a->pool[k], (const C*)a->Q[qc],
+                                   (C*)a->Q[qc ^ 1], a->grad, (const F*)ctx->uv, (const F*)ctx->Dh, ctx->lp, ctx->lf,
+                                   a->lq, (C)ctx->p.phi_ref, (int)(ctx->p.tau2_mode == TRTR_TAU2_FIXED),
+                                   (C)ctx->p.magic,
+                                   (C)(ctx->p.tau2_mode == TRTR_TAU2_FIXED ? 1.0 / ctx->p.tau2 : 0.0), dtau1_dD,
+                                   d_enters);
             });
+            if (e == cudaSuccess) e = le;
             qc ^= 1;
         }
         ctx->launches += 2 * len;

@@ -122,6 +122,10 @@ struct SmallPipe {
     static constexpr int PAIRS = BX / 64 / WPR;
 };
 
+#ifndef TRTR_STEP_PDL
+#define TRTR_STEP_PDL 1  // launch the step with programmatic dependent launch
+#endif
+
 template <typename S, int SRC, int STAGES, class G>
 __global__ void __launch_bounds__(G::THREADS, G::CTAS)
     step_kernel(const __grid_constant__ CUtensorMap mp, const __grid_constant__ CUtensorMap mu,
@@ -165,6 +169,11 @@ __global__ void __launch_bounds__(G::THREADS, G::CTAS)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
+    // Programmatic dependent launch: the next launch on the stream may be set up from here on,
+    // and nothing written by earlier kernels is read before they have completed (both no-ops
+    // when the launch does not allow it).
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if (tid == 0) {
         for (int k = 0; k < STAGES && k < my_tiles; ++k)
             issue_tile<S, SRC, kBX, kBY>(smem + k * T::STAGE, &full[k], &mp, &mu, &md, &ms, tile_x0(k), tile_y0(k), a);
@@ -301,8 +310,19 @@ cudaError_t launch_typed(trtr_ctx* ctx, const CUtensorMap& src_map, void* dst, l
     const long ntiles = (long)((ctx->lp.nx + kBX - 1) / kBX) * ((ctx->lp.ny + kBY - 1) / kBY);
     const long cap = (long)ctx->num_sms * ctas_per_sm;
     const int grid = (int)(ntiles < cap ? ntiles : cap);
-    kernel<<<grid, kThreads, smem, ctx->stream>>>(src_map, ctx->maps[kMapU], ctx->maps[kMapD], ctx->maps[kMapS], a);
-    return cudaGetLastError();
+    // launched with programmatic stream serialisation: the launch overlaps the tail of the
+    // kernel before it, whose results the kernel waits for (griddepcontrol.wait)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = TRTR_STEP_PDL;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, src_map, ctx->maps[kMapU], ctx->maps[kMapD], ctx->maps[kMapS], a);
 }
 
 template <typename S, int SRC>
