@@ -504,6 +504,8 @@ def run_batch(args):
                      "bytes_per_node": bpn, "kernel": "batch_kernel"},
         "gpu_launches": args.steps,
         "clocks": clk,
+        "cpu_baseline": None if args.no_cpu_baseline else cpu_baseline(
+            max(pulses, key=lambda p: p.nx * p.ny), args.cpu_seconds),
         "batch": {"solves_per_s": round(solves_per_s, 3), "steps_per_solve": pulses[0].steps,
                   "per_instance_launch_glups": round(base_value, 3),
                   "speedup_vs_per_instance_launches": round(value / world / base_value, 3),
@@ -548,11 +550,17 @@ def run_adjoint(args):
             misfit_and_gradient(s, dev["ux"], dev["uy"], D, dev["phi0"], phi_obs, steps)
         torch.cuda.synchronize()
         launches0 = s.launches
+        props = torch.cuda.get_device_properties(local)
+        uuid = str(getattr(props, "uuid", "")) or None
+        clocks = ClockSampler(("GPU-" + uuid) if uuid and not uuid.startswith("GPU-") else uuid)
+        clocks.start()
+        time.sleep(0.4)
         t0 = time.perf_counter()
         for _ in range(evals):
             J, g = misfit_and_gradient(s, dev["ux"], dev["uy"], D, dev["phi0"], phi_obs, steps)
         torch.cuda.synchronize()
         t_grad = (time.perf_counter() - t0) / evals
+        clk = clocks.stop()
         launches_per_gradient = (s.launches - launches0) // evals
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s.init_equilibrium(dev["phi0"])
@@ -566,6 +574,14 @@ def run_adjoint(args):
     if rank != 0:
         return None
     value = steps * n * n / t_grad / 1e9
+    # algorithmic bytes per node and step of one gradient: the recorded forward step and its
+    # recomputation (84 B each in FP32) and the adjoint step (9 populations and 9 + 9 adjoint
+    # values, u, D, the FP64 gradient read and written: 136 B)
+    pb = 8 if prec == T.TRTR_F64 else 4
+    bpn = 2 * algorithmic_bytes_per_node(pb, pb) + (27 * pb + 3 * pb + 16)
+    peak, peak_kind = measured_hbm_peak()
+    achieved = bpn * n * n * steps / t_grad / 1e9
+    cpu = None if args.no_cpu_baseline else adjoint_cpu_baseline(args.cpu_seconds)
     return {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": evals,
         "warmup": args.warmup, "ms_per_step": round(t_grad * 1e3 / steps, 5), "higher_is_better": True,
@@ -580,7 +596,40 @@ def run_adjoint(args):
                     "checkpoint_memory_MB": round((interval + (steps + interval - 1) // interval) * state_mb, 1),
                     "misfit": float(J)},
         "gpu_launches": launches_per_gradient * evals,
+        "clocks": clk,
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": f"{peak_kind} copy bandwidth",
+                     "bytes_per_node": bpn, "kernel": "step_kernel + adj_step_kernel",
+                     "note": "512^2: the 22 MB per step stay in L2 and each launch is latency-bound"},
+        "cpu_baseline": cpu,
     }
+
+
+def adjoint_cpu_baseline(seconds: float):
+    """The oracle's discrete adjoint (it keeps every state, so a bounded sample: 64^2 grid,
+    120 steps per gradient) in forward node-steps per second of a gradient evaluation."""
+    import numpy as np
+
+    import oracle
+
+    n, steps = 64, 120
+    pulse = W.Pulse(n=n, courant=0.8)
+    f = W.fields(pulse)
+    sp = oracle.SimParams(nx=n, ny=n, dx=pulse.dx, dt=pulse.dt, grad_mode=1)
+    lam = np.ones((n, n))
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        o = oracle.Sim(sp)
+        o.set_fields(f["ux"], f["uy"], f["D"])
+        o.init_equilibrium(f["phi0"])
+        o.adjoint(steps, lam)
+        o.close()
+        reps += 1
+        el = time.perf_counter() - t0
+        if el > seconds or reps >= 200:
+            break
+    return {"value": reps * steps * n * n / el / 1e9, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{reps} gradient(s) of the oracle's adjoint over a 64x64 pulse, {steps} steps each ({el:.1f} s)"}
 
 
 def run_table2(args):
