@@ -153,7 +153,9 @@ trtr_status trtr_set_pulse(trtr_ctx* ctx, double omega, double xc, double yc, do
 trtr_status trtr_init_equilibrium(trtr_ctx* ctx, const double* phi0, int on_device);
 
 /* Advances n >= 0 time steps of Eq. (14): one fused pull-stream + collide kernel per step on
- * the context's stream, ping-pong buffers, no host synchronisation (unless check_every). */
+ * the context's stream (plus the boundary pass with TRTR_BC_DIRICHLET_NEE), ping-pong buffers,
+ * no host synchronisation (unless check_every).  The step kernels use programmatic dependent
+ * launch: each waits for the work before it on the stream before reading its results. */
 trtr_status trtr_step(trtr_ctx* ctx, long n);
 
 /* phi(x, t_n) = sum_i g_i(x, t_n) of the pre-collision populations (B_0^neq = 0, Sec. 2.2),
