@@ -40,6 +40,10 @@ WORKLOADS = {
     "pulse8192_bf16_varD_mms": (W.C3_HALF_8192, "bf16", 2),
     "pulse8192_f32_varD_mms": (W.C3_HALF_8192, "f32", 4),
     "pulse4096_f16_varD_mms": (W.C2B_F32_4096, "f16", 2),
+    # small grids (constant D, S = 0): launch- and latency-bound steps
+    "pulse256_f32_constD": (W.Pulse(n=256, courant=0.8, name="pulse256_f32_constD"), "f32", 4),
+    "pulse512_f32_constD": (W.Pulse(n=512, courant=0.8, name="pulse512_f32_constD"), "f32", 4),
+    "pulse2048_f32_constD": (W.Pulse(n=2048, courant=0.8, name="pulse2048_f32_constD"), "f32", 4),
 }
 DEFAULT_WORKLOAD = "pulse4096_f32_varD_mms"
 # batched workloads: 256 seeded pulses, square grids drawn from {64 ... 1024}, one launch per step
@@ -68,6 +72,9 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--parity-steps", type=int, default=1000,
                     help="steps of the FP64 GPU comparison run that states the L2 error (0: skip)")
+    ap.add_argument("--src", default="auto", choices=["auto", "none", "field", "pulse"],
+                    help="source mode of the timed step kernel (auto: the workload's; 'field' uses the "
+                         "manufactured source as a stationary field); other than auto skips parity and e2e")
     return ap.parse_args()
 
 
@@ -262,7 +269,13 @@ def run_ours(args):
     n_nodes = pulse.nx * pulse.ny
 
     # ---- device-resident throughput
-    solver = T.pulse_solver(pulse, precision=prec, stream=sh)
+    src_override = {"auto": None, "none": T.TRTR_SRC_NONE, "field": T.TRTR_SRC_FIELD,
+                    "pulse": T.TRTR_SRC_PULSE}[args.src]
+    if src_override is not None:
+        args.parity_steps, args.no_e2e = 0, True
+    solver = T.pulse_solver(pulse, precision=prec, stream=sh, src_mode=src_override)
+    if src_override == T.TRTR_SRC_FIELD:
+        solver.set_source(W.source(pulse, 0.0))  # the manufactured source as a stationary field
     solver.step(args.warmup)
     solver.sync()
     barrier(world)
@@ -292,9 +305,11 @@ def run_ours(args):
     avg_launch_ms = sum(per_launch) / len(per_launch)
 
     bpn = algorithmic_bytes_per_node(pop_bytes)
+    if src_override == T.TRTR_SRC_FIELD:
+        bpn += 2 * (8 if prec == T.TRTR_F64 else 4)  # S^n and S^{n-1} planes in the compute type
     peak, peak_kind = measured_hbm_peak()
     achieved = bpn * n_nodes / (avg_launch_ms * 1e-3) / 1e9
-    traffic = ncu_traffic(args.workload)
+    traffic = ncu_traffic(args.workload) if src_override is None else None
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_kind": f"{peak_kind} copy bandwidth", "bytes_per_node": bpn,
@@ -359,7 +374,9 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": prec_key, "data": "synthetic",
         "config": {"workload": args.workload, "nx": pulse.nx, "ny": pulse.ny, "precision": prec_key,
                    "courant": pulse.courant, "D": f"{pulse.D0}*(1+{pulse.D_amp} sin(pi x) sin(pi y))",
-                   "source": "manufactured (in-kernel)" if pulse.D_amp else "none",
+                   "source": ("manufactured (in-kernel)" if pulse.D_amp else "none") if src_override is None
+                   else {"none": "none (override)", "field": "manufactured, as a stationary field (override)",
+                         "pulse": "manufactured (in-kernel, override)"}[args.src],
                    "omega": pulse.omega, "sigma0": pulse.sigma0,
                    "tau2": "magic 1/12" if pulse.tau2 is None else pulse.tau2, "parallelism": f"replicas{world}",
                    "l2_flush": f"inputs larger than L2: {2 * 9 * pop_bytes * n_nodes / 1e9:.2f} GB of populations"},

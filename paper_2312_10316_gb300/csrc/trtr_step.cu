@@ -50,25 +50,28 @@ constexpr int kBX = 128;  // nodes per tile along x
 // mode, whose stages carry two more planes, runs two CTAs per SM on 128 x 8 tiles so that each
 // still has two stages.  The TRTR_STEP_* macros override the geometry of the storages of
 // TRTR_STEP_SIZE bytes in source mode TRTR_STEP_SRC (sweeps).
+//
+// SMALL_BELOW: grids with fewer than this many of these tiles per SM take the small-grid
+// geometry (SmallPipe below) instead; measured per storage and source mode.
 template <typename S, int SRC>
 struct Geom {  // FP64
-    static constexpr int BY = 8, WPR = 1, CTAS = 2, STAGES = 2, ORDER = 2, TST = 0;
+    static constexpr int BY = 8, WPR = 1, CTAS = 2, STAGES = 2, ORDER = 2, TST = 0, SMALL_BELOW = 2;
 };
 template <int SRC>
 struct Geom<float, SRC> {  // pulse source
-    static constexpr int BY = 16, WPR = 1, CTAS = 1, STAGES = 2, ORDER = 0, TST = 1;
+    static constexpr int BY = 16, WPR = 1, CTAS = 1, STAGES = 2, ORDER = 0, TST = 1, SMALL_BELOW = 2;
 };
 template <>
-struct Geom<float, TRTR_SRC_NONE> {
-    static constexpr int BY = 16, WPR = 1, CTAS = 1, STAGES = 2, ORDER = 2, TST = 0;
+struct Geom<float, TRTR_SRC_NONE> {  // the small tiles win up to 4096^2 here (not at 8192^2)
+    static constexpr int BY = 16, WPR = 1, CTAS = 1, STAGES = 2, ORDER = 2, TST = 0, SMALL_BELOW = 100;
 };
 template <>
 struct Geom<float, TRTR_SRC_FIELD> {
-    static constexpr int BY = 8, WPR = 1, CTAS = 2, STAGES = 2, ORDER = 0, TST = 0;
+    static constexpr int BY = 8, WPR = 1, CTAS = 2, STAGES = 2, ORDER = 0, TST = 0, SMALL_BELOW = 2;
 };
 template <int SRC>
 struct Geom<__half, SRC> {
-    static constexpr int BY = 16, WPR = 1, CTAS = 1, STAGES = 3, ORDER = 0, TST = 0;
+    static constexpr int BY = 16, WPR = 1, CTAS = 1, STAGES = 3, ORDER = 0, TST = 0, SMALL_BELOW = 2;
 };
 template <int SRC>
 struct Geom<__nv_bfloat16, SRC> : Geom<__half, SRC> {};
@@ -110,10 +113,8 @@ struct Pipe {
 // Small grids: with the geometry above a grid of a few hundred nodes per side has fewer tiles
 // than SMs, and each step is one tile's load-compute-store latency.  64 x 8 tiles, two
 // 256-thread CTAs per SM, one node pair per lane, spread such a grid over the whole GPU.
-// Chosen when the geometry above would give fewer than TRTR_SMALL_TILES_PER_SM tiles per SM.
-#ifndef TRTR_SMALL_TILES_PER_SM
-#define TRTR_SMALL_TILES_PER_SM 2
-#endif
+// Chosen when the geometry above would give fewer than Geom::SMALL_BELOW tiles per SM
+// (TRTR_SMALL_TILES_PER_SM overrides that for every storage and mode: sweeps).
 template <typename S, int SRC>
 struct SmallPipe {
     static constexpr int BX = 64, BY = 8, WPR = 1, CTAS = 2, STAGES = 2, ORDER = 0;
@@ -359,7 +360,12 @@ cudaError_t encode_geom(trtr_ctx* ctx) {
     // the small-grid geometry when the large one leaves most SMs without a second tile
     using G = Pipe<S, SRC>;
     const long tiles = (long)((ctx->lp.nx + G::BX - 1) / G::BX) * ((ctx->lp.ny + G::BY - 1) / G::BY);
-    ctx->small_tiles = tiles < (long)TRTR_SMALL_TILES_PER_SM * ctx->num_sms;
+#ifdef TRTR_SMALL_TILES_PER_SM
+    constexpr long kBelow = TRTR_SMALL_TILES_PER_SM;
+#else
+    constexpr long kBelow = Geom<S, SRC>::SMALL_BELOW;
+#endif
+    ctx->small_tiles = tiles < kBelow * ctx->num_sms;
     return ctx->small_tiles ? encode_typed<S, SRC, SmallPipe<S, SRC>>(ctx) : encode_typed<S, SRC, G>(ctx);
 }
 

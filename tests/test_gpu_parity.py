@@ -105,7 +105,8 @@ def test_random_state_steps(nx, ny, prec, src_mode):
                                            ("f16", 0), ("f16", 2), ("bf16", 2)])
 def test_large_geometry_ragged_grid(prec, src_mode):
     """1101 x 700 nodes: enough tiles for the large-grid step geometry (128 x 16 tiles, or 128 x 8
-    for FP64 and the FP32 source fields; at least two per SM on a 152-SM GPU), with a ragged last
+    for FP64 and the FP32 source fields; at least two per SM on a 152-SM GPU; FP32 without a
+    source keeps the small-grid tiles up to about 4096^2, see the sampled 8192^2 check), with a ragged last
     tile column (77 nodes: the FP32 pulse path's bulk row copies leave its last column, the
     2-byte storages' its last five, to the lanes) and a ragged last tile row.  Two steps from
     random populations against the oracle; the 2-byte storages use phi_ref = 1."""
@@ -235,6 +236,12 @@ def _sampled_step_check(pulse, prec, warm_steps, nsamples, tol, seed=0):
 @pytest.mark.parametrize("pulse", [W.C2A_F32_1024, W.C2B_F32_4096], ids=lambda p: p.name)
 def test_fullsize_sampled_f32(pulse):
     _sampled_step_check(pulse, T.TRTR_F32, 100, 4000, 2e-6)
+
+
+def test_fullsize_sampled_f32_no_source_8192():
+    """FP32 without a source takes the large-grid tile geometry only on the largest grids
+    (the small tiles measured faster up to 4096^2): 8192^2, constant D, S = 0."""
+    _sampled_step_check(W.Pulse(n=8192, courant=0.8, tau2=0.8), T.TRTR_F32, 20, 2000, 2e-6)
 
 
 def test_fullsize_sampled_f64_8192():
