@@ -226,7 +226,7 @@ def _sampled_step_check(pulse, prec, warm_steps, nsamples, tol, seed=0):
         y = pulse.y0 + (node // n) * pulse.dx
         D = pulse.D0 * (1 + pulse.D_amp * math.sin(math.pi * x) * math.sin(math.pi * y))
         Sn = osim.pulse_source_at(x, y, t_n)
-        Sp = osim.pulse_source_at(x, y, t_n - pulse.dt) if step_n > 0 else Sn
+        Sp = osim.pulse_source_at(x, y, t_n - pulse.dt)  # the closed form at t_n - dt (first step too)
         ref[k] = oracle.node_post(op, g_n[k], -pulse.omega * y, pulse.omega * x, du, D, Sn, Sp)
     err = rel_l2(gpu, ref)
     assert err <= tol, err
