@@ -238,6 +238,14 @@ def test_fullsize_sampled_f32(pulse):
     _sampled_step_check(pulse, T.TRTR_F32, 100, 4000, 2e-6)
 
 
+@pytest.mark.parametrize("prec", ["f16", "bf16"])
+def test_fullsize_sampled_half_8192(prec):
+    """The 8192^2 half-precision storage workload in the bench's launch configuration: one step at
+    sampled nodes against the oracle's single-node update of the GPU's own (decoded) state; the
+    results are rounded to the storage format, so the one-step tolerance of that format."""
+    _sampled_step_check(W.C3_HALF_8192, PREC[prec], 20, 2000, ONE_STEP_TOL[prec])
+
+
 def test_fullsize_sampled_f32_no_source_8192():
     """FP32 without a source takes the large-grid tile geometry only on the largest grids
     (the small tiles measured faster up to 4096^2): 8192^2, constant D, S = 0."""
