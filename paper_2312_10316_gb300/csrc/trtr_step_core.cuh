@@ -320,7 +320,8 @@ __device__ __forceinline__ void issue_tile(unsigned char* stage, uint64_t* bar, 
 // copy of the row's first `bulk_cols(nx - i0)` columns (16-byte multiples: the row starts are
 // 16-byte aligned in both memories).  The lanes store the few columns past those, and the ghost
 // copies of edge nodes, directly.
-template <typename S, int SRC, int BX, int BY, int NM = BX / 64, bool TST = false>
+// UNR: the unroll factor of the pair loop (1: one pair at a time; NM: all pairs interleaved).
+template <typename S, int SRC, int BX, int BY, int NM = BX / 64, bool TST = false, int UNR = 1>
 __device__ __forceinline__ void tile_row_pairs(const unsigned char* st, int r, int lane, int i0, int j,
                                                const StepArgs<float>& a, const F2* sx, const F2* cx, float sy,
                                                float cy, int c0 = 0) {
@@ -339,7 +340,7 @@ __device__ __forceinline__ void tile_row_pairs(const unsigned char* st, int r, i
     S* dst = static_cast<S*>(a.dst);
     const size_t pl = a.lp.plane;
     const F2 magic(a.magic), w2f(a.omega2_fixed);
-#pragma unroll 1
+#pragma unroll (UNR)
     for (int m = 0; m < NM; ++m) {
         const int c = c0 + 64 * m + 2 * lane;  // column of the pair inside the tile
         const int i = i0 + c;
