@@ -56,7 +56,7 @@ constexpr Geometry kGeoms[] = {{128, 8}, {64, 8}, {128, 4}, {128, 16}, {64, 16}}
 constexpr int kNumGeoms = 5;
 constexpr int kNumSchedules = 3;  // 0 interleaved, 1 chunked, 2 chunked with the largest instances first
 constexpr int kNumConfigs = kNumGeoms * kNumSchedules;
-constexpr int kDefaultConfig = 1;  // 128 x 8 tiles, chunked
+constexpr int kDefaultConfig = 9;  // 128 x 16 tiles, interleaved: what the tuner picked on GB300
 
 // Pulse source uniforms of step n (t_n = n dt and t_{n-1}), in double, stored as float.
 __host__ __device__ inline TimeFields<float> time_fields(const Pulse& p, double dt, long long n) {
