@@ -197,8 +197,17 @@ trtr_status trtr_save(trtr_ctx* ctx, void* host_buf, size_t* bytes);
  * precision; fields and pulse are not part of it. */
 trtr_status trtr_load(trtr_ctx* ctx, const void* host_buf, size_t bytes);
 
-/* Waits for the context's stream and reports any pending CUDA error. */
+/* Waits for the context's stream and reports any pending CUDA error, or TRTR_ETIMEOUT if a
+ * step kernel gave up one of its bounded waits for its TMA loads (about 2 s of SM clock: the
+ * context's flag is then cleared, so the context stays usable). */
 trtr_status trtr_sync(trtr_ctx* ctx);
+
+/* Failure-detection check (the paper has no counterpart): launches one block whose bounded
+ * wait on a barrier that nothing ever completes gives up after `cycles` SM clock cycles
+ * (1 .. 2^31), through the same path as a step kernel's wait on its loads, and synchronises.
+ * Returns TRTR_ETIMEOUT when that path works; the flag is cleared as it is reported, so the
+ * next calls on the context run normally.  No copy is in flight, so nothing is left behind. */
+trtr_status trtr_check_timeout_path(trtr_ctx* ctx, long long cycles);
 
 /* Number of kernels the library enqueued on this context since creation (launch count). */
 trtr_status trtr_launch_count(const trtr_ctx* ctx, long* launches);

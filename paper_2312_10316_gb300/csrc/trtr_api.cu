@@ -97,12 +97,16 @@ trtr_status check_launch(trtr_ctx* ctx, cudaError_t e, const char* what) {
     return TRTR_OK;
 }
 
-// Synchronises the context's stream and reports a step kernel whose bounded wait gave up.
+// Synchronises the context's stream and reports a step kernel whose bounded wait gave up.  The
+// flag is cleared once reported, so the context stays usable.
 trtr_status sync_and_check(trtr_ctx* ctx, const char* where) {
     int* hflag = reinterpret_cast<int*>(ctx->hres + 3);
     TRTR_CUDA(ctx, cudaMemcpyAsync(hflag, ctx->dflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), where);
     TRTR_CUDA(ctx, cudaStreamSynchronize(ctx->stream), where);
-    if (*hflag != 0) return fail(ctx, TRTR_ETIMEOUT, "%s: a step kernel timed out waiting for its TMA loads", where);
+    if (*hflag != 0) {
+        TRTR_CUDA(ctx, cudaMemsetAsync(ctx->dflag, 0, sizeof(int), ctx->stream), where);
+        return fail(ctx, TRTR_ETIMEOUT, "%s: a kernel timed out waiting for its loads", where);
+    }
     return TRTR_OK;
 }
 
@@ -633,6 +637,14 @@ trtr_status trtr_sync(trtr_ctx* ctx) {
     if (s != TRTR_OK) return s;
     TRTR_CUDA(ctx, cudaGetLastError(), "sync");
     return TRTR_OK;
+}
+
+trtr_status trtr_check_timeout_path(trtr_ctx* ctx, long long cycles) {
+    if (!ctx) return TRTR_EINVAL;
+    if (cycles < 1 || cycles > (1LL << 31)) return fail(ctx, TRTR_EINVAL, "cycles must be in 1 .. 2^31");
+    trtr_status s = check_launch(ctx, trtr::launch_wait_timeout(ctx, cycles), "timeout check");
+    if (s != TRTR_OK) return s;
+    return sync_and_check(ctx, "timeout check");
 }
 
 trtr_status trtr_launch_count(const trtr_ctx* ctx, long* launches) {

@@ -585,7 +585,13 @@ trtr_status trtr_batch_sync(trtr_batch* b) {
         cudaGetLastError();
         return TRTR_ECUDA;
     }
-    return *b->h_flag ? TRTR_ETIMEOUT : TRTR_OK;
+    if (*b->h_flag == 0) return TRTR_OK;
+    // reported once: cleared for the following steps
+    if (cudaMemsetAsync(b->d_flag, 0, sizeof(int), b->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return TRTR_ECUDA;
+    }
+    return TRTR_ETIMEOUT;
 }
 
 trtr_status trtr_batch_tune(trtr_batch* b, int trial_steps, int* config_out, float* ms_out) {

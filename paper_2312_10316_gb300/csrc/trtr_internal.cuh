@@ -174,6 +174,8 @@ cudaError_t launch_step(trtr_ctx* ctx);
 // one step from an arbitrary population buffer (its map from encode_pop_map) into dst, as step `step`
 cudaError_t launch_step_from(trtr_ctx* ctx, const CUtensorMap* src_map, void* dst, long step);
 cudaError_t encode_pop_map(trtr_ctx* ctx, void* buffer, CUtensorMap* out);
+// one block whose bounded wait on a barrier that nothing completes gives up after `cycles`
+cudaError_t launch_wait_timeout(trtr_ctx* ctx, long long cycles);
 void free_adjoint(trtr_ctx* ctx);
 cudaError_t launch_convert_fields(trtr_ctx* ctx, const double* ux, const double* uy, const double* D);
 cudaError_t launch_pulse_fields(trtr_ctx* ctx);

@@ -240,6 +240,17 @@ __global__ void __launch_bounds__(G::THREADS, G::CTAS)
     if (kTST && lane == 0) bulk_wait_all();  // this warp's row copies have completed
 }
 
+// The failure path of the step kernels' bounded waits, on its own: a barrier that nothing ever
+// completes (no copy is issued), waited on for `cycles`, then the context's timeout flag.
+__global__ void wait_timeout_kernel(int* flag, long long cycles) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (!mbar_wait_bounded(&bar, 0, cycles)) atomicExch(flag, 1);
+    }
+}
+
 // Stages per CTA: G::STAGES, or fewer while they do not fit in the 227 KB a CTA may use.
 template <typename S, int SRC, class G>
 constexpr int stages_for() {
@@ -397,6 +408,12 @@ cudaError_t encode_maps(trtr_ctx* ctx) {
         case TRTR_BF16_OFS: return encode_src<__nv_bfloat16>(ctx);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_wait_timeout(trtr_ctx* ctx, long long cycles) {
+    ctx->launches += 1;
+    wait_timeout_kernel<<<1, 32, 0, ctx->stream>>>(ctx->dflag, cycles);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_step_from(trtr_ctx* ctx, const CUtensorMap* src_map, void* dst, long step) {

@@ -96,6 +96,7 @@ _SIGNATURES = {
     "trtr_last_error": (ctypes.c_char_p, [_vp]),
     "trtr_d2q9": (None, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _dbl_p]),
     "trtr_abi_version": (ctypes.c_int, []),
+    "trtr_check_timeout_path": (_st, [_vp, ctypes.c_longlong]),
 }
 
 
@@ -324,6 +325,11 @@ def trtr_d2q9():
     w = (ctypes.c_double * 9)()
     lib.trtr_d2q9(ex, ey, w)
     return np.array(ex[:]), np.array(ey[:]), np.array(w[:])
+
+
+def trtr_check_timeout_path(ctx, cycles: int) -> int:
+    """Status of the failure-detection check (TRTR_ETIMEOUT when the timeout path works)."""
+    return int(lib.trtr_check_timeout_path(ctx, int(cycles)))
 
 
 def trtr_abi_version() -> int:

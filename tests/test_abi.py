@@ -101,6 +101,7 @@ def test_null_arguments(T):
     assert lib.trtr_sync(None) == T.TRTR_EINVAL
     assert lib.trtr_set_dirichlet(None, None, 0) == T.TRTR_EINVAL
     assert lib.trtr_set_source_prev(None, None, 0) == T.TRTR_EINVAL
+    assert lib.trtr_check_timeout_path(None, 1000) == T.TRTR_EINVAL
 
 
 def test_batch_rejects_bad_instances_before_touching_cuda(T):

@@ -319,6 +319,30 @@ def test_field_source_save_load():
         assert np.array_equal(s.get_populations(), ref)
 
 
+def test_bounded_wait_gives_up_and_the_context_stays_usable():
+    """Failure detection without a fault: a kernel waits on a barrier that nothing completes,
+    gives up after about half a millisecond through the step kernels' bounded-wait path, and
+    the host reads TRTR_ETIMEOUT; the flag is cleared as it is reported, and the context then
+    steps exactly as a fresh one does."""
+    nx, ny = 40, 24
+    case = random_case(3, nx, ny)
+    p = T.Params(nx=nx, ny=ny, dx=case["dx"], dt=case["dt"], precision=T.TRTR_F64)
+    results = []
+    for check in (True, False):
+        with T.Solver(p) as s:
+            s.set_fields(case["ux"], case["uy"], case["D"])
+            s.set_populations(case["g"])
+            if check:
+                assert T.trtr_check_timeout_path(s.ctx, 1_000_000) == T.TRTR_ETIMEOUT
+                assert "timed out" in T.trtr_last_error(s.ctx)
+                assert T.trtr_check_timeout_path(s.ctx, 0) == T.TRTR_EINVAL
+                s.sync()  # reported once: nothing pending any more
+            s.step(3)
+            s.sync()
+            results.append(s.get_populations())
+    assert np.array_equal(results[0], results[1])
+
+
 def test_unstable_run_is_reported():
     """Host-side fault injection: a NaN population is detected by the periodic check."""
     nx, ny = 32, 32
