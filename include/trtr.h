@@ -53,7 +53,8 @@ typedef enum {
     TRTR_ECUDA = 3,
     TRTR_EUNSTABLE = 4,
     TRTR_ETIMEOUT = 5,
-    TRTR_ESTATE = 6
+    TRTR_ESTATE = 6,
+    TRTR_EBOUNDS = 7 /* bounds-checked builds only: a kernel access out of bounds was caught */
 } trtr_status;
 
 /* Storage / arithmetic of the populations.  F64: stored and computed in double.  F32:
@@ -273,7 +274,8 @@ trtr_status trtr_batch_set_config(trtr_batch* b, int config);
  * must not be stepped through their own contexts in between (TRTR_ESTATE). */
 trtr_status trtr_batch_step(trtr_batch* b, long n);
 
-/* Waits for the batch's stream; TRTR_ETIMEOUT if a step kernel gave up a bounded wait. */
+/* Waits for the batch's stream; TRTR_ETIMEOUT if a step kernel gave up a bounded wait
+ * (TRTR_EBOUNDS in the bounds-checked build if a kernel access out of bounds was caught). */
 trtr_status trtr_batch_sync(trtr_batch* b);
 
 /* The context of instance k (owned by the batch): moments, mass, error, populations. */
@@ -326,6 +328,34 @@ void trtr_d2q9(int* ex, int* ey, double* w);
 
 /* ABI version (incremented on incompatible change). */
 int trtr_abi_version(void);
+
+/* ---- Bounds-checked debug build ---------------------------------------------------------
+ * The library built with TRTR_BOUNDS_CHECK=1 (libtrtr_checked.so) checks its kernels' memory
+ * accesses against the ghosted plane layout: every plane index, the two-node stores, the bulk
+ * row copies (inside the interior row, 16-byte aligned addresses and size) and the TMA load
+ * coordinates (x times the element size a multiple of 16 bytes, 128-byte aligned destination).
+ * A bad access is recorded and skipped (or kept inside the ghost frame); nothing traps.  The
+ * next call that synchronises a context's stream (or trtr_batch_sync) then returns
+ * TRTR_EBOUNDS with the first access in trtr_last_error.  The default build compiles none of
+ * these checks. */
+
+/* 1 in the bounds-checked build, 0 in the default build. */
+int trtr_bounds_checked(void);
+
+/* Synchronises the current device, then returns the record of every kernel since the last
+ * report and clears it: out[0] = accesses caught, out[1] = kind of the first (1 plane index,
+ * 2 two-node store, 3 bulk row copy, 4 TMA load), out[2] = its column i | row j << 32 (for a
+ * TMA load, x | y << 32).  The default build writes zeros.  TRTR_EINVAL: out is NULL;
+ * TRTR_ECUDA: a CUDA call failed. */
+trtr_status trtr_bounds_report(unsigned long long out[3]);
+
+/* Checks the recording path of the bounds-checked build without a bad access: one thread gives
+ * the checks four bad arguments (a plane index one column past the ghost frame, a TMA x
+ * coordinate of 12 bytes, a TMA destination off its 128-byte boundary, a bulk row copy past
+ * the row end) and accesses nothing with them.  Returns TRTR_EBOUNDS in the checked build
+ * (trtr_last_error: 4 accesses, the first of kind 1 at (nx + 1, 0)), TRTR_OK in the default
+ * build; the record is cleared either way.  Needs a created context (any state). */
+trtr_status trtr_check_bounds_path(trtr_ctx* ctx);
 
 #ifdef __cplusplus
 }

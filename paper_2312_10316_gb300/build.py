@@ -17,6 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtrtr.so")
+# debug build whose kernels check their memory accesses (TRTR_BOUNDS_CHECK=1)
+LIB_CHECKED = os.path.join(HERE, "libtrtr_checked.so")
 
 SOURCES = ["trtr_api.cu", "trtr_step.cu", "trtr_aux.cu", "trtr_noalloc.cu", "trtr_batch.cu", "trtr_adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -38,25 +40,28 @@ def _deps() -> list[str]:
     return files
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _deps())
 
 
 def build_library(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None,
-                  out: str | None = None) -> str:
-    """Compile and link libtrtr.so (or `out`); returns its path.  Raises on any compiler error."""
-    if not force and out is None and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+                  out: str | None = None, checked: bool = False) -> str:
+    """Compile and link libtrtr.so (or `out`); returns its path.  Raises on any compiler error.
+    checked=True builds the bounds-checked debug library libtrtr_checked.so instead."""
+    default = LIB_CHECKED if checked else LIB
+    if not force and out is None and up_to_date(default):
+        return default
+    objdir = os.path.join(BUILD, "checked") if checked else BUILD
+    os.makedirs(objdir, exist_ok=True)
     cc = nvcc()
-    flags = NVCC_FLAGS + (extra_flags or [])
+    flags = NVCC_FLAGS + (["-DTRTR_BOUNDS_CHECK=1"] if checked else []) + (extra_flags or [])
     procs = []
     objs = []
     for s in SOURCES:
-        obj = os.path.join(BUILD, s.replace(".cu", ".o"))
+        obj = os.path.join(objdir, s.replace(".cu", ".o"))
         objs.append(obj)
         cmd = [cc, *flags, "-c", os.path.join(CSRC, s), "-o", obj]
         if verbose:
@@ -71,7 +76,7 @@ def build_library(force: bool = False, verbose: bool = False, extra_flags: list[
             errors.append(f"{s}:\n{log.decode(errors='replace')}")
     if errors:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
-    target = out or LIB
+    target = out or default
     tmp = target + ".tmp"
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
@@ -84,4 +89,4 @@ def build_library(force: bool = False, verbose: bool = False, extra_flags: list[
 if __name__ == "__main__":
     v = "-v" in sys.argv
     extra = ["-Xptxas", "-v"] if "--ptxas" in sys.argv else None
-    print(build_library(force=True, verbose=v or bool(extra), extra_flags=extra))
+    print(build_library(force=True, verbose=v or bool(extra), extra_flags=extra, checked="--checked" in sys.argv))

@@ -190,6 +190,8 @@ void free_adjoint(trtr_ctx* ctx) {
     ctx->adj = nullptr;
 }
 
+TRTR_BOUNDS_TAKE(adjoint)
+
 }  // namespace trtr
 
 namespace {

@@ -11,6 +11,25 @@
 
 #include "trtr_internal.cuh"
 
+namespace trtr {
+cudaError_t bounds_take_all(cudaStream_t s, unsigned long long* out) {
+    out[0] = out[1] = out[2] = 0ull;
+    cudaError_t (*units[])(cudaStream_t, unsigned long long*) = {bounds_take_step, bounds_take_aux, bounds_take_batch,
+                                                                  bounds_take_adjoint};
+    for (auto take : units) {
+        unsigned long long u[3];
+        const cudaError_t e = take(s, u);
+        if (e != cudaSuccess) return e;
+        if (u[0] != 0ull && out[0] == 0ull) {
+            out[1] = u[1];
+            out[2] = u[2];
+        }
+        out[0] += u[0];
+    }
+    return cudaSuccess;
+}
+}  // namespace trtr
+
 namespace {
 
 constexpr int kAbiVersion = 2;
@@ -107,6 +126,13 @@ trtr_status sync_and_check(trtr_ctx* ctx, const char* where) {
         TRTR_CUDA(ctx, cudaMemsetAsync(ctx->dflag, 0, sizeof(int), ctx->stream), where);
         return fail(ctx, TRTR_ETIMEOUT, "%s: a kernel timed out waiting for its loads", where);
     }
+#if TRTR_BOUNDS_CHECK
+    unsigned long long log[3];
+    TRTR_CUDA(ctx, trtr::bounds_take_all(ctx->stream, log), where);
+    if (log[0] != 0ull)
+        return fail(ctx, TRTR_EBOUNDS, "%s: %llu out-of-bounds accesses; the first of kind %llu at (%d, %d)", where,
+                    log[0], log[1], (int)(unsigned)(log[2] & 0xffffffffull), (int)(unsigned)(log[2] >> 32));
+#endif
     return TRTR_OK;
 }
 
@@ -136,6 +162,14 @@ extern "C" {
 
 int trtr_abi_version(void) { return kAbiVersion; }
 
+int trtr_bounds_checked(void) { return TRTR_BOUNDS_CHECK; }
+
+trtr_status trtr_bounds_report(unsigned long long out[3]) {
+    if (!out) return TRTR_EINVAL;
+    if (cudaDeviceSynchronize() != cudaSuccess) return TRTR_ECUDA;
+    return trtr::bounds_take_all(0, out) == cudaSuccess ? TRTR_OK : TRTR_ECUDA;
+}
+
 const char* trtr_status_str(trtr_status s) {
     switch (s) {
         case TRTR_OK: return "ok";
@@ -145,6 +179,7 @@ const char* trtr_status_str(trtr_status s) {
         case TRTR_EUNSTABLE: return "non-finite populations (unstable run)";
         case TRTR_ETIMEOUT: return "timed out";
         case TRTR_ESTATE: return "call out of order";
+        case TRTR_EBOUNDS: return "out-of-bounds access caught (bounds-checked build)";
         default: return "unknown status";
     }
 }
@@ -645,6 +680,13 @@ trtr_status trtr_check_timeout_path(trtr_ctx* ctx, long long cycles) {
     trtr_status s = check_launch(ctx, trtr::launch_wait_timeout(ctx, cycles), "timeout check");
     if (s != TRTR_OK) return s;
     return sync_and_check(ctx, "timeout check");
+}
+
+trtr_status trtr_check_bounds_path(trtr_ctx* ctx) {
+    if (!ctx) return TRTR_EINVAL;
+    trtr_status s = check_launch(ctx, trtr::launch_bounds_probe(ctx), "bounds check");
+    if (s != TRTR_OK) return s;
+    return sync_and_check(ctx, "bounds check");
 }
 
 trtr_status trtr_launch_count(const trtr_ctx* ctx, long* launches) {

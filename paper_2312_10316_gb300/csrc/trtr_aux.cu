@@ -468,4 +468,6 @@ cudaError_t launch_dirichlet(trtr_ctx* ctx, void* P) {
     });
 }
 
+TRTR_BOUNDS_TAKE(aux)
+
 }  // namespace trtr

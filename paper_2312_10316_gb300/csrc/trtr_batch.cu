@@ -122,12 +122,16 @@ __global__ void __launch_bounds__(32 * BY, min_blocks<BY>())
         unsigned char* stage = smem + s * T::STAGE;
         uint64_t* bar = &full[s];
         mbar_expect_tx(bar, T::TX);
+        constexpr int kPe = (int)sizeof(S), kFe = (int)sizeof(C);
 #pragma unroll
-        for (int q = 0; q < kQ; ++q)
-            tma_load_3d(stage + q * T::POP_PLANE, &d->mp[parity], bar, t.y + gxp - (lattice_ex(q) == 1 ? T::A : 0),
-                        t.z + 1 - lattice_ey(q), q);
-        tma_load_3d(stage + T::POP, &d->mu, bar, t.y + gxf - T::AC, t.z, 0);
-        tma_load_2d(stage + T::POP + T::U, &d->md, bar, t.y + gxf, t.z + 1);
+        for (int q = 0; q < kQ; ++q) {
+            const int x = t.y + gxp - (lattice_ex(q) == 1 ? T::A : 0), y = t.z + 1 - lattice_ey(q);
+            if (tma_ok(stage + q * T::POP_PLANE, x, y, kPe)) tma_load_3d(stage + q * T::POP_PLANE, &d->mp[parity], bar, x, y, q);
+        }
+        if (tma_ok(stage + T::POP, t.y + gxf - T::AC, t.z, kFe))
+            tma_load_3d(stage + T::POP, &d->mu, bar, t.y + gxf - T::AC, t.z, 0);
+        if (tma_ok(stage + T::POP + T::U, t.y + gxf, t.z + 1, kFe))
+            tma_load_2d(stage + T::POP + T::U, &d->md, bar, t.y + gxf, t.z + 1);
         constexpr int kStatic = (int)(sizeof(StepArgs<C>) - sizeof(TimeFields<C>));
         cp_async_16(&sargs[s], &d->base[parity], kStatic);
         if (SRC == TRTR_SRC_PULSE) cp_async_16(&sargs[s].tf, &tu[t.x], (int)sizeof(TimeFields<C>));
@@ -472,6 +476,8 @@ trtr_status advance(trtr_batch* b, long n) {
 }
 
 }  // namespace
+TRTR_BOUNDS_TAKE(batch)
+
 }  // namespace trtr
 
 extern "C" {
@@ -585,6 +591,16 @@ trtr_status trtr_batch_sync(trtr_batch* b) {
         cudaGetLastError();
         return TRTR_ECUDA;
     }
+#if TRTR_BOUNDS_CHECK
+    if (*b->h_flag == 0) {
+        unsigned long long log[3];
+        if (trtr::bounds_take_all(b->stream, log) != cudaSuccess) {
+            cudaGetLastError();
+            return TRTR_ECUDA;
+        }
+        return log[0] != 0ull ? TRTR_EBOUNDS : TRTR_OK;
+    }
+#endif
     if (*b->h_flag == 0) return TRTR_OK;
     // reported once: cleared for the following steps
     if (cudaMemsetAsync(b->d_flag, 0, sizeof(int), b->stream) != cudaSuccess) {

@@ -48,6 +48,67 @@ struct PulseTime {
     double amp;       // s0^2 / s^2(t)
 };
 
+// ---- bounds-checked builds (TRTR_BOUNDS_CHECK=1) ----------------------------------------
+// The debug build checks the kernels' memory accesses against the layout: every plane index
+// (PlaneLayout::at), the pair stores, the bulk row copies and the TMA load coordinates.  An
+// access out of bounds is recorded in this translation unit's log and then skipped, or kept
+// inside the ghost frame; it never traps, so the context stays usable and the host reports
+// TRTR_EBOUNDS at the next synchronisation.  The default build compiles none of it.
+#ifndef TRTR_BOUNDS_CHECK
+#define TRTR_BOUNDS_CHECK 0
+#endif
+
+enum BoundsKind {
+    kBoundsPlane = 1,  // a plane index outside the interior and its ghost frame
+    kBoundsPair = 2,   // a two-node store past the row or not aligned to the pair
+    kBoundsBulk = 3,   // a bulk row copy outside the interior row, or not 16-byte aligned
+    kBoundsTma = 4,    // a TMA load whose x coordinate or destination breaks the alignment rules
+    kBoundsTile = 5,   // a tile column or row outside the tile
+};
+
+#if TRTR_BOUNDS_CHECK
+// [0] number of accesses caught, [1] kind of the first, [2] its (j << 32 | i); one log per
+// translation unit (read and cleared by bounds_take_<unit>()).
+static __device__ unsigned long long bounds_log[3];
+__device__ __forceinline__ void bounds_fault(int kind, int i, int j) {
+    if (atomicAdd(&bounds_log[0], 1ull) == 0ull) {
+        bounds_log[1] = (unsigned long long)kind;
+        bounds_log[2] = ((unsigned long long)(unsigned)j << 32) | (unsigned)i;
+    }
+}
+#define TRTR_BOUNDS_FAULT(kind, i, j) ::trtr::bounds_fault((kind), (i), (j))
+#else
+#define TRTR_BOUNDS_FAULT(kind, i, j) ((void)0)
+#endif
+
+// Host side of a translation unit's log: copies {count, kind, where} to `out` and clears it
+// (zeros in the default build).
+#if TRTR_BOUNDS_CHECK
+#define TRTR_BOUNDS_TAKE(unit)                                                                       \
+    cudaError_t bounds_take_##unit(cudaStream_t s, unsigned long long* out) {                        \
+        static const unsigned long long zero[3] = {0ull, 0ull, 0ull};                                \
+        cudaError_t e = cudaMemcpyFromSymbolAsync(out, bounds_log, sizeof(zero), 0,                  \
+                                                  cudaMemcpyDeviceToHost, s);                        \
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);                                          \
+        if (e == cudaSuccess && out[0] != 0ull)                                                      \
+            e = cudaMemcpyToSymbolAsync(bounds_log, zero, sizeof(zero), 0, cudaMemcpyHostToDevice, s); \
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);                                          \
+        return e;                                                                                    \
+    }
+#else
+#define TRTR_BOUNDS_TAKE(unit)                                                \
+    cudaError_t bounds_take_##unit(cudaStream_t, unsigned long long* out) {   \
+        out[0] = out[1] = out[2] = 0ull;                                      \
+        return cudaSuccess;                                                   \
+    }
+#endif
+cudaError_t bounds_take_step(cudaStream_t s, unsigned long long* out);
+cudaError_t bounds_take_aux(cudaStream_t s, unsigned long long* out);
+cudaError_t bounds_take_batch(cudaStream_t s, unsigned long long* out);
+cudaError_t bounds_take_adjoint(cudaStream_t s, unsigned long long* out);
+// All units: the summed count, and the kind and place of the first unit's first access.
+cudaError_t bounds_take_all(cudaStream_t s, unsigned long long* out);
+
 struct PlaneLayout {
     int nx, ny;
     int gx;        // column of interior x = 0 (128 bytes of columns)
@@ -55,6 +116,13 @@ struct PlaneLayout {
     int rows;      // rows per plane (>= ny + 2)
     size_t plane;  // rows * pitch
     __host__ __device__ __forceinline__ size_t at(int i, int j) const {
+#if TRTR_BOUNDS_CHECK && defined(__CUDA_ARCH__)
+        if (i < -1 || i > nx || j < -1 || j > ny) {  // outside the interior and its ghost frame
+            TRTR_BOUNDS_FAULT(kBoundsPlane, i, j);
+            i = i < -1 ? -1 : (i > nx ? nx : i);
+            j = j < -1 ? -1 : (j > ny ? ny : j);
+        }
+#endif
         return (size_t)(j + 1) * (size_t)pitch + (size_t)(i + gx);
     }
 };
@@ -176,6 +244,8 @@ cudaError_t launch_step_from(trtr_ctx* ctx, const CUtensorMap* src_map, void* ds
 cudaError_t encode_pop_map(trtr_ctx* ctx, void* buffer, CUtensorMap* out);
 // one block whose bounded wait on a barrier that nothing completes gives up after `cycles`
 cudaError_t launch_wait_timeout(trtr_ctx* ctx, long long cycles);
+// one thread that gives the bounds checks four bad arguments and accesses nothing with them
+cudaError_t launch_bounds_probe(trtr_ctx* ctx);
 void free_adjoint(trtr_ctx* ctx);
 cudaError_t launch_convert_fields(trtr_ctx* ctx, const double* ux, const double* uy, const double* D);
 cudaError_t launch_pulse_fields(trtr_ctx* ctx);

@@ -251,6 +251,22 @@ __global__ void wait_timeout_kernel(int* flag, long long cycles) {
     }
 }
 
+// The recording path of the bounds-checked build, on its own: one thread puts four bad
+// arguments to the checks -- a plane index one column past the ghost frame, a TMA x coordinate
+// of 12 bytes, a TMA destination 16 bytes off a 128-byte boundary, and a bulk row copy past the
+// row end -- and performs no access with any of them (the clamped plane index is compared, not
+// used).  The checked build records the four; the default build records nothing.
+__global__ void bounds_probe_kernel(PlaneLayout L) {
+    __shared__ __align__(128) unsigned char buf[256];
+    if (threadIdx.x != 0) return;
+    const size_t k = L.at(L.nx + 1, 0);
+    const bool clamped = k == L.at(L.nx, 0);
+    const bool t1 = tma_ok(buf, 3, 0, 4);
+    const bool t2 = tma_ok(buf + 16, 0, 0, 4);
+    const bool b1 = bulk_ok(static_cast<const float*>(nullptr), buf, L.nx - 4, 0, 8, L);
+    if (clamped && t1 && t2 && b1) buf[0] = 0;  // keeps the checks (no global access)
+}
+
 // Stages per CTA: G::STAGES, or fewer while they do not fit in the 227 KB a CTA may use.
 template <typename S, int SRC, class G>
 constexpr int stages_for() {
@@ -416,6 +432,12 @@ cudaError_t launch_wait_timeout(trtr_ctx* ctx, long long cycles) {
     return cudaGetLastError();
 }
 
+cudaError_t launch_bounds_probe(trtr_ctx* ctx) {
+    ctx->launches += 1;
+    bounds_probe_kernel<<<1, 32, 0, ctx->stream>>>(ctx->lp);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_step_from(trtr_ctx* ctx, const CUtensorMap* src_map, void* dst, long step) {
     switch (ctx->p.precision) {
         case TRTR_F64: return launch_src<double>(ctx, *src_map, dst, step);
@@ -439,5 +461,7 @@ cudaError_t encode_pop_map(trtr_ctx* ctx, void* buffer, CUtensorMap* out) {
         default: return cudaErrorInvalidValue;
     }
 }
+
+TRTR_BOUNDS_TAKE(step)
 
 }  // namespace trtr

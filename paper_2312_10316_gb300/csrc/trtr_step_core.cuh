@@ -108,6 +108,34 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// Checked builds (TRTR_BOUNDS_CHECK): a tiled TMA load's x coordinate times the element size is
+// a multiple of 16 bytes and its shared-memory destination is 128-byte aligned; a load that
+// breaks either is recorded and not issued (its barrier then times out, which is reported).
+__device__ __forceinline__ bool tma_ok(const void* dst, int x, int y, int elem) {
+#if TRTR_BOUNDS_CHECK
+    if ((x * elem) % 16 != 0 || (smem_addr(dst) & 127u) != 0u) {
+        TRTR_BOUNDS_FAULT(kBoundsTma, x, y);
+        return false;
+    }
+#endif
+    return true;
+}
+
+// Checked builds: a bulk copy of nb interior columns of row j from column i0 stays inside the
+// interior row and has 16-byte aligned addresses and size; otherwise it is recorded and skipped.
+template <typename S>
+__device__ __forceinline__ bool bulk_ok(const S* gdst, const void* src, int i0, int j, int nb, const PlaneLayout& L) {
+#if TRTR_BOUNDS_CHECK
+    const unsigned bytes = (unsigned)nb * (unsigned)sizeof(S);
+    if (i0 < 0 || i0 + nb > L.nx || j < 0 || j >= L.ny || (reinterpret_cast<uintptr_t>(gdst) & 15u) != 0u ||
+        (smem_addr(src) & 15u) != 0u || (bytes & 15u) != 0u) {
+        TRTR_BOUNDS_FAULT(kBoundsBulk, i0, j);
+        return false;
+    }
+#endif
+    return true;
+}
+
 // ---- arithmetic types --------------------------------------------------------------------
 // FP32-computing storages work on pairs of adjacent nodes with the packed FP32 instructions
 // of sm_100-family SMs (two lanes of FP32 per FADD2 / FMUL2 / FFMA2); FP64 works per node.
@@ -296,17 +324,21 @@ __device__ __forceinline__ void issue_tile(unsigned char* stage, uint64_t* bar, 
     using T = Tile<S, SRC, BX, BY>;
     mbar_expect_tx(bar, T::TX);
 #pragma unroll
+    constexpr int kPe = (int)sizeof(S), kFe = (int)sizeof(typename Store<S>::C);
     for (int q = 0; q < kQ; ++q) {
         const int x = i0 + a.lp.gx - (lattice_ex(q) == 1 ? T::A : 0);
         const int y = j0 + 1 - lattice_ey(q);
-        tma_load_3d(stage + q * T::POP_PLANE, mp, bar, x, y, q);
+        if (tma_ok(stage + q * T::POP_PLANE, x, y, kPe)) tma_load_3d(stage + q * T::POP_PLANE, mp, bar, x, y, q);
     }
-    tma_load_3d(stage + T::POP, mu, bar, i0 + a.lf.gx - T::AC, j0, 0);
-    tma_load_2d(stage + T::POP + T::U, md, bar, i0 + a.lf.gx, j0 + 1);
+    if (tma_ok(stage + T::POP, i0 + a.lf.gx - T::AC, j0, kFe))
+        tma_load_3d(stage + T::POP, mu, bar, i0 + a.lf.gx - T::AC, j0, 0);
+    if (tma_ok(stage + T::POP + T::U, i0 + a.lf.gx, j0 + 1, kFe))
+        tma_load_2d(stage + T::POP + T::U, md, bar, i0 + a.lf.gx, j0 + 1);
     if (SRC == TRTR_SRC_FIELD) {
         unsigned char* s = stage + T::POP + T::U + T::D;
-        tma_load_3d(s, ms, bar, i0 + a.lf.gx, j0 + 1, a.s_cur);
-        tma_load_3d(s + T::S_TILE, ms, bar, i0 + a.lf.gx, j0 + 1, a.s_prev);
+        if (tma_ok(s, i0 + a.lf.gx, j0 + 1, kFe)) tma_load_3d(s, ms, bar, i0 + a.lf.gx, j0 + 1, a.s_cur);
+        if (tma_ok(s + T::S_TILE, i0 + a.lf.gx, j0 + 1, kFe))
+            tma_load_3d(s + T::S_TILE, ms, bar, i0 + a.lf.gx, j0 + 1, a.s_prev);
     }
 }
 
@@ -419,6 +451,12 @@ __device__ __forceinline__ void tile_row_pairs(const unsigned char* st, int r, i
             }
         } else if (!edge) {
             S* d0 = dst + a.lp.at(i, j);
+#if TRTR_BOUNDS_CHECK
+            if (i + 1 >= nx || (reinterpret_cast<uintptr_t>(d0) % sizeof(S2)) != 0u) {
+                TRTR_BOUNDS_FAULT(kBoundsPair, i, j);
+                continue;
+            }
+#endif
 #pragma unroll
             for (int q = 0; q < kQ; ++q)
                 *reinterpret_cast<S2*>(d0 + q * pl) = P::encode_raw(out[q]);
@@ -438,7 +476,8 @@ __device__ __forceinline__ void tile_row_pairs(const unsigned char* st, int r, i
         if (lane == 0 && nb > 0) {
 #pragma unroll
             for (int q = 0; q < kQ; ++q)
-                bulk_store(dst + q * pl + a.lp.at(i0, j), sp + q * T::PLANE_ELEMS, (uint32_t)(nb * sizeof(S)));
+                if (bulk_ok(dst + q * pl + a.lp.at(i0, j), sp + q * T::PLANE_ELEMS, i0, j, nb, a.lp))
+                    bulk_store(dst + q * pl + a.lp.at(i0, j), sp + q * T::PLANE_ELEMS, (uint32_t)(nb * sizeof(S)));
             bulk_commit();
             bulk_wait_read();  // the stage may be refilled after the CTA barrier
         }
@@ -520,7 +559,9 @@ __device__ __forceinline__ void tile_row_f64(const unsigned char* st, int r, int
         if (lane == 0 && nb > 0) {
 #pragma unroll
             for (int q = 0; q < kQ; ++q)
-                bulk_store(dst + q * pl + a.lp.at(i0, j), sp + q * T::PLANE_ELEMS, (uint32_t)(nb * sizeof(double)));
+                if (bulk_ok(dst + q * pl + a.lp.at(i0, j), sp + q * T::PLANE_ELEMS, i0, j, nb, a.lp))
+                    bulk_store(dst + q * pl + a.lp.at(i0, j), sp + q * T::PLANE_ELEMS,
+                               (uint32_t)(nb * sizeof(double)));
             bulk_commit();
             bulk_wait_read();
         }

@@ -15,9 +15,11 @@ from dataclasses import dataclass, fields as dc_fields
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libtrtr.so")
+# TRTR_BOUNDS_CHECK=1 in the environment loads the bounds-checked debug build instead
+BOUNDS_CHECKED = os.environ.get("TRTR_BOUNDS_CHECK", "0") == "1"
+LIB_PATH = os.path.join(_HERE, "libtrtr_checked.so" if BOUNDS_CHECKED else "libtrtr.so")
 
-TRTR_OK, TRTR_EINVAL, TRTR_ENOMEM, TRTR_ECUDA, TRTR_EUNSTABLE, TRTR_ETIMEOUT, TRTR_ESTATE = range(7)
+TRTR_OK, TRTR_EINVAL, TRTR_ENOMEM, TRTR_ECUDA, TRTR_EUNSTABLE, TRTR_ETIMEOUT, TRTR_ESTATE, TRTR_EBOUNDS = range(8)
 TRTR_F64, TRTR_F32, TRTR_F16_OFS, TRTR_BF16_OFS = range(4)
 TRTR_TAU2_MAGIC, TRTR_TAU2_FIXED = range(2)
 TRTR_GRAD_PERIODIC, TRTR_GRAD_ONESIDED_EDGE = range(2)
@@ -97,12 +99,16 @@ _SIGNATURES = {
     "trtr_d2q9": (None, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _dbl_p]),
     "trtr_abi_version": (ctypes.c_int, []),
     "trtr_check_timeout_path": (_st, [_vp, ctypes.c_longlong]),
+    "trtr_bounds_checked": (ctypes.c_int, []),
+    "trtr_bounds_report": (_st, [ctypes.POINTER(ctypes.c_ulonglong)]),
+    "trtr_check_bounds_path": (_st, [_vp]),
 }
 
 
 def _load() -> ctypes.CDLL:
     if not os.path.exists(LIB_PATH):
-        raise ImportError(f"{LIB_PATH} is missing: build it with paper_2312_10316_gb300.build.build_library()")
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_2312_10316_gb300.build.build_library"
+                          f"({'checked=True' if BOUNDS_CHECKED else ''})")
     lib = ctypes.CDLL(LIB_PATH)
     for name, (res, args) in _SIGNATURES.items():
         f = getattr(lib, name)
@@ -334,6 +340,26 @@ def trtr_check_timeout_path(ctx, cycles: int) -> int:
 
 def trtr_abi_version() -> int:
     return int(lib.trtr_abi_version())
+
+
+def trtr_check_bounds_path(ctx) -> int:
+    """Status of the bounds-check probe (TRTR_EBOUNDS in the checked build, TRTR_OK otherwise)."""
+    return int(lib.trtr_check_bounds_path(ctx))
+
+
+def trtr_bounds_checked() -> bool:
+    return bool(lib.trtr_bounds_checked())
+
+
+def trtr_bounds_report() -> tuple[int, int, int, int]:
+    """(accesses caught, kind of the first, its column or x, its row or y) since the last report;
+    the record is cleared.  Zeros in the default build."""
+    out = (ctypes.c_ulonglong * 3)()
+    _check(None, lib.trtr_bounds_report(out))
+    where = int(out[2])
+    i, j = where & 0xFFFFFFFF, where >> 32
+    signed = lambda v: v - (1 << 32) if v >= 1 << 31 else v  # noqa: E731
+    return int(out[0]), int(out[1]), signed(i), signed(j)
 
 
 # --------------------------------------------------------------------------------------

@@ -64,7 +64,23 @@ def test_host_only_calls(T):
     for a in (1, 3, 5, 7):
         assert ex[a] == -ex[a + 1] and ey[a] == -ey[a + 1]
     assert T.trtr_status_str(T.TRTR_EUNSTABLE).startswith("non-finite")
+    assert "bounds" in T.trtr_status_str(T.TRTR_EBOUNDS)
     assert T.trtr_last_error(None) == "null context"
+    assert T.trtr_bounds_checked() == T.BOUNDS_CHECKED
+
+
+def test_bounds_checked_build_exports_the_same_boundary(T):
+    """The debug build (TRTR_BOUNDS_CHECK=1) is a second library with the same entry points."""
+    from paper_2312_10316_gb300.build import build_library
+
+    path = build_library(checked=True)
+    lib = ctypes.CDLL(path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    lib.trtr_bounds_checked.restype = ctypes.c_int
+    assert lib.trtr_bounds_checked() == 1
+    assert lib.trtr_bounds_report(None) == T.TRTR_EINVAL
+    assert lib.trtr_check_bounds_path(None) == T.TRTR_EINVAL
 
 
 def test_library_and_oracle_share_the_lattice_convention(T):
@@ -102,6 +118,7 @@ def test_null_arguments(T):
     assert lib.trtr_set_dirichlet(None, None, 0) == T.TRTR_EINVAL
     assert lib.trtr_set_source_prev(None, None, 0) == T.TRTR_EINVAL
     assert lib.trtr_check_timeout_path(None, 1000) == T.TRTR_EINVAL
+    assert lib.trtr_bounds_report(None) == T.TRTR_EINVAL
 
 
 def test_batch_rejects_bad_instances_before_touching_cuda(T):
