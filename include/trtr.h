@@ -155,9 +155,17 @@ trtr_status trtr_init_equilibrium(trtr_ctx* ctx, const double* phi0, int on_devi
 
 /* Advances n >= 0 time steps of Eq. (14): one fused pull-stream + collide kernel per step on
  * the context's stream (plus the boundary pass with TRTR_BC_DIRICHLET_NEE), ping-pong buffers,
- * no host synchronisation (unless check_every).  The step kernels use programmatic dependent
+ * no host synchronisation (unless check_every).  With FP32 storage, periodic boundaries and
+ * src_mode NONE or PULSE, pairs of steps run as one launch of the two-step kernel (the same
+ * arithmetic, the same results bit for bit; populations read and written once per two steps;
+ * see trtr_set_steps_per_launch); an odd last step, or a pair whose middle step is a
+ * check_every point, runs one step per launch.  The step kernels use programmatic dependent
  * launch: each waits for the work before it on the stream before reading its results. */
 trtr_status trtr_step(trtr_ctx* ctx, long n);
+
+/* k = 2 (the default): trtr_step uses the two-step kernel where it applies; k = 1: one step per
+ * launch always.  TRTR_EINVAL for other k. */
+trtr_status trtr_set_steps_per_launch(trtr_ctx* ctx, int k);
 
 /* phi(x, t_n) = sum_i g_i(x, t_n) of the pre-collision populations (B_0^neq = 0, Sec. 2.2),
  * written as doubles [ny][nx].  Synchronises. */
@@ -353,7 +361,8 @@ trtr_status trtr_bounds_report(unsigned long long out[3]);
  * the checks four bad arguments (a plane index one column past the ghost frame, a TMA x
  * coordinate of 12 bytes, a TMA destination off its 128-byte boundary, a bulk row copy past
  * the row end) and accesses nothing with them.  Returns TRTR_EBOUNDS in the checked build
- * (trtr_last_error: 4 accesses, the first of kind 1 at (nx + 1, 0)), TRTR_OK in the default
+ * (trtr_last_error: 4 accesses, the first of kind 1 at (nx + 2, 0), the population planes
+ * having two ghost columns), TRTR_OK in the default
  * build; the record is cleared either way.  Needs a created context (any state). */
 trtr_status trtr_check_bounds_path(trtr_ctx* ctx);
 

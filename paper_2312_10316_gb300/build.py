@@ -20,7 +20,8 @@ LIB = os.path.join(HERE, "libtrtr.so")
 # debug build whose kernels check their memory accesses (TRTR_BOUNDS_CHECK=1)
 LIB_CHECKED = os.path.join(HERE, "libtrtr_checked.so")
 
-SOURCES = ["trtr_api.cu", "trtr_step.cu", "trtr_aux.cu", "trtr_noalloc.cu", "trtr_batch.cu", "trtr_adjoint.cu"]
+SOURCES = ["trtr_api.cu", "trtr_step.cu", "trtr_step2.cu", "trtr_aux.cu", "trtr_noalloc.cu", "trtr_batch.cu",
+           "trtr_adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
                      "-I", INCLUDE, "-I", CSRC]

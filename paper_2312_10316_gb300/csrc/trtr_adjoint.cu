@@ -222,7 +222,7 @@ trtr_status trtr_forward_record(trtr_ctx* ctx, long steps, int interval) {
     if (a->interval > steps) a->interval = (int)steps;
     a->nseg = (int)((steps + a->interval - 1) / a->interval);
     a->state_bytes = trtr::kQ * ctx->lp.plane * ctx->esize;
-    a->lq = trtr::make_layout(ctx->p.nx, ctx->p.ny, trtr::adj_csize(ctx));
+    a->lq = trtr::make_layout(ctx->p.nx, ctx->p.ny, trtr::adj_csize(ctx), 1);
     const size_t qbytes = trtr::kQ * a->lq.plane * trtr::adj_csize(ctx);
     bool ok = cudaMalloc(&a->Q[0], qbytes) == cudaSuccess && cudaMalloc(&a->Q[1], qbytes) == cudaSuccess &&
               cudaMalloc(&a->grad, (size_t)ctx->p.nx * ctx->p.ny * sizeof(double)) == cudaSuccess;
@@ -254,6 +254,7 @@ trtr_status trtr_forward_record(trtr_ctx* ctx, long steps, int interval) {
         if (trtr::launch_step(ctx) != cudaSuccess) return adj_fail(ctx, TRTR_ECUDA, "step launch failed");
         ctx->launches += 1;
         ctx->cur ^= 1;
+        ctx->ghost2_ready = false;
         ctx->step += 1;
     }
     return TRTR_OK;

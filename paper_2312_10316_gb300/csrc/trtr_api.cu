@@ -15,7 +15,7 @@ namespace trtr {
 cudaError_t bounds_take_all(cudaStream_t s, unsigned long long* out) {
     out[0] = out[1] = out[2] = 0ull;
     cudaError_t (*units[])(cudaStream_t, unsigned long long*) = {bounds_take_step, bounds_take_aux, bounds_take_batch,
-                                                                  bounds_take_adjoint};
+                                                                  bounds_take_adjoint, bounds_take_step2};
     for (auto take : units) {
         unsigned long long u[3];
         const cudaError_t e = take(s, u);
@@ -216,8 +216,8 @@ trtr_status trtr_create(const trtr_params* p, void* cuda_stream, trtr_ctx** out)
     if (p->check_every < 0 || !isfinite(p->phi_ref)) return TRTR_EINVAL;
     if (p->bc_mode != TRTR_BC_PERIODIC && p->bc_mode != TRTR_BC_DIRICHLET_NEE) return TRTR_EINVAL;
     if (p->bc_mode == TRTR_BC_DIRICHLET_NEE && (p->nx < 3 || p->ny < 3)) return TRTR_EINVAL;
-    const trtr::PlaneLayout lp = trtr::make_layout(p->nx, p->ny, (int)es);
-    const trtr::PlaneLayout lf = trtr::make_layout(p->nx, p->ny, p->precision == TRTR_F64 ? 8 : 4);
+    const trtr::PlaneLayout lp = trtr::make_layout(p->nx, p->ny, (int)es, trtr::kGhostP);
+    const trtr::PlaneLayout lf = trtr::make_layout(p->nx, p->ny, p->precision == TRTR_F64 ? 8 : 4, trtr::kGhostF);
     if ((long long)trtr::kQ * (long long)lp.plane >= (1LL << 31) || 2LL * (long long)lf.plane >= (1LL << 31))
         return TRTR_EINVAL;
 
@@ -231,6 +231,11 @@ trtr_status trtr_create(const trtr_params* p, void* cuda_stream, trtr_ctx** out)
     ctx->lp = lp;
     ctx->lf = lf;
     ctx->S_cur = ctx->S_prev = -1;
+    ctx->steps_per_launch = 2;
+    // the two-step kernel's packed fields (FP32 storage, periodic, no field source)
+    const bool two_step = p->precision == TRTR_F32 && p->bc_mode == TRTR_BC_PERIODIC &&
+                          p->src_mode != TRTR_SRC_FIELD && p->nx >= 2 && p->ny >= 2;
+    ctx->lt = trtr::make_layout(p->nx, p->ny, 4, trtr::kGhostP);
 
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
@@ -260,6 +265,7 @@ trtr_status trtr_create(const trtr_params* p, void* cuda_stream, trtr_ctx** out)
         {(void**)&ctx->dflag, sizeof(int), true},
         {(void**)&ctx->phib,
          p->bc_mode == TRTR_BC_DIRICHLET_NEE ? (size_t)trtr::edge_count(p->nx, p->ny) * sizeof(double) : 0, true},
+        {&ctx->fld2, two_step ? 5 * ctx->lt.plane * sizeof(float) : 0, true},
     };
     for (auto& a : allocs) {
         if (a.bytes == 0) continue;
@@ -280,7 +286,7 @@ trtr_status trtr_create(const trtr_params* p, void* cuda_stream, trtr_ctx** out)
         trtr_destroy(ctx);
         return TRTR_ENOMEM;
     }
-    if (trtr::encode_maps(ctx) != cudaSuccess) {
+    if (trtr::encode_maps(ctx) != cudaSuccess || trtr::encode_maps2(ctx) != cudaSuccess) {
         cudaGetLastError();
         trtr_destroy(ctx);
         return TRTR_ECUDA;
@@ -295,7 +301,7 @@ trtr_status trtr_destroy(trtr_ctx* ctx) {
     cudaGetLastError();
     trtr::free_adjoint(ctx);
     void* ptrs[] = {ctx->pop[0], ctx->pop[1],  ctx->uv,   ctx->Dh,    ctx->S,    ctx->tab_x,
-                    ctx->tab_y,  ctx->scratch, ctx->dres, ctx->dflag, ctx->dtmp, ctx->phib};
+                    ctx->tab_y,  ctx->scratch, ctx->dres, ctx->dflag, ctx->dtmp, ctx->phib, ctx->fld2};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (ctx->hres) cudaFreeHost(ctx->hres);
@@ -385,6 +391,7 @@ trtr_status trtr_set_fields(trtr_ctx* ctx, const double* ux, const double* uy, c
     s = check_launch(ctx, trtr::launch_convert_fields(ctx, dux, duy, dD), "field conversion");
     if (s != TRTR_OK) return s;
     ctx->fields_set = true;
+    ctx->fld2_ready = false;
     if (S) {
         ctx->S_cur = ctx->S_prev = -1;
         // staging slot 0 is reused; the copy into it is ordered after the conversion above
@@ -414,6 +421,7 @@ trtr_status trtr_set_pulse(trtr_ctx* ctx, double omega, double xc, double yc, do
     if (s != TRTR_OK) return s;
     ctx->pulse_set = true;
     ctx->fields_set = true;
+    ctx->fld2_ready = false;
     return TRTR_OK;
 }
 
@@ -431,6 +439,7 @@ trtr_status trtr_init_equilibrium(trtr_ctx* ctx, const double* phi0, int on_devi
     }
     trtr_status s = check_launch(ctx, trtr::launch_init_equilibrium(ctx, dev), "init");
     if (s != TRTR_OK) return s;
+    ctx->ghost2_ready = true;  // written with the whole ghost frame
     ctx->step = 0;
     ctx->initialized = true;
     ctx->S_prev = -1;
@@ -449,16 +458,41 @@ trtr_status trtr_step(trtr_ctx* ctx, long n) {
     const bool nee = ctx->p.bc_mode == TRTR_BC_DIRICHLET_NEE;
     if (nee && !ctx->dirichlet_set)
         return fail(ctx, TRTR_ESTATE, "bc_mode DIRICHLET_NEE needs boundary values (trtr_set_dirichlet)");
-    for (long k = 0; k < n; ++k) {
-        cudaError_t e = trtr::launch_step(ctx);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "step launch");
-        ctx->launches += 1;
-        if (nee) {
-            e = trtr::launch_dirichlet(ctx, ctx->pop[ctx->cur ^ 1]);
-            if (e != cudaSuccess) return cuda_fail(ctx, e, "boundary launch");
+    const bool two = trtr::two_step_applies(ctx);
+    const long every = ctx->p.check_every;
+    for (long k = 0; k < n;) {
+        // two steps per launch where the kernel applies, unless the step between them is one
+        // that the stability check looks at
+        if (two && n - k >= 2 && !(every > 0 && (ctx->step + 1) % every == 0)) {
+            if (!ctx->fld2_ready) {
+                cudaError_t e = trtr::launch_pack_fields2(ctx);
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "field packing launch");
+                ctx->fld2_ready = true;
+            }
+            if (!ctx->ghost2_ready) {  // after one-step launches: complete the two-wide frame
+                cudaError_t e = trtr::launch_refresh_ghosts2(ctx);
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "ghost refresh launch");
+            }
+            cudaError_t e = trtr::launch_step2(ctx);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "two-step launch");
+            ctx->launches += 1;
+            ctx->ghost2_ready = true;
+            ctx->cur ^= 1;
+            ctx->step += 2;
+            k += 2;
+        } else {
+            cudaError_t e = trtr::launch_step(ctx);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "step launch");
+            ctx->launches += 1;
+            ctx->ghost2_ready = false;  // the one-step kernel writes the one-wide frame
+            if (nee) {
+                e = trtr::launch_dirichlet(ctx, ctx->pop[ctx->cur ^ 1]);
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "boundary launch");
+            }
+            ctx->cur ^= 1;
+            ctx->step += 1;
+            k += 1;
         }
-        ctx->cur ^= 1;
-        ctx->step += 1;
         if (ctx->p.src_mode == TRTR_SRC_FIELD) ctx->S_prev = ctx->S_cur;
         if (ctx->p.check_every > 0 && (ctx->step % ctx->p.check_every) == 0) {
             double r[2];
@@ -562,6 +596,7 @@ trtr_status trtr_set_populations(trtr_ctx* ctx, const double* g, int on_device, 
     if (s == TRTR_OK) s = stage_in(ctx, g, trtr::kQ * n_nodes(ctx), on_device, 0, &dev);
     if (s != TRTR_OK) return s;
     s = check_launch(ctx, trtr::launch_set_populations(ctx, dev), "set populations");
+    if (s == TRTR_OK) ctx->ghost2_ready = true;
     if (s != TRTR_OK) return s;
     ctx->step = step;
     ctx->initialized = true;
@@ -662,6 +697,7 @@ trtr_status trtr_load(trtr_ctx* ctx, const void* host_buf, size_t bytes) {
     }
     TRTR_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "load");
     ctx->step = h.step;
+    ctx->ghost2_ready = false;  // the saved frame may be the one-step kernels' one-wide one
     ctx->initialized = true;
     return TRTR_OK;
 }
@@ -687,6 +723,13 @@ trtr_status trtr_check_bounds_path(trtr_ctx* ctx) {
     trtr_status s = check_launch(ctx, trtr::launch_bounds_probe(ctx), "bounds check");
     if (s != TRTR_OK) return s;
     return sync_and_check(ctx, "bounds check");
+}
+
+trtr_status trtr_set_steps_per_launch(trtr_ctx* ctx, int k) {
+    if (!ctx) return TRTR_EINVAL;
+    if (k != 1 && k != 2) return fail(ctx, TRTR_EINVAL, "steps per launch must be 1 or 2");
+    ctx->steps_per_launch = k;
+    return TRTR_OK;
 }
 
 trtr_status trtr_launch_count(const trtr_ctx* ctx, long* launches) {

@@ -125,13 +125,13 @@ __global__ void __launch_bounds__(32 * BY, min_blocks<BY>())
         constexpr int kPe = (int)sizeof(S), kFe = (int)sizeof(C);
 #pragma unroll
         for (int q = 0; q < kQ; ++q) {
-            const int x = t.y + gxp - (lattice_ex(q) == 1 ? T::A : 0), y = t.z + 1 - lattice_ey(q);
+            const int x = t.y + gxp - (lattice_ex(q) == 1 ? T::A : 0), y = t.z + kGhostP - lattice_ey(q);
             if (tma_ok(stage + q * T::POP_PLANE, x, y, kPe)) tma_load_3d(stage + q * T::POP_PLANE, &d->mp[parity], bar, x, y, q);
         }
-        if (tma_ok(stage + T::POP, t.y + gxf - T::AC, t.z, kFe))
-            tma_load_3d(stage + T::POP, &d->mu, bar, t.y + gxf - T::AC, t.z, 0);
-        if (tma_ok(stage + T::POP + T::U, t.y + gxf, t.z + 1, kFe))
-            tma_load_2d(stage + T::POP + T::U, &d->md, bar, t.y + gxf, t.z + 1);
+        if (tma_ok(stage + T::POP, t.y + gxf - T::AC, t.z + kGhostF - 1, kFe))
+            tma_load_3d(stage + T::POP, &d->mu, bar, t.y + gxf - T::AC, t.z + kGhostF - 1, 0);
+        if (tma_ok(stage + T::POP + T::U, t.y + gxf, t.z + kGhostF, kFe))
+            tma_load_2d(stage + T::POP + T::U, &d->md, bar, t.y + gxf, t.z + kGhostF);
         constexpr int kStatic = (int)(sizeof(StepArgs<C>) - sizeof(TimeFields<C>));
         cp_async_16(&sargs[s], &d->base[parity], kStatic);
         if (SRC == TRTR_SRC_PULSE) cp_async_16(&sargs[s].tf, &tu[t.x], (int)sizeof(TimeFields<C>));
@@ -470,6 +470,7 @@ trtr_status advance(trtr_batch* b, long n) {
     for (int k = 0; k < b->count; ++k) {
         b->ctx[k]->step = b->step;
         b->ctx[k]->cur = b->parity;
+        b->ctx[k]->ghost2_ready = false;
         b->ctx[k]->launches += n;
     }
     return TRTR_OK;

@@ -2,9 +2,10 @@
 // library (not part of the public ABI).
 //
 // Device layout (all buffers owned by the context).  Every plane is "ghosted": the interior
-// node (i, j) sits at row j + 1 and column gx + i of a [rows][pitch] plane, where gx is one
-// 128-byte line of columns, so interior rows start on a 128-byte boundary and the column
-// before / after the interior and the row above / below it hold ghost copies:
+// node (i, j) sits at row j + gy and column gx + i of a [rows][pitch] plane, where gx is one
+// 128-byte line of columns, so interior rows start on a 128-byte boundary, and the gy columns
+// before / after the interior and the gy rows above / below it hold ghost copies (gy = 2 for
+// the populations, 1 for the fields of the one-step kernel):
 //
 //   populations  2 x [9][rows][pitch] in the storage type: the post-collision values P_i(x)
 //                of the previous step; the pre-collision population is the pull
@@ -21,7 +22,7 @@
 //                (TRTR_BC_DIRICHLET_NEE), in the order of edge_node()
 //   scratch      FP64 partial sums of the reductions, one pair per reduction block
 //   flag         device int set by a kernel whose bounded wait gave up
-// rows >= ny + 2 and pitch >= nx + 2 gx are padded so that every TMA box fits inside the
+// rows >= ny + 2 gy and pitch >= nx + 2 gx are padded so that every TMA box fits inside the
 // allocation.
 #pragma once
 
@@ -106,28 +107,45 @@ cudaError_t bounds_take_step(cudaStream_t s, unsigned long long* out);
 cudaError_t bounds_take_aux(cudaStream_t s, unsigned long long* out);
 cudaError_t bounds_take_batch(cudaStream_t s, unsigned long long* out);
 cudaError_t bounds_take_adjoint(cudaStream_t s, unsigned long long* out);
+cudaError_t bounds_take_step2(cudaStream_t s, unsigned long long* out);
 // All units: the summed count, and the kind and place of the first unit's first access.
 cudaError_t bounds_take_all(cudaStream_t s, unsigned long long* out);
+
+// Ghost frame widths: the population planes keep two ghost columns and rows on each side (the
+// two-step kernel pulls twice across an edge); the field planes of the one-step kernel one.
+#ifndef TRTR_GHOST_P
+#define TRTR_GHOST_P 2
+#endif
+constexpr int kGhostP = TRTR_GHOST_P;
+constexpr int kGhostF = 1;
 
 struct PlaneLayout {
     int nx, ny;
     int gx;        // column of interior x = 0 (128 bytes of columns)
+    int gy;        // row of interior y = 0 = width of the ghost frame
     int pitch;     // elements per row
-    int rows;      // rows per plane (>= ny + 2)
+    int rows;      // rows per plane (>= ny + 2 gy)
     size_t plane;  // rows * pitch
-    __host__ __device__ __forceinline__ size_t at(int i, int j) const {
+    __host__ __device__ __forceinline__ size_t at(int i, int j) const { return at_w(i, j, gy); }
+    // the same for a layout whose ghost width G is known at compile time (G == gy)
+    template <int G>
+    __host__ __device__ __forceinline__ size_t at_g(int i, int j) const {
+        return at_w(i, j, G);
+    }
+    __host__ __device__ __forceinline__ size_t at_w(int i, int j, int g) const {
 #if TRTR_BOUNDS_CHECK && defined(__CUDA_ARCH__)
-        if (i < -1 || i > nx || j < -1 || j > ny) {  // outside the interior and its ghost frame
+        if (g != gy || i < -g || i >= nx + g || j < -g || j >= ny + g) {  // outside the interior and its ghost frame
             TRTR_BOUNDS_FAULT(kBoundsPlane, i, j);
-            i = i < -1 ? -1 : (i > nx ? nx : i);
-            j = j < -1 ? -1 : (j > ny ? ny : j);
+            g = gy;
+            i = i < -g ? -g : (i >= nx + g ? nx + g - 1 : i);
+            j = j < -g ? -g : (j >= ny + g ? ny + g - 1 : j);
         }
 #endif
-        return (size_t)(j + 1) * (size_t)pitch + (size_t)(i + gx);
+        return (size_t)(j + g) * (size_t)pitch + (size_t)(i + gx);
     }
 };
 
-PlaneLayout make_layout(int nx, int ny, int elem_bytes);
+PlaneLayout make_layout(int nx, int ny, int elem_bytes, int ghost);
 
 // Storage traits: how a population is kept in memory and turned into the compute type.
 template <typename S>
@@ -226,6 +244,13 @@ struct trtr_ctx {
     double* phib;     // Dirichlet values of the edge nodes (TRTR_BC_DIRICHLET_NEE)
     bool fields_set, pulse_set, initialized, maps_ready, dirichlet_set;
     bool small_tiles;  // step kernel geometry for small grids (chosen by encode_maps)
+    // two-step kernel (FP32 storage, periodic boundaries, no source or the pulse source)
+    CUtensorMap maps2[3];   // populations (buffers 0, 1) and packed fields, its tile boxes
+    void* fld2;             // [5][rows][pitch] float: uhat_x, uhat_y, a_x, a_y, Dh, two-wide periodic ghosts
+    trtr::PlaneLayout lt;   // layout of fld2
+    bool fld2_ready;        // fld2 holds the current fields
+    bool ghost2_ready;      // the current population buffer's whole two-wide ghost frame is up to date
+    int steps_per_launch;   // 2: trtr_step uses the two-step kernel where it applies; 1: never
     trtr::Pulse pulse;
     long step;
     long launches;
@@ -242,6 +267,14 @@ cudaError_t launch_step(trtr_ctx* ctx);
 // one step from an arbitrary population buffer (its map from encode_pop_map) into dst, as step `step`
 cudaError_t launch_step_from(trtr_ctx* ctx, const CUtensorMap* src_map, void* dst, long step);
 cudaError_t encode_pop_map(trtr_ctx* ctx, void* buffer, CUtensorMap* out);
+// The two-step kernel: whether it applies to the context, its maps (at creation), the packed
+// fields (after each change of u or D), and one launch advancing the state by two steps.
+bool two_step_applies(const trtr_ctx* ctx);
+cudaError_t encode_maps2(trtr_ctx* ctx);
+cudaError_t launch_pack_fields2(trtr_ctx* ctx);
+cudaError_t launch_step2(trtr_ctx* ctx);
+// the distance-2 ghost cells of the current population buffer from its interior (periodic)
+cudaError_t launch_refresh_ghosts2(trtr_ctx* ctx);
 // one block whose bounded wait on a barrier that nothing completes gives up after `cycles`
 cudaError_t launch_wait_timeout(trtr_ctx* ctx, long long cycles);
 // one thread that gives the bounds checks four bad arguments and accesses nothing with them
@@ -280,27 +313,32 @@ __host__ __device__ inline void edge_node(int k, int nx, int ny, int* i, int* j)
 __host__ __device__ constexpr int lattice_ex(int q) { return q == 1 || q == 5 || q == 7 ? 1 : (q == 2 || q == 6 || q == 8 ? -1 : 0); }
 __host__ __device__ constexpr int lattice_ey(int q) { return q == 3 || q == 5 || q == 8 ? 1 : (q == 4 || q == 6 || q == 7 ? -1 : 0); }
 
-// Stores one population value at every ghost cell that repeats interior node (i, j) (the
-// periodic images just outside the interior); nothing for nodes off the edges.
-template <typename T>
+// Stores one population value at every ghost cell that repeats interior node (i, j): the
+// periodic images within W of the edges (W = 0: the layout's whole frame, L.gy wide), placed
+// by a layout whose ghost width is GY (GY = 0: L.gy, read at run time; the step kernels know
+// it at compile time).  The one-step kernels write the W = 1 frame that they read; the
+// two-step kernel writes and reads the whole W = 2 frame (refresh_ghosts2 completes a frame
+// left by one-step launches).
+template <int W = 0, int GY = 0, typename T>
 __device__ __forceinline__ void store_ghosts(T* plane, const PlaneLayout& L, int i, int j, T v) {
-    const bool xl = i == 0, xr = i == L.nx - 1, yl = j == 0, yr = j == L.ny - 1;
+    const int w = W > 0 ? W : L.gy, g = GY > 0 ? GY : L.gy;
+    const bool xl = i < w, xr = i >= L.nx - w, yl = j < w, yr = j >= L.ny - w;
     if (!(xl || xr || yl || yr)) return;
-    if (xl) plane[L.at(L.nx, j)] = v;
-    if (xr) plane[L.at(-1, j)] = v;
-    if (yl) plane[L.at(i, L.ny)] = v;
-    if (yr) plane[L.at(i, -1)] = v;
-    if (xl && yl) plane[L.at(L.nx, L.ny)] = v;
-    if (xl && yr) plane[L.at(L.nx, -1)] = v;
-    if (xr && yl) plane[L.at(-1, L.ny)] = v;
-    if (xr && yr) plane[L.at(-1, -1)] = v;
+    if (xl) plane[L.at_w(i + L.nx, j, g)] = v;
+    if (xr) plane[L.at_w(i - L.nx, j, g)] = v;
+    if (yl) plane[L.at_w(i, j + L.ny, g)] = v;
+    if (yr) plane[L.at_w(i, j - L.ny, g)] = v;
+    if (xl && yl) plane[L.at_w(i + L.nx, j + L.ny, g)] = v;
+    if (xl && yr) plane[L.at_w(i + L.nx, j - L.ny, g)] = v;
+    if (xr && yl) plane[L.at_w(i - L.nx, j + L.ny, g)] = v;
+    if (xr && yr) plane[L.at_w(i - L.nx, j - L.ny, g)] = v;
 }
 
 // Stores one population value at interior node (i, j) and at its ghost cells.
-template <typename T>
+template <int W = 0, int GY = 0, typename T>
 __device__ __forceinline__ void store_with_ghosts(T* plane, const PlaneLayout& L, int i, int j, T v) {
-    plane[L.at(i, j)] = v;
-    store_ghosts(plane, L, i, j, v);
+    plane[L.at_w(i, j, GY > 0 ? GY : L.gy)] = v;
+    store_ghosts<W, GY>(plane, L, i, j, v);
 }
 
 }  // namespace trtr

@@ -259,8 +259,8 @@ __global__ void wait_timeout_kernel(int* flag, long long cycles) {
 __global__ void bounds_probe_kernel(PlaneLayout L) {
     __shared__ __align__(128) unsigned char buf[256];
     if (threadIdx.x != 0) return;
-    const size_t k = L.at(L.nx + 1, 0);
-    const bool clamped = k == L.at(L.nx, 0);
+    const size_t k = L.at(L.nx + L.gy, 0);
+    const bool clamped = k == L.at(L.nx + L.gy - 1, 0);
     const bool t1 = tma_ok(buf, 3, 0, 4);
     const bool t2 = tma_ok(buf + 16, 0, 0, 4);
     const bool b1 = bulk_ok(static_cast<const float*>(nullptr), buf, L.nx - 4, 0, 8, L);

@@ -327,18 +327,19 @@ __device__ __forceinline__ void issue_tile(unsigned char* stage, uint64_t* bar, 
     constexpr int kPe = (int)sizeof(S), kFe = (int)sizeof(typename Store<S>::C);
     for (int q = 0; q < kQ; ++q) {
         const int x = i0 + a.lp.gx - (lattice_ex(q) == 1 ? T::A : 0);
-        const int y = j0 + 1 - lattice_ey(q);
+        const int y = j0 + kGhostP - lattice_ey(q);
         if (tma_ok(stage + q * T::POP_PLANE, x, y, kPe)) tma_load_3d(stage + q * T::POP_PLANE, mp, bar, x, y, q);
     }
-    if (tma_ok(stage + T::POP, i0 + a.lf.gx - T::AC, j0, kFe))
-        tma_load_3d(stage + T::POP, mu, bar, i0 + a.lf.gx - T::AC, j0, 0);
-    if (tma_ok(stage + T::POP + T::U, i0 + a.lf.gx, j0 + 1, kFe))
-        tma_load_2d(stage + T::POP + T::U, md, bar, i0 + a.lf.gx, j0 + 1);
+    const int yf = j0 + kGhostF;  // field row of the tile's first row
+    if (tma_ok(stage + T::POP, i0 + a.lf.gx - T::AC, yf - 1, kFe))
+        tma_load_3d(stage + T::POP, mu, bar, i0 + a.lf.gx - T::AC, yf - 1, 0);
+    if (tma_ok(stage + T::POP + T::U, i0 + a.lf.gx, yf, kFe))
+        tma_load_2d(stage + T::POP + T::U, md, bar, i0 + a.lf.gx, yf);
     if (SRC == TRTR_SRC_FIELD) {
         unsigned char* s = stage + T::POP + T::U + T::D;
-        if (tma_ok(s, i0 + a.lf.gx, j0 + 1, kFe)) tma_load_3d(s, ms, bar, i0 + a.lf.gx, j0 + 1, a.s_cur);
-        if (tma_ok(s + T::S_TILE, i0 + a.lf.gx, j0 + 1, kFe))
-            tma_load_3d(s + T::S_TILE, ms, bar, i0 + a.lf.gx, j0 + 1, a.s_prev);
+        if (tma_ok(s, i0 + a.lf.gx, yf, kFe)) tma_load_3d(s, ms, bar, i0 + a.lf.gx, yf, a.s_cur);
+        if (tma_ok(s + T::S_TILE, i0 + a.lf.gx, yf, kFe))
+            tma_load_3d(s + T::S_TILE, ms, bar, i0 + a.lf.gx, yf, a.s_prev);
     }
 }
 
@@ -429,7 +430,8 @@ __device__ __forceinline__ void tile_row_pairs(const unsigned char* st, int r, i
         // 2-byte storages: g and out stay offsets (the offset is folded into the moments)
         collide_node<F2, kOfs>(g, ux, uy, ax, ay, Dh, src, magic, w2f, a.tau2_fixed, out, F2(phi_ref));
 
-        // a8: store P_i(x); edge nodes also write their periodic ghost copies
+        // a8: store P_i(x); edge nodes also write their periodic ghost copies (the one-wide frame
+        // that the one-step kernel reads)
         const bool edge = j == 0 || j == ny - 1 || i == 0 || i + 1 >= nx - 1;
         if constexpr (TST) {
             __syncwarp();  // every lane has read its inputs of pair m
@@ -443,14 +445,14 @@ __device__ __forceinline__ void tile_row_pairs(const unsigned char* st, int r, i
                 for (int q = 0; q < kQ; ++q) {
                     const S2 v = P::encode_raw(out[q]);
                     const S v0 = reinterpret_cast<const S*>(&v)[0], v1 = reinterpret_cast<const S*>(&v)[1];
-                    if (c >= nb) dst[q * pl + a.lp.at(i, j)] = v0;
-                    if (c + 1 >= nb && i + 1 < nx) dst[q * pl + a.lp.at(i + 1, j)] = v1;
-                    store_ghosts(dst + q * pl, a.lp, i, j, v0);
-                    if (i + 1 < nx) store_ghosts(dst + q * pl, a.lp, i + 1, j, v1);
+                    if (c >= nb) dst[q * pl + a.lp.at_g<kGhostP>(i, j)] = v0;
+                    if (c + 1 >= nb && i + 1 < nx) dst[q * pl + a.lp.at_g<kGhostP>(i + 1, j)] = v1;
+                    store_ghosts<1, kGhostP>(dst + q * pl, a.lp, i, j, v0);
+                    if (i + 1 < nx) store_ghosts<1, kGhostP>(dst + q * pl, a.lp, i + 1, j, v1);
                 }
             }
         } else if (!edge) {
-            S* d0 = dst + a.lp.at(i, j);
+            S* d0 = dst + a.lp.at_g<kGhostP>(i, j);
 #if TRTR_BOUNDS_CHECK
             if (i + 1 >= nx || (reinterpret_cast<uintptr_t>(d0) % sizeof(S2)) != 0u) {
                 TRTR_BOUNDS_FAULT(kBoundsPair, i, j);
@@ -464,8 +466,8 @@ __device__ __forceinline__ void tile_row_pairs(const unsigned char* st, int r, i
 #pragma unroll
             for (int q = 0; q < kQ; ++q) {
                 const S2 v = P::encode_raw(out[q]);
-                store_with_ghosts(dst + q * pl, a.lp, i, j, reinterpret_cast<const S*>(&v)[0]);
-                if (i + 1 < nx) store_with_ghosts(dst + q * pl, a.lp, i + 1, j, reinterpret_cast<const S*>(&v)[1]);
+                store_with_ghosts<1, kGhostP>(dst + q * pl, a.lp, i, j, reinterpret_cast<const S*>(&v)[0]);
+                if (i + 1 < nx) store_with_ghosts<1, kGhostP>(dst + q * pl, a.lp, i + 1, j, reinterpret_cast<const S*>(&v)[1]);
             }
         }
     }
@@ -476,8 +478,8 @@ __device__ __forceinline__ void tile_row_pairs(const unsigned char* st, int r, i
         if (lane == 0 && nb > 0) {
 #pragma unroll
             for (int q = 0; q < kQ; ++q)
-                if (bulk_ok(dst + q * pl + a.lp.at(i0, j), sp + q * T::PLANE_ELEMS, i0, j, nb, a.lp))
-                    bulk_store(dst + q * pl + a.lp.at(i0, j), sp + q * T::PLANE_ELEMS, (uint32_t)(nb * sizeof(S)));
+                if (bulk_ok(dst + q * pl + a.lp.at_g<kGhostP>(i0, j), sp + q * T::PLANE_ELEMS, i0, j, nb, a.lp))
+                    bulk_store(dst + q * pl + a.lp.at_g<kGhostP>(i0, j), sp + q * T::PLANE_ELEMS, (uint32_t)(nb * sizeof(S)));
             bulk_commit();
             bulk_wait_read();  // the stage may be refilled after the CTA barrier
         }
@@ -543,13 +545,13 @@ __device__ __forceinline__ void tile_row_f64(const unsigned char* st, int r, int
                 const bool tail = c >= bulk_cols<double>(nx - i0);
 #pragma unroll
                 for (int q = 0; q < kQ; ++q) {
-                    if (tail) dst[q * pl + a.lp.at(i, j)] = out[q];
-                    store_ghosts(dst + q * pl, a.lp, i, j, out[q]);
+                    if (tail) dst[q * pl + a.lp.at_g<kGhostP>(i, j)] = out[q];
+                    store_ghosts<1, kGhostP>(dst + q * pl, a.lp, i, j, out[q]);
                 }
             }
         } else {
 #pragma unroll
-            for (int q = 0; q < kQ; ++q) store_with_ghosts(dst + q * pl, a.lp, i, j, out[q]);
+            for (int q = 0; q < kQ; ++q) store_with_ghosts<1, kGhostP>(dst + q * pl, a.lp, i, j, out[q]);
         }
     }
     if constexpr (TST) {
@@ -559,8 +561,8 @@ __device__ __forceinline__ void tile_row_f64(const unsigned char* st, int r, int
         if (lane == 0 && nb > 0) {
 #pragma unroll
             for (int q = 0; q < kQ; ++q)
-                if (bulk_ok(dst + q * pl + a.lp.at(i0, j), sp + q * T::PLANE_ELEMS, i0, j, nb, a.lp))
-                    bulk_store(dst + q * pl + a.lp.at(i0, j), sp + q * T::PLANE_ELEMS,
+                if (bulk_ok(dst + q * pl + a.lp.at_g<kGhostP>(i0, j), sp + q * T::PLANE_ELEMS, i0, j, nb, a.lp))
+                    bulk_store(dst + q * pl + a.lp.at_g<kGhostP>(i0, j), sp + q * T::PLANE_ELEMS,
                                (uint32_t)(nb * sizeof(double)));
             bulk_commit();
             bulk_wait_read();

@@ -102,6 +102,7 @@ _SIGNATURES = {
     "trtr_bounds_checked": (ctypes.c_int, []),
     "trtr_bounds_report": (_st, [ctypes.POINTER(ctypes.c_ulonglong)]),
     "trtr_check_bounds_path": (_st, [_vp]),
+    "trtr_set_steps_per_launch": (_st, [_vp, ctypes.c_int]),
 }
 
 
@@ -342,6 +343,10 @@ def trtr_abi_version() -> int:
     return int(lib.trtr_abi_version())
 
 
+def trtr_set_steps_per_launch(ctx, k: int):
+    _check(ctx, lib.trtr_set_steps_per_launch(ctx, int(k)))
+
+
 def trtr_check_bounds_path(ctx) -> int:
     """Status of the bounds-check probe (TRTR_EBOUNDS in the checked build, TRTR_OK otherwise)."""
     return int(lib.trtr_check_bounds_path(ctx))
@@ -434,6 +439,9 @@ class Solver:
 
     def step(self, n: int = 1):
         trtr_step(self.ctx, n)
+
+    def set_steps_per_launch(self, k: int):
+        trtr_set_steps_per_launch(self.ctx, k)
 
     def moments(self, out=None):
         if out is None:

@@ -24,7 +24,7 @@ if not torch.cuda.is_available():
 from paper_2312_10316_gb300 import trtr as T  # noqa: E402
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-SUITES = ["tests/test_gpu_parity.py", "tests/test_gpu_paper.py", "tests/test_gpu_batch.py",
+SUITES = ["tests/test_gpu_parity.py", "tests/test_gpu_step2.py", "tests/test_gpu_paper.py", "tests/test_gpu_batch.py",
           "tests/test_gpu_adjoint.py", "tests/test_gpu_bounds_checked.py"]
 
 
@@ -37,7 +37,7 @@ def test_recording_path_without_a_bad_access():
         st = T.trtr_check_bounds_path(s.ctx)
         if T.BOUNDS_CHECKED:
             assert st == T.TRTR_EBOUNDS
-            assert f"4 out-of-bounds accesses; the first of kind 1 at ({nx + 1}, 0)" in T.trtr_last_error(s.ctx)
+            assert f"4 out-of-bounds accesses; the first of kind 1 at ({nx + 2}, 0)" in T.trtr_last_error(s.ctx)
         else:
             assert st == T.TRTR_OK
         # the record was cleared as it was reported: the context runs on

@@ -1,0 +1,137 @@
+"""The two-step kernel (two time steps of Eq. (14) per launch; FP32 storage, periodic
+boundaries, no source or the pulse source).
+
+Its node update is the one-step kernel's, so the populations after any number of steps must
+equal those of one launch per step bit for bit; the one-step path is checked against the FP64
+oracle elsewhere, and one case here checks the two-step path against the oracle directly.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2312_10316_gb300 import workloads as W
+
+from ._gpu_util import TOL_F32, oracle_for_pulse, random_case, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2312_10316_gb300 import trtr as T  # noqa: E402
+
+GRIDS = [(2, 3), (3, 5), (5, 3), (37, 23), (130, 9), (128, 8), (257, 19), (300, 130)]
+
+
+def _random_solver(nx, ny, grad_mode, k):
+    case = random_case(900 + 13 * nx + ny, nx, ny)
+    p = T.Params(nx=nx, ny=ny, dx=case["dx"], dt=case["dt"], precision=T.TRTR_F32, grad_mode=grad_mode,
+                 src_mode=T.TRTR_SRC_NONE)
+    s = T.Solver(p)
+    s.set_steps_per_launch(k)
+    s.set_fields(case["ux"], case["uy"], case["D"])
+    s.set_populations(case["g"], step=0)
+    return s
+
+
+def _pulse_solver(nx, ny, grad_mode, k, D_amp=0.5):
+    pulse = W.Pulse(n=max(nx, ny), D_amp=D_amp, courant=0.4)
+    p = T.Params(nx=nx, ny=ny, dx=pulse.dx, dt=pulse.dt, x0=pulse.x0, y0=pulse.y0, precision=T.TRTR_F32,
+                 grad_mode=grad_mode, src_mode=T.TRTR_SRC_PULSE)
+    s = T.Solver(p)
+    s.set_steps_per_launch(k)
+    s.set_pulse(pulse.omega, pulse.xc, pulse.yc, pulse.sigma0, pulse.D0, pulse.D_amp)
+    s.init_equilibrium(None)
+    return s
+
+
+@pytest.mark.parametrize("nx,ny", GRIDS)
+@pytest.mark.parametrize("grad_mode", [T.TRTR_GRAD_PERIODIC, T.TRTR_GRAD_ONESIDED_EDGE])
+@pytest.mark.parametrize("kind", ["none", "pulse"])
+def test_two_steps_per_launch_equal_one_step_launches_bitwise(nx, ny, grad_mode, kind):
+    make = _random_solver if kind == "none" else _pulse_solver
+    out = {}
+    for k in (1, 2):
+        with make(nx, ny, grad_mode, k) as s:
+            s.step(5)  # two two-step launches and one single step
+            s.step(3)  # the ghost frame's refresh after that single step, a pair, a single step
+            out[k] = (s.get_populations(), s.launches)
+    assert np.array_equal(out[1][0], out[2][0], equal_nan=True)
+    if min(nx, ny) >= 8:
+        assert np.isfinite(out[2][0]).all()
+
+
+def test_launch_counts_and_the_stability_check_cadence():
+    with _pulse_solver(64, 48, T.TRTR_GRAD_ONESIDED_EDGE, 2) as s:
+        l0 = s.launches
+        s.step(6)
+        assert s.launches - l0 == 1 + 3  # field packing, then three two-step launches
+        s.step(6)
+        assert s.launches - l0 == 1 + 6
+        s.step(1)
+        s.step(2)
+        assert s.launches - l0 == 1 + 6 + 1 + 2  # a single step, then ghost refresh + a pair
+    # check_every = 3: the pair whose middle step is a check point runs as single steps
+    ref = None
+    for k in (1, 2):
+        pulse = W.Pulse(n=64, D_amp=0.5, courant=0.4)
+        p = T.Params(nx=64, ny=48, dx=pulse.dx, dt=pulse.dt, x0=pulse.x0, y0=pulse.y0, precision=T.TRTR_F32,
+                     grad_mode=T.TRTR_GRAD_ONESIDED_EDGE, src_mode=T.TRTR_SRC_PULSE, check_every=3)
+        with T.Solver(p) as s:
+            s.set_steps_per_launch(k)
+            s.set_pulse(pulse.omega, pulse.xc, pulse.yc, pulse.sigma0, pulse.D0, pulse.D_amp)
+            s.init_equilibrium(None)
+            s.step(7)
+            g = s.get_populations()
+        ref = g if ref is None else ref
+        assert np.array_equal(g, ref)
+
+
+def test_new_fields_after_steps_are_repacked():
+    nx, ny = 96, 40
+    res = {}
+    for k in (1, 2):
+        with _random_solver(nx, ny, T.TRTR_GRAD_ONESIDED_EDGE, k) as s:
+            s.step(4)
+            case = random_case(77, nx, ny)
+            s.set_fields(case["ux"], case["uy"], case["D"])
+            s.step(4)
+            res[k] = s.get_populations()
+    assert np.array_equal(res[1], res[2])
+
+
+def test_two_step_path_against_the_oracle():
+    pulse = W.Pulse(n=200, D_amp=0.5, courant=0.4)
+    with T.pulse_solver(pulse, precision=T.TRTR_F32) as s:
+        assert s.params.src_mode == T.TRTR_SRC_PULSE
+        l0 = s.launches
+        s.step(8)
+        launches = s.launches - l0
+        phi = s.moments()
+    o = oracle_for_pulse(pulse)
+    o.step(8)
+    assert rel_l2(phi, o.phi()) <= TOL_F32
+    assert launches == 1 + 4  # field packing, four two-step launches
+
+
+def test_save_load_and_recorded_runs_keep_the_two_step_path_exact():
+    nx, ny = 70, 33
+    res = {}
+    for k in (1, 2):
+        with _pulse_solver(nx, ny, T.TRTR_GRAD_ONESIDED_EDGE, k) as s:
+            s.step(3)
+            blob = s.save()
+            s.step(2)
+            s.load(blob)  # back to step 3, saved after a single step
+            s.step(4)
+            res[k] = s.get_populations()
+    assert np.array_equal(res[1], res[2])
+
+
+def test_steps_per_launch_is_validated():
+    with _random_solver(16, 16, T.TRTR_GRAD_PERIODIC, 2) as s:
+        for bad in (0, 3, -1):
+            with pytest.raises(T.TrtrError) as e:
+                s.set_steps_per_launch(bad)
+            assert e.value.status == T.TRTR_EINVAL
