@@ -55,7 +55,8 @@ ADJOINT_WORKLOADS = {"adjoint512_f32": "f32"}
 # rotating pulse on [-2 pi, 2 pi]^2 with Dirichlet edges, through the library
 TABLE2_WORKLOADS = {"table2_f64": "f64", "table2_f32": "f32"}
 TABLE2_PRINTED = os.path.join(ROOT, "tests", "golden", "table2_convergence.txt")
-STEP_SOURCES = ["paper_2312_10316_gb300/csrc/trtr_step.cu", "paper_2312_10316_gb300/csrc/trtr_step_core.cuh",
+STEP_SOURCES = ["paper_2312_10316_gb300/csrc/trtr_step.cu", "paper_2312_10316_gb300/csrc/trtr_step2.cu",
+                "paper_2312_10316_gb300/csrc/trtr_step_core.cuh",
                 "paper_2312_10316_gb300/csrc/trtr_internal.cuh"]
 
 
@@ -73,6 +74,9 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--parity-steps", type=int, default=1000,
                     help="steps of the FP64 GPU comparison run that states the L2 error (0: skip)")
+    ap.add_argument("--steps-per-launch", default="auto", choices=["auto", "1", "2"],
+                    help="auto: two steps per launch where the two-step kernel applies; 1: one step per launch "
+                         "(the one-step kernel); 2: as auto")
     ap.add_argument("--src", default="auto", choices=["auto", "none", "field", "pulse"],
                     help="source mode of the timed step kernel (auto: the workload's; 'field' uses the "
                          "manufactured source as a stationary field); other than auto skips parity and e2e")
@@ -82,6 +86,12 @@ def parse_args():
 def algorithmic_bytes_per_node(pop_bytes: int, field_bytes: int = 4) -> int:
     """9 populations read + 9 written, plus u_x, u_y, D read once per node."""
     return 2 * 9 * pop_bytes + 3 * field_bytes
+
+
+def two_step_bytes_per_node(pop_bytes: int = 4, field_bytes: int = 4) -> int:
+    """One launch of the two-step kernel (two time steps): 9 populations read + 9 written, plus
+    the packed u_x, u_y, a_x, a_y, D read once per node."""
+    return 2 * 9 * pop_bytes + 5 * field_bytes
 
 
 def measured_hbm_peak():
@@ -101,8 +111,8 @@ def step_kernel_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload: str):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary, if it was taken
+def ncu_traffic(workload: str, kernel: str):
+    """DRAM bytes per launch of the timed kernel from the committed ncu summary, if it was taken
     on the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "step_kernel_counters.json")
     try:
@@ -111,7 +121,7 @@ def ncu_traffic(workload: str):
     except Exception:
         return None
     entry = d.get(workload)
-    if not entry or entry.get("kernel_sha") != step_kernel_sha():
+    if not entry or entry.get("kernel_sha") != step_kernel_sha() or entry.get("kernel", "step_kernel") != kernel:
         return None
     return entry.get("dram_bytes_per_launch")
 
@@ -286,35 +296,47 @@ def run_ours(args):
     clocks = ClockSampler(("GPU-" + uuid) if uuid and not uuid.startswith("GPU-") else uuid)
     clocks.start()
     time.sleep(0.4)  # let the sampler take a reading at the start of the region
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    # one event interval per launch: two steps per launch where the two-step kernel applies
+    if args.steps_per_launch == "1":
+        solver.set_steps_per_launch(1)
+    spl = solver.steps_per_launch
+    n_launch, tail = divmod(args.steps, spl)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(n_launch + 1 + (1 if tail else 0))]
     launches0 = solver.launches
     with torch.cuda.stream(stream):
         ev[0].record(stream)
-        for k in range(args.steps):
-            T.trtr_step(solver.ctx, 1)
+        for k in range(n_launch):
+            T.trtr_step(solver.ctx, spl)
             ev[k + 1].record(stream)
+        if tail:
+            T.trtr_step(solver.ctx, tail)
+            ev[-1].record(stream)
     stream.synchronize()
     torch.cuda.synchronize()
     barrier(world)
     clk = clocks.stop()
     gpu_launches = solver.launches - launches0
-    per_launch = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    per_launch = [ev[k].elapsed_time(ev[k + 1]) for k in range(n_launch)]
     total_ms = ev[0].elapsed_time(ev[-1])
     total_ms = max_over_ranks(total_ms, world)
     ms_per_step = total_ms / args.steps
     value = n_nodes * args.steps * world / (total_ms * 1e-3) / 1e9
     avg_launch_ms = sum(per_launch) / len(per_launch)
 
-    bpn = algorithmic_bytes_per_node(pop_bytes)
+    if spl == 2:
+        bpn, kernel = two_step_bytes_per_node(pop_bytes), "step2_kernel"
+    else:
+        bpn, kernel = algorithmic_bytes_per_node(pop_bytes), "step_kernel"
     if src_override == T.TRTR_SRC_FIELD:
         bpn += 2 * (8 if prec == T.TRTR_F64 else 4)  # S^n and S^{n-1} planes in the compute type
     peak, peak_kind = measured_hbm_peak()
     achieved = bpn * n_nodes / (avg_launch_ms * 1e-3) / 1e9
-    traffic = ncu_traffic(args.workload) if src_override is None else None
+    traffic = ncu_traffic(args.workload, kernel) if src_override is None else None
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_kind": f"{peak_kind} copy bandwidth", "bytes_per_node": bpn,
-                "kernel": "step_kernel", "median_launch_ms": round(statistics.median(per_launch), 5)}
+                "kernel": kernel, "steps_per_launch": spl,
+                "median_launch_ms": round(statistics.median(per_launch), 5)}
     phi_gpu = solver.moments() if args.parity_steps else None
     solver.close()
 
@@ -345,6 +367,8 @@ def run_ours(args):
                      tau2_mode=T.TRTR_TAU2_MAGIC if pulse.tau2 is None else T.TRTR_TAU2_FIXED,
                      tau2=pulse.tau2 or 1.0)
         with T.Solver(p, sh) as s:
+            if args.steps_per_launch == "1":
+                s.set_steps_per_launch(1)
             s.set_pulse(pulse.omega, pulse.xc, pulse.yc, pulse.sigma0, pulse.D0, pulse.D_amp)
             s.sync()
             barrier(world)

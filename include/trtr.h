@@ -167,6 +167,10 @@ trtr_status trtr_step(trtr_ctx* ctx, long n);
  * launch always.  TRTR_EINVAL for other k. */
 trtr_status trtr_set_steps_per_launch(trtr_ctx* ctx, int k);
 
+/* The steps one launch of trtr_step advances where it can on this context: 2 when the two-step
+ * kernel applies (FP32, periodic, src_mode NONE or PULSE, not disabled), else 1. */
+trtr_status trtr_get_steps_per_launch(const trtr_ctx* ctx, int* k);
+
 /* phi(x, t_n) = sum_i g_i(x, t_n) of the pre-collision populations (B_0^neq = 0, Sec. 2.2),
  * written as doubles [ny][nx].  Synchronises. */
 trtr_status trtr_moments(trtr_ctx* ctx, double* phi_out, int on_device);

@@ -88,6 +88,9 @@ def build_library(force: bool = False, verbose: bool = False, extra_flags: list[
 
 
 if __name__ == "__main__":
+    # python build.py [-v] [--ptxas] [--checked] [-DNAME=VALUE ...]: a forced rebuild; -D options
+    # set the kernels' compile-time geometry switches (TRTR_STEP_*, TRTR_STEP2_*)
     v = "-v" in sys.argv
-    extra = ["-Xptxas", "-v"] if "--ptxas" in sys.argv else None
-    print(build_library(force=True, verbose=v or bool(extra), extra_flags=extra, checked="--checked" in sys.argv))
+    extra = (["-Xptxas", "-v"] if "--ptxas" in sys.argv else []) + [a for a in sys.argv[1:] if a.startswith("-D")]
+    print(build_library(force=True, verbose=v or "--ptxas" in sys.argv, extra_flags=extra or None,
+                        checked="--checked" in sys.argv))

@@ -732,6 +732,12 @@ trtr_status trtr_set_steps_per_launch(trtr_ctx* ctx, int k) {
     return TRTR_OK;
 }
 
+trtr_status trtr_get_steps_per_launch(const trtr_ctx* ctx, int* k) {
+    if (!ctx || !k) return TRTR_EINVAL;
+    *k = trtr::two_step_applies(ctx) ? 2 : 1;
+    return TRTR_OK;
+}
+
 trtr_status trtr_launch_count(const trtr_ctx* ctx, long* launches) {
     if (!ctx || !launches) return TRTR_EINVAL;
     *launches = ctx->launches;

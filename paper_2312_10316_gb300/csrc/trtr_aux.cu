@@ -32,11 +32,6 @@ PlaneLayout make_layout(int nx, int ny, int elem_bytes, int ghost) {
     if (pitch < 320) pitch = 320;  // wider than every TMA box (<= 256 elements + origin shift)
     L.pitch = (int)pitch;
     L.rows = ny + 2 * ghost < 16 ? 16 : ny + 2 * ghost;
-#if defined(TRTR_ROWS_RULE) && TRTR_ROWS_RULE == 1
-    L.rows |= 1;  // odd
-#elif defined(TRTR_ROWS_RULE) && TRTR_ROWS_RULE == 2
-    while (L.rows % 4 != 2) ++L.rows;
-#endif
     L.plane = (size_t)L.rows * (size_t)L.pitch;
     return L;
 }

@@ -18,6 +18,9 @@
 //   Step 2 runs on the output nodes: node (r2, c2) = R1 node (r2 + 1, c2 + 2) pulls
 //   P1_q(x - e_q) from (row r2 + 2 - 2 ey_q, column c2 + 4 - 2 ex_q) and stores P2 to global
 //   memory with its ghost copies (nodes within two of an edge).
+// Block: 512 threads (16 warps, about 106 registers each) and two stages of 86 KB, one CTA per
+// SM; the kernel is latency-bound at this size (measured: 16 warps 82 GLUPS, 8 warps 77, 12
+// warps 75 at 4096^2), step 1 takes two passes of the block (660 node pairs), step 2 one (512).
 // R1 nodes outside the grid are periodic images: their populations come from the ghost frame,
 // their fields from the packed fields' ghost frame (copies of the wrapped node, the acceleration
 // included, whatever the gradient mode), and their source from the wrapped node's coordinates,
@@ -36,7 +39,6 @@ constexpr int kT2FR = kT2Y + 2;                      // staged field rows
 constexpr int kT2NF = 5;                             // uhat_x, uhat_y, a_x, a_y, Dh
 constexpr int kT2R1 = (kT2Y + 2) * (kT2X + 4) / 2;  // node pairs of step 1
 constexpr int kT2R2 = kT2Y * kT2X / 2;               // node pairs of step 2
-constexpr int kT2Threads = 256;
 constexpr int kT2PopPlane = kT2PR * kT2W;             // floats
 constexpr int kT2FldPlane = kT2FR * kT2W;
 constexpr int kT2PopBytes = kQ * kT2PopPlane * 4;
@@ -45,11 +47,10 @@ constexpr int kT2TX = kT2PopBytes + kT2FldBytes;     // bytes per tile (boxes in
 constexpr int kT2Stage = (kT2TX + 127) / 128 * 128;
 static_assert(kT2PopBytes % 128 == 0, "the field box must start on a 128-byte boundary");
 static_assert(kT2W <= 256 && kT2PR <= 256, "TMA box dimensions are at most 256");
-static_assert(kT2R2 % kT2Threads == 0, "step 2 is whole passes of the block");
 
-template <int STAGES, int CTAS>
+template <int STAGES, int CTAS, int THREADS>
 struct Geom2 {
-    static constexpr int kStages = STAGES, kCtas = CTAS;
+    static constexpr int kStages = STAGES, kCtas = CTAS, kThreads = THREADS;
 };
 #ifndef TRTR_STEP2_STAGES
 #define TRTR_STEP2_STAGES 2
@@ -57,7 +58,10 @@ struct Geom2 {
 #ifndef TRTR_STEP2_CTAS
 #define TRTR_STEP2_CTAS 1
 #endif
-using Geom2Default = Geom2<TRTR_STEP2_STAGES, TRTR_STEP2_CTAS>;
+#ifndef TRTR_STEP2_THREADS
+#define TRTR_STEP2_THREADS 512
+#endif
+using Geom2Default = Geom2<TRTR_STEP2_STAGES, TRTR_STEP2_CTAS, TRTR_STEP2_THREADS>;
 
 struct alignas(16) Step2Args {
     StepArgs<float> a;  // tf: the pulse uniforms of the first step
@@ -94,9 +98,9 @@ __device__ __forceinline__ F2 pair_source(const StepArgs<float>& a, const TimeFi
 }
 
 template <int SRC, class G>
-__global__ void __launch_bounds__(kT2Threads, G::kCtas)
+__global__ void __launch_bounds__(G::kThreads, G::kCtas)
     step2_kernel(const __grid_constant__ CUtensorMap mp, const __grid_constant__ CUtensorMap mf, const Step2Args args) {
-    constexpr int STAGES = G::kStages;
+    constexpr int STAGES = G::kStages, kT2Threads = G::kThreads;
     const StepArgs<float>& a = args.a;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int s_abort;
@@ -181,9 +185,7 @@ __global__ void __launch_bounds__(kT2Threads, G::kCtas)
         __syncthreads();  // P1 complete (and s_abort visible)
         if (ok && !s_abort) {
             // step 2 on the output nodes
-#pragma unroll
-            for (int kk = 0; kk < kT2R2 / kT2Threads; ++kk) {
-                const int p = tid + kk * kT2Threads;
+            for (int p = tid; p < kT2R2; p += kT2Threads) {
                 const int r2 = p / (kT2X / 2), c2 = 2 * (p - r2 * (kT2X / 2));
                 const int i = i0 + c2, j = j0 + r2;
                 if (i >= nx || j >= ny) continue;
@@ -293,7 +295,7 @@ cudaError_t launch2_typed(trtr_ctx* ctx) {
     if (configured_device != ctx->device) {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas_per_sm, kernel, kT2Threads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas_per_sm, kernel, G::kThreads, smem);
         if (e != cudaSuccess) return e;
         if (ctas_per_sm < 1) return cudaErrorInvalidConfiguration;
         configured_device = ctx->device;
@@ -332,7 +334,7 @@ cudaError_t launch2_typed(trtr_ctx* ctx) {
     const long cap = (long)ctx->num_sms * ctas_per_sm;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(ntiles < cap ? ntiles : cap));
-    cfg.blockDim = dim3(kT2Threads);
+    cfg.blockDim = dim3(G::kThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = ctx->stream;
     cudaLaunchAttribute attr[1];

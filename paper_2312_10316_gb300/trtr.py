@@ -103,6 +103,7 @@ _SIGNATURES = {
     "trtr_bounds_report": (_st, [ctypes.POINTER(ctypes.c_ulonglong)]),
     "trtr_check_bounds_path": (_st, [_vp]),
     "trtr_set_steps_per_launch": (_st, [_vp, ctypes.c_int]),
+    "trtr_get_steps_per_launch": (_st, [_vp, ctypes.POINTER(ctypes.c_int)]),
 }
 
 
@@ -347,6 +348,12 @@ def trtr_set_steps_per_launch(ctx, k: int):
     _check(ctx, lib.trtr_set_steps_per_launch(ctx, int(k)))
 
 
+def trtr_get_steps_per_launch(ctx) -> int:
+    k = ctypes.c_int()
+    _check(ctx, lib.trtr_get_steps_per_launch(ctx, ctypes.byref(k)))
+    return int(k.value)
+
+
 def trtr_check_bounds_path(ctx) -> int:
     """Status of the bounds-check probe (TRTR_EBOUNDS in the checked build, TRTR_OK otherwise)."""
     return int(lib.trtr_check_bounds_path(ctx))
@@ -442,6 +449,10 @@ class Solver:
 
     def set_steps_per_launch(self, k: int):
         trtr_set_steps_per_launch(self.ctx, k)
+
+    @property
+    def steps_per_launch(self) -> int:
+        return trtr_get_steps_per_launch(self.ctx)
 
     def moments(self, out=None):
         if out is None:

@@ -81,6 +81,8 @@ def test_bounds_checked_build_exports_the_same_boundary(T):
     assert lib.trtr_bounds_checked() == 1
     assert lib.trtr_bounds_report(None) == T.TRTR_EINVAL
     assert lib.trtr_check_bounds_path(None) == T.TRTR_EINVAL
+    assert lib.trtr_set_steps_per_launch(None, 2) == T.TRTR_EINVAL
+    assert lib.trtr_get_steps_per_launch(None, None) == T.TRTR_EINVAL
 
 
 def test_library_and_oracle_share_the_lattice_convention(T):
