@@ -55,9 +55,10 @@ ADJOINT_WORKLOADS = {"adjoint512_f32": "f32"}
 # rotating pulse on [-2 pi, 2 pi]^2 with Dirichlet edges, through the library
 TABLE2_WORKLOADS = {"table2_f64": "f64", "table2_f32": "f32"}
 TABLE2_PRINTED = os.path.join(ROOT, "tests", "golden", "table2_convergence.txt")
-STEP_SOURCES = ["paper_2312_10316_gb300/csrc/trtr_step.cu", "paper_2312_10316_gb300/csrc/trtr_step2.cu",
-                "paper_2312_10316_gb300/csrc/trtr_step_core.cuh",
-                "paper_2312_10316_gb300/csrc/trtr_internal.cuh"]
+# the sources each timed kernel is compiled from (its counters are valid while they are unchanged)
+_CORE = ["paper_2312_10316_gb300/csrc/trtr_step_core.cuh", "paper_2312_10316_gb300/csrc/trtr_internal.cuh"]
+KERNEL_SOURCES = {"step_kernel": ["paper_2312_10316_gb300/csrc/trtr_step.cu"] + _CORE,
+                  "step2_kernel": ["paper_2312_10316_gb300/csrc/trtr_step2.cu"] + _CORE}
 
 
 def parse_args():
@@ -103,9 +104,9 @@ def measured_hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def step_kernel_sha() -> str:
+def kernel_sha(kernel: str) -> str:
     h = hashlib.sha256()
-    for rel in STEP_SOURCES:
+    for rel in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -121,7 +122,7 @@ def ncu_traffic(workload: str, kernel: str):
     except Exception:
         return None
     entry = d.get(workload)
-    if not entry or entry.get("kernel_sha") != step_kernel_sha() or entry.get("kernel", "step_kernel") != kernel:
+    if not entry or entry.get("kernel", "step_kernel") != kernel or entry.get("kernel_sha") != kernel_sha(kernel):
         return None
     return entry.get("dram_bytes_per_launch")
 

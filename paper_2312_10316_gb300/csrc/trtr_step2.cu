@@ -18,9 +18,9 @@
 //   Step 2 runs on the output nodes: node (r2, c2) = R1 node (r2 + 1, c2 + 2) pulls
 //   P1_q(x - e_q) from (row r2 + 2 - 2 ey_q, column c2 + 4 - 2 ex_q) and stores P2 to global
 //   memory with its ghost copies (nodes within two of an edge).
-// Block: 512 threads (16 warps, about 106 registers each) and two stages of 86 KB, one CTA per
-// SM; the kernel is latency-bound at this size (measured: 16 warps 82 GLUPS, 8 warps 77, 12
-// warps 75 at 4096^2), step 1 takes two passes of the block (660 node pairs), step 2 one (512).
+// Geometry (Geom2For): narrow tiles (32 columns; 8 rows with the pulse source, 16 without) and
+// several CTAs per SM with two stages each, so that while one CTA waits at the barrier between
+// its two steps the others compute (the kernel is latency-bound, not HBM-bound).
 // R1 nodes outside the grid are periodic images: their populations come from the ghost frame,
 // their fields from the packed fields' ghost frame (copies of the wrapped node, the acceleration
 // included, whatever the gradient mode), and their source from the wrapped node's coordinates,
@@ -32,36 +32,54 @@ namespace {
 
 using namespace core;
 
-constexpr int kT2X = 128, kT2Y = 8;                  // output tile
-constexpr int kT2W = kT2X + 8;                       // staged columns
-constexpr int kT2PR = kT2Y + 4;                      // staged population rows
-constexpr int kT2FR = kT2Y + 2;                      // staged field rows
-constexpr int kT2NF = 5;                             // uhat_x, uhat_y, a_x, a_y, Dh
-constexpr int kT2R1 = (kT2Y + 2) * (kT2X + 4) / 2;  // node pairs of step 1
-constexpr int kT2R2 = kT2Y * kT2X / 2;               // node pairs of step 2
-constexpr int kT2PopPlane = kT2PR * kT2W;             // floats
-constexpr int kT2FldPlane = kT2FR * kT2W;
-constexpr int kT2PopBytes = kQ * kT2PopPlane * 4;
-constexpr int kT2FldBytes = kT2NF * kT2FldPlane * 4;
-constexpr int kT2TX = kT2PopBytes + kT2FldBytes;     // bytes per tile (boxes include any fill)
-constexpr int kT2Stage = (kT2TX + 127) / 128 * 128;
-static_assert(kT2PopBytes % 128 == 0, "the field box must start on a 128-byte boundary");
-static_assert(kT2W <= 256 && kT2PR <= 256, "TMA box dimensions are at most 256");
+constexpr int kT2NF = 5;  // packed fields: uhat_x, uhat_y, a_x, a_y, Dh
 
-template <int STAGES, int CTAS, int THREADS>
+// Stage of one BX x BY output tile: the population box (9 planes) and the field box (5 planes).
+template <int BX, int BY>
+struct Tile2 {
+    static constexpr int X = BX, Y = BY;
+    static constexpr int W = BX + 8;                     // staged columns [i0 - 4, i0 + BX + 4)
+    static constexpr int PR = BY + 4;                    // staged population rows
+    static constexpr int FR = BY + 2;                    // staged field rows
+    static constexpr int R1 = (BY + 2) * (BX + 4) / 2;  // node pairs of step 1
+    static constexpr int R2 = BY * BX / 2;               // node pairs of step 2
+    static constexpr int PopPlane = PR * W;              // floats
+    static constexpr int FldPlane = FR * W;
+    static constexpr int PopBytes = kQ * PopPlane * 4;
+    static constexpr int FldBytes = kT2NF * FldPlane * 4;
+    static constexpr int TX = PopBytes + FldBytes;       // bytes per tile (boxes include any fill)
+    static constexpr int Stage = (TX + 127) / 128 * 128;
+    static_assert(BX % 4 == 0, "tile origins on 16-byte boundaries");
+    static_assert(PopBytes % 128 == 0, "the field box must start on a 128-byte boundary");
+    static_assert(W <= 256 && PR <= 256, "TMA box dimensions are at most 256");
+};
+
+template <int STAGES, int CTAS, int THREADS, int BX, int BY>
 struct Geom2 {
     static constexpr int kStages = STAGES, kCtas = CTAS, kThreads = THREADS;
+    using T = Tile2<BX, BY>;
+    static_assert(STAGES * T::Stage + 256 <= 227 * 1024, "the stages must fit in shared memory");
 };
-#ifndef TRTR_STEP2_STAGES
-#define TRTR_STEP2_STAGES 2
+// Geometry per source mode (stages, CTAs per SM, threads, tile width, tile height), from the
+// sweeps of rebuilds with -DTRTR_STEP2_STAGES=S -DTRTR_STEP2_CTAS=C -DTRTR_STEP2_THREADS=T
+// -DTRTR_STEP2_BX=X -DTRTR_STEP2_BY=Y (all five; they set it for both modes): a few
+// independent CTAs per SM hide each one's barrier between the two steps, the pulse source's
+// arithmetic favours more of them.
+template <int SRC>
+struct Geom2For {  // in-kernel pulse source
+    using type = Geom2<2, 3, 128, 32, 8>;
+};
+template <>
+struct Geom2For<TRTR_SRC_NONE> {
+    using type = Geom2<2, 2, 256, 32, 16>;
+};
+#ifdef TRTR_STEP2_BX
+template <int SRC>
+using Geom2Of = Geom2<TRTR_STEP2_STAGES, TRTR_STEP2_CTAS, TRTR_STEP2_THREADS, TRTR_STEP2_BX, TRTR_STEP2_BY>;
+#else
+template <int SRC>
+using Geom2Of = typename Geom2For<SRC>::type;
 #endif
-#ifndef TRTR_STEP2_CTAS
-#define TRTR_STEP2_CTAS 1
-#endif
-#ifndef TRTR_STEP2_THREADS
-#define TRTR_STEP2_THREADS 512
-#endif
-using Geom2Default = Geom2<TRTR_STEP2_STAGES, TRTR_STEP2_CTAS, TRTR_STEP2_THREADS>;
 
 struct alignas(16) Step2Args {
     StepArgs<float> a;  // tf: the pulse uniforms of the first step
@@ -101,6 +119,10 @@ template <int SRC, class G>
 __global__ void __launch_bounds__(G::kThreads, G::kCtas)
     step2_kernel(const __grid_constant__ CUtensorMap mp, const __grid_constant__ CUtensorMap mf, const Step2Args args) {
     constexpr int STAGES = G::kStages, kT2Threads = G::kThreads;
+    using T = typename G::T;
+    constexpr int kT2X = T::X, kT2Y = T::Y, kT2W = T::W, kT2R1 = T::R1, kT2R2 = T::R2;
+    constexpr int kT2PopPlane = T::PopPlane, kT2FldPlane = T::FldPlane, kT2PopBytes = T::PopBytes;
+    constexpr int kT2TX = T::TX, kT2Stage = T::Stage;
     const StepArgs<float>& a = args.a;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int s_abort;
@@ -289,7 +311,7 @@ __global__ void refresh_ghosts2_kernel(float* P, PlaneLayout L) {
 template <int SRC, class G>
 cudaError_t launch2_typed(trtr_ctx* ctx) {
     auto kernel = step2_kernel<SRC, G>;
-    const size_t smem = (size_t)G::kStages * kT2Stage + 128 + G::kStages * sizeof(uint64_t);
+    const size_t smem = (size_t)G::kStages * G::T::Stage + 128 + G::kStages * sizeof(uint64_t);
     static int configured_device = -1;
     static int ctas_per_sm = 1;
     if (configured_device != ctx->device) {
@@ -330,7 +352,7 @@ cudaError_t launch2_typed(trtr_ctx* ctx) {
         put(a.tf, t1, t0);
         put(args.tf2, t2, t1);
     }
-    const long ntiles = (long)((ctx->lp.nx + kT2X - 1) / kT2X) * ((ctx->lp.ny + kT2Y - 1) / kT2Y);
+    const long ntiles = (long)((ctx->lp.nx + G::T::X - 1) / G::T::X) * ((ctx->lp.ny + G::T::Y - 1) / G::T::Y);
     const long cap = (long)ctx->num_sms * ctas_per_sm;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(ntiles < cap ? ntiles : cap));
@@ -352,13 +374,20 @@ bool two_step_applies(const trtr_ctx* ctx) {
            (ctx->p.src_mode == TRTR_SRC_NONE || ctx->p.src_mode == TRTR_SRC_PULSE);
 }
 
-cudaError_t encode_maps2(trtr_ctx* ctx) {
-    if (!ctx->fld2) return cudaSuccess;
+template <class G>
+cudaError_t encode2_typed(trtr_ctx* ctx) {
+    using T = typename G::T;
     bool ok = true;
     for (int b = 0; b < 2; ++b)
-        ok = ok && encode(&ctx->maps2[b], tma_type<float>(), 4, ctx->pop[b], ctx->lp, kQ, kT2W, kT2PR, kQ);
-    ok = ok && encode(&ctx->maps2[2], tma_type<float>(), 4, ctx->fld2, ctx->lt, kT2NF, kT2W, kT2FR, kT2NF);
+        ok = ok && encode(&ctx->maps2[b], tma_type<float>(), 4, ctx->pop[b], ctx->lp, kQ, T::W, T::PR, kQ);
+    ok = ok && encode(&ctx->maps2[2], tma_type<float>(), 4, ctx->fld2, ctx->lt, kT2NF, T::W, T::FR, kT2NF);
     return ok ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t encode_maps2(trtr_ctx* ctx) {
+    if (!ctx->fld2) return cudaSuccess;
+    return ctx->p.src_mode == TRTR_SRC_PULSE ? encode2_typed<Geom2Of<TRTR_SRC_PULSE>>(ctx)
+                                             : encode2_typed<Geom2Of<TRTR_SRC_NONE>>(ctx);
 }
 
 cudaError_t launch_pack_fields2(trtr_ctx* ctx) {
@@ -381,8 +410,8 @@ cudaError_t launch_refresh_ghosts2(trtr_ctx* ctx) {
 }
 
 cudaError_t launch_step2(trtr_ctx* ctx) {
-    return ctx->p.src_mode == TRTR_SRC_PULSE ? launch2_typed<TRTR_SRC_PULSE, Geom2Default>(ctx)
-                                             : launch2_typed<TRTR_SRC_NONE, Geom2Default>(ctx);
+    return ctx->p.src_mode == TRTR_SRC_PULSE ? launch2_typed<TRTR_SRC_PULSE, Geom2Of<TRTR_SRC_PULSE>>(ctx)
+                                             : launch2_typed<TRTR_SRC_NONE, Geom2Of<TRTR_SRC_NONE>>(ctx);
 }
 
 TRTR_BOUNDS_TAKE(step2)

@@ -323,8 +323,8 @@ __device__ __forceinline__ void issue_tile(unsigned char* stage, uint64_t* bar, 
                                            int i0, int j0, const StepArgs<typename Store<S>::C>& a) {
     using T = Tile<S, SRC, BX, BY>;
     mbar_expect_tx(bar, T::TX);
-#pragma unroll
     constexpr int kPe = (int)sizeof(S), kFe = (int)sizeof(typename Store<S>::C);
+#pragma unroll
     for (int q = 0; q < kQ; ++q) {
         const int x = i0 + a.lp.gx - (lattice_ex(q) == 1 ? T::A : 0);
         const int y = j0 + kGhostP - lattice_ey(q);
