@@ -272,8 +272,8 @@ trtr_status trtr_batch_destroy(trtr_batch* b);
 int trtr_batch_config_count(void);
 const char* trtr_batch_config_name(int config);
 
-/* Autotuner: times every configuration over trial_steps (>= 2) steps with CUDA events and
- * keeps the fastest; *config_out (may be NULL) receives it and ms_out (may be NULL, else
+/* Autotuner: times every configuration (of the one-step kernel, one step per launch) over
+ * trial_steps (>= 2) steps with CUDA events and keeps the fastest; *config_out (may be NULL) receives it and ms_out (may be NULL, else
  * trtr_batch_config_count() floats) the milliseconds per step of each.  A batch tuned at
  * step 0 is reset to its initial condition afterwards; otherwise the trial steps advance
  * every instance.  Synchronises. */
@@ -282,9 +282,17 @@ trtr_status trtr_batch_tune(trtr_batch* b, int trial_steps, int* config_out, flo
 /* Selects a configuration explicitly. */
 trtr_status trtr_batch_set_config(trtr_batch* b, int config);
 
-/* Advances every instance by n >= 0 steps (asynchronous on the batch's stream).  Instances
- * must not be stepped through their own contexts in between (TRTR_ESTATE). */
+/* Advances every instance by n >= 0 steps (asynchronous on the batch's stream).  With FP32
+ * instances, pairs of steps run as launches of the two-step kernel over a work-list of its
+ * tiles (the same results bit for bit; see trtr_batch_set_steps_per_launch), the other steps
+ * with the configured one-step kernel.  Instances must not be stepped through their own
+ * contexts in between (TRTR_ESTATE). */
 trtr_status trtr_batch_step(trtr_batch* b, long n);
+
+/* k = 2 (the default): trtr_batch_step runs pairs of steps with the two-step kernel where it
+ * applies (FP32 instances); k = 1: every step with the configured one-step kernel.
+ * TRTR_EINVAL for other k. */
+trtr_status trtr_batch_set_steps_per_launch(trtr_batch* b, int k);
 
 /* Waits for the batch's stream; TRTR_ETIMEOUT if a step kernel gave up a bounded wait
  * (TRTR_EBOUNDS in the bounds-checked build if a kernel access out of bounds was caught). */

@@ -22,7 +22,7 @@
 #include <new>
 #include <vector>
 
-#include "trtr_step_core.cuh"
+#include "trtr_step2_core.cuh"
 
 namespace trtr {
 namespace {
@@ -44,7 +44,20 @@ struct alignas(64) InstanceDesc {
     Pulse pulse;
     double dt;
 };
+// Two-step launches (FP32): the two-step kernel's maps and arguments per instance.
+struct alignas(64) InstanceDesc2 {
+    CUtensorMap mp[2];        // populations, source buffer 0 / 1, the two-step tile's box
+    CUtensorMap mf;           // packed fields
+    StepArgs<float> base[2];  // by source-buffer parity; time part unused
+    Pulse pulse;
+    double dt;
+};
+// Pulse uniforms of a two-step launch from step n: steps n and n + 1.
+struct alignas(16) TimeFields2 {
+    TimeFields<float> t1, t2;
+};
 static_assert(sizeof(StepArgs<float>) % 16 == 0 && sizeof(TimeFields<float>) % 16 == 0, "16-byte chunks");
+static_assert(offsetof(InstanceDesc2, base) % 16 == 0, "16-byte aligned arguments");
 static_assert(offsetof(InstanceDesc<float>, base) % 16 == 0, "16-byte aligned arguments");
 
 struct Geometry {
@@ -94,7 +107,8 @@ constexpr int min_blocks() {
 template <typename S, int SRC, int BX, int BY, int STAGES>
 __global__ void __launch_bounds__(32 * BY, min_blocks<BY>())
     batch_kernel(const InstanceDesc<typename Store<S>::C>* __restrict__ desc, const int4* __restrict__ tiles,
-                 int ntiles, TimeFields<float>* tu, BatchClock* clk, int count, int parity, int interleaved) {
+                 int ntiles, TimeFields<float>* tu, TimeFields2* tu2, BatchClock* clk, int count, int parity,
+                 int interleaved) {
     using C = typename Store<S>::C;
     using T = Tile<S, SRC, BX, BY>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -206,10 +220,105 @@ __global__ void __launch_bounds__(32 * BY, min_blocks<BY>())
         __threadfence();
         const long long n1 = clk->n + 1;
         if (SRC == TRTR_SRC_PULSE)
-            for (int k = tid; k < count; k += blockDim.x) tu[k] = time_fields(desc[k].pulse, desc[k].dt, n1);
+            for (int k = tid; k < count; k += blockDim.x) {
+                tu[k] = time_fields(desc[k].pulse, desc[k].dt, n1);
+                if (tu2) tu2[k] = TimeFields2{tu[k], time_fields(desc[k].pulse, desc[k].dt, n1 + 1)};
+            }
         __syncthreads();
         if (tid == 0) {
             clk->n = n1;
+            clk->done = 0;
+            __threadfence();
+        }
+    }
+}
+
+// Two time steps per launch over the work-list of two-step tiles (FP32): per tile the producer
+// issues the instance's two TMA boxes and copies its arguments and the time uniforms of both
+// steps into the stage's slot (the barrier's second arrival), then the block runs the two-step
+// kernel's two steps on the staged tile.  The last CTA advances the clock by two steps and both
+// time tables.
+template <int SRC, class G>
+__global__ void __launch_bounds__(G::kThreads, G::kCtas)
+    batch2_kernel(const InstanceDesc2* __restrict__ desc, const int4* __restrict__ tiles, int ntiles,
+                  TimeFields<float>* tu, TimeFields2* tu2, BatchClock* clk, int count, int parity) {
+    constexpr int STAGES = G::kStages, NT = G::kThreads;
+    using T = typename G::T;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(16) StepArgs<float> sargs[STAGES];
+    __shared__ __align__(16) TimeFields<float> stf2[STAGES];
+    __shared__ int s_abort, s_last;
+    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) &
+                                                           ~static_cast<uintptr_t>(127));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * T::Stage);
+    const int tid = threadIdx.x;
+    const int first = blockIdx.x, stride = gridDim.x;
+    const int my_tiles = first < ntiles ? (ntiles - 1 - first) / stride + 1 : 0;
+
+    auto issue = [&](int k, int s) {
+        const int4 t = tiles[first + k * stride];  // (instance, i0, j0, gx_p)
+        const InstanceDesc2* d = desc + t.x;
+        uint64_t* bar = &full[s];
+        mbar_expect_tx(bar, T::TX);
+        step2_issue<T>(smem + s * T::Stage, bar, &d->mp[parity], &d->mf, t.y, t.z, t.w);
+        constexpr int kStatic = (int)(sizeof(StepArgs<float>) - sizeof(TimeFields<float>));
+        cp_async_16(&sargs[s], &d->base[parity], kStatic);
+        if (SRC == TRTR_SRC_PULSE) {
+            cp_async_16(&sargs[s].tf, &tu2[t.x].t1, (int)sizeof(TimeFields<float>));
+            cp_async_16(&stf2[s], &tu2[t.x].t2, (int)sizeof(TimeFields<float>));
+        }
+        asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+    };
+
+    if (tid == 0) {
+        s_abort = 0;
+        for (int s = 0; s < STAGES; ++s) mbar_init(&full[s], 2);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int k = 0; k < STAGES && k < my_tiles; ++k) issue(k, k);
+
+    int4 t_next = my_tiles > 0 ? tiles[first] : make_int4(0, 0, 0, 0);
+    for (int k = 0; k < my_tiles; ++k) {
+        const int s = k % STAGES;
+        const int4 t = t_next;
+        if (k + 1 < my_tiles) t_next = tiles[first + (k + 1) * stride];
+        const bool ok = mbar_wait_bounded(&full[s], (k / STAGES) & 1);
+        if (!ok) s_abort = 1;
+        float* sp = reinterpret_cast<float*>(smem + s * T::Stage);
+        const float* sf = reinterpret_cast<const float*>(smem + s * T::Stage + T::PopBytes);
+        if (ok) step2_first<SRC, T, NT>(sp, sf, t.y, t.z, sargs[s], sargs[s].tf, tid);
+        __syncthreads();  // step 1 complete (and s_abort visible)
+        if (ok && !s_abort) step2_second<SRC, T, NT>(sp, sf, t.y, t.z, sargs[s], stf2[s], tid);
+        __syncthreads();  // stage s and its argument slot fully read
+        if (s_abort) {
+            if (tid == 0) {
+                atomicExch(desc[t.x].base[0].flag, 1);
+                for (int kk = k + 1; kk < my_tiles && kk < k + STAGES; ++kk)
+                    mbar_wait_bounded(&full[kk % STAGES], (kk / STAGES) & 1);
+            }
+            return;
+        }
+        if (tid == 0 && k + STAGES < my_tiles) issue(k + STAGES, s);
+    }
+
+    if (tid == 0) {
+        __threadfence();
+        s_last = atomicAdd(&clk->done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        const long long n2 = clk->n + 2;
+        if (SRC == TRTR_SRC_PULSE)
+            for (int k = tid; k < count; k += blockDim.x) {
+                tu[k] = time_fields(desc[k].pulse, desc[k].dt, n2);
+                tu2[k] = TimeFields2{tu[k], time_fields(desc[k].pulse, desc[k].dt, n2 + 1)};
+            }
+        __syncthreads();
+        if (tid == 0) {
+            clk->n = n2;
             clk->done = 0;
             __threadfence();
         }
@@ -220,6 +329,7 @@ __global__ void __launch_bounds__(32 * BY, min_blocks<BY>())
 }  // namespace trtr
 
 using trtr::BatchClock;
+using trtr::TimeFields2;
 using TimeUniforms = trtr::TimeFields<float>;
 
 struct trtr_batch {
@@ -233,6 +343,17 @@ struct trtr_batch {
     int4* d_tiles;
     int ntiles;
     TimeUniforms* d_tu;  // per-instance pulse uniforms of the current step
+    // two steps per launch (FP32 instances): descriptors, work-list and time table of the
+    // two-step kernel, its graph, and whether pairs of steps use it
+    void* d_desc2;
+    int4* d_tiles2;
+    int ntiles2;
+    TimeFields2* d_tu2;
+    int grid2;
+    bool two_step;
+    int steps_per_launch;
+    cudaGraphExec_t graph2;
+    bool graph2_valid;
     BatchClock* d_clk;
     int* d_flag;
     int* h_flag;
@@ -277,7 +398,8 @@ struct BatchLaunch {
     static cudaError_t launch(trtr_batch* b, int parity, int interleaved) {
         auto kernel = batch_kernel<S, SRC, BX, BY, kStages>;
         kernel<<<b->grid, 32 * BY, smem(), b->stream>>>(static_cast<const InstanceDesc<C>*>(b->d_desc), b->d_tiles,
-                                                         b->ntiles, b->d_tu, b->d_clk, b->count, parity, interleaved);
+                                                         b->ntiles, b->d_tu, b->d_tu2, b->d_clk, b->count, parity,
+                                                         interleaved);
         return cudaGetLastError();
     }
     static bool encode_desc(trtr_batch* b, InstanceDesc<C>* h) {
@@ -365,6 +487,95 @@ cudaError_t dispatch(trtr_batch* b, int geom, int what, int parity = 0, int inte
     }
 }
 
+// The two-step kernel over the batch (FP32 instances; geometry of the batch's source mode).
+template <int SRC>
+struct Batch2Launch {
+    using G = Geom2Of<SRC>;
+    using T = typename G::T;
+    static size_t smem() { return (size_t)G::kStages * T::Stage + 128 + G::kStages * sizeof(uint64_t); }
+    static cudaError_t configure(trtr_batch* b) {
+        auto kernel = batch2_kernel<SRC, G>;
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem());
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, G::kThreads, smem());
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        b->grid2 = b->ctx[0]->num_sms * per_sm;
+        return cudaSuccess;
+    }
+    static cudaError_t launch(trtr_batch* b, int parity) {
+        batch2_kernel<SRC, G><<<b->grid2, G::kThreads, smem(), b->stream>>>(
+            static_cast<const InstanceDesc2*>(b->d_desc2), b->d_tiles2, b->ntiles2, b->d_tu, b->d_tu2, b->d_clk,
+            b->count, parity);
+        return cudaGetLastError();
+    }
+    static bool encode_desc(trtr_batch* b, InstanceDesc2* h) {
+        for (int k = 0; k < b->count; ++k) {
+            const trtr_ctx* c = b->ctx[k];
+            InstanceDesc2& d = h[k];
+            bool ok = true;
+            for (int p = 0; p < 2; ++p)
+                ok = ok && encode(&d.mp[p], tma_type<float>(), 4, c->pop[p], c->lp, kQ, T::W, T::PR, kQ);
+            ok = ok && encode(&d.mf, tma_type<float>(), 4, c->fld2, c->lt, kT2NF, T::W, T::FR, kT2NF);
+            if (!ok) return false;
+            StepArgs<float>& a = d.base[0];
+            memset(static_cast<void*>(&a), 0, sizeof(a));
+            a.tab_x = static_cast<const float*>(c->tab_x);
+            a.tab_y = static_cast<const float*>(c->tab_y);
+            a.flag = b->d_flag;
+            a.lp = c->lp;
+            a.lf = c->lt;
+            a.tau2_fixed = c->p.tau2_mode == TRTR_TAU2_FIXED;
+            a.magic = (float)c->p.magic;
+            a.omega2_fixed = (float)(c->p.tau2_mode == TRTR_TAU2_FIXED ? 1.0 / c->p.tau2 : 0.0);
+            a.phi_ref = (float)c->p.phi_ref;
+            a.x0 = (float)c->p.x0;
+            a.y0 = (float)c->p.y0;
+            a.dx = (float)c->p.dx;
+            a.dt = (float)c->p.dt;
+            a.dD_amp = (float)(c->pulse.D0 * c->pulse.D_amp);
+            d.base[1] = a;
+            d.base[0].dst = c->pop[1];
+            d.base[1].dst = c->pop[0];
+            d.pulse = c->pulse;
+            d.dt = c->p.dt;
+        }
+        return true;
+    }
+    // descriptors and the work-list of two-step tiles (interleaved over the CTAs)
+    static trtr_status setup(trtr_batch* b) {
+        if (configure(b) != cudaSuccess) return TRTR_ECUDA;
+        std::vector<InstanceDesc2> h(b->count);
+        if (!encode_desc(b, h.data())) return TRTR_ECUDA;
+        std::vector<int4> t;
+        for (int k = 0; k < b->count; ++k) {
+            const int nx = b->ctx[k]->p.nx, ny = b->ctx[k]->p.ny;
+            for (int j0 = 0; j0 < ny; j0 += T::Y)
+                for (int i0 = 0; i0 < nx; i0 += T::X) t.push_back(make_int4(k, i0, j0, b->ctx[k]->lp.gx));
+        }
+        if (cudaMalloc(&b->d_tiles2, t.size() * sizeof(int4)) != cudaSuccess) return TRTR_ENOMEM;
+        if (cudaMemcpyAsync(b->d_desc2, h.data(), sizeof(InstanceDesc2) * b->count, cudaMemcpyHostToDevice,
+                            b->stream) != cudaSuccess ||
+            cudaMemcpyAsync(b->d_tiles2, t.data(), t.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(b->stream) != cudaSuccess)
+            return TRTR_ECUDA;
+        b->ntiles2 = (int)t.size();
+        if (b->grid2 > b->ntiles2) b->grid2 = b->ntiles2;
+        return TRTR_OK;
+    }
+};
+
+cudaError_t launch_two(trtr_batch* b, int parity) {
+    return b->src == TRTR_SRC_PULSE ? Batch2Launch<TRTR_SRC_PULSE>::launch(b, parity)
+                                    : Batch2Launch<TRTR_SRC_NONE>::launch(b, parity);
+}
+
+trtr_status setup_two_step(trtr_batch* b) {
+    return b->src == TRTR_SRC_PULSE ? Batch2Launch<TRTR_SRC_PULSE>::setup(b) : Batch2Launch<TRTR_SRC_NONE>::setup(b);
+}
+
 size_t desc_size(int precision) {
     return precision == TRTR_F64 ? sizeof(InstanceDesc<double>) : sizeof(InstanceDesc<float>);
 }
@@ -437,7 +648,14 @@ trtr_status build_graph(trtr_batch* b) {
 
 trtr_status reset_clock(trtr_batch* b) {
     std::vector<TimeUniforms> u(b->count);
-    for (int k = 0; k < b->count; ++k) u[k] = time_fields(b->pulses[k], b->ctx[k]->p.dt, b->step);
+    std::vector<TimeFields2> u2(b->count);
+    for (int k = 0; k < b->count; ++k) {
+        u[k] = time_fields(b->pulses[k], b->ctx[k]->p.dt, b->step);
+        u2[k] = TimeFields2{u[k], time_fields(b->pulses[k], b->ctx[k]->p.dt, b->step + 1)};
+    }
+    if (b->d_tu2 && cudaMemcpyAsync(b->d_tu2, u2.data(), u2.size() * sizeof(TimeFields2), cudaMemcpyHostToDevice,
+                                    b->stream) != cudaSuccess)
+        return TRTR_ECUDA;
     BatchClock c;
     c.n = b->step;
     c.done = 0;
@@ -450,12 +668,66 @@ trtr_status reset_clock(trtr_batch* b) {
     return TRTR_OK;
 }
 
-trtr_status advance(trtr_batch* b, long n) {
+// Two-launch graph of the two-step kernel: parity 0 then parity 1 (four steps).
+trtr_status build_graph2(trtr_batch* b) {
+    if (b->graph2_valid) return TRTR_OK;
+    cudaGraph_t g;
+    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return TRTR_ECUDA;
+    cudaError_t e0 = launch_two(b, 0);
+    cudaError_t e1 = launch_two(b, 1);
+    cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    if (e0 != cudaSuccess || e1 != cudaSuccess || e != cudaSuccess) {
+        cudaGetLastError();
+        return TRTR_ECUDA;
+    }
+    e = cudaGraphInstantiate(&b->graph2, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return TRTR_ECUDA;
+    b->graph2_valid = true;
+    return TRTR_OK;
+}
+
+// n steps: pairs through the two-step kernel where it applies (steps_per_launch 2), the rest
+// (an odd step, or all with steps_per_launch 1) through the one-step kernel of the configured
+// geometry.  Both kernels advance the device clock and both time tables, so they interleave.
+trtr_status advance(trtr_batch* b, long n, int steps_per_launch) {
     for (int k = 0; k < b->count; ++k)
         if (b->ctx[k]->step != b->step || b->ctx[k]->cur != b->parity) return TRTR_ESTATE;
     long left = n;
-    if (left > 0 && b->parity == 1) {  // bring the ping-pong to parity 0 for the graph
+    int par = b->parity;
+    bool last_two = false;
+    if (b->two_step && steps_per_launch == 2 && left >= 2) {
+        for (int k = 0; k < b->count; ++k) {
+            trtr_ctx* c = b->ctx[k];  // instances share the batch's stream
+            if (!c->fld2_ready) {
+                if (launch_pack_fields2(c) != cudaSuccess) return TRTR_ECUDA;
+                c->fld2_ready = true;
+            }
+            if (!c->ghost2_ready && launch_refresh_ghosts2(c) != cudaSuccess) return TRTR_ECUDA;
+        }
+        long pairs = left / 2;
+        left -= 2 * pairs;
+        if (par == 1) {
+            if (launch_two(b, 1) != cudaSuccess) return TRTR_ECUDA;
+            par = 0;
+            --pairs;
+        }
+        if (pairs >= 2) {
+            trtr_status s = build_graph2(b);
+            if (s != TRTR_OK) return s;
+            for (; pairs >= 2; pairs -= 2)
+                if (cudaGraphLaunch(b->graph2, b->stream) != cudaSuccess) return TRTR_ECUDA;
+        }
+        if (pairs == 1) {
+            if (launch_two(b, 0) != cudaSuccess) return TRTR_ECUDA;
+            par = 1;
+        }
+        last_two = true;
+    }
+    if (left > 0) last_two = false;  // one-step launches follow: the one-wide ghost frame
+    if (left > 0 && par == 1) {  // bring the ping-pong to parity 0 for the graph
         if (launch_one(b, 1) != cudaSuccess) return TRTR_ECUDA;
+        par = 0;
         --left;
     }
     if (left >= 2) {
@@ -464,13 +736,16 @@ trtr_status advance(trtr_batch* b, long n) {
         for (; left >= 2; left -= 2)
             if (cudaGraphLaunch(b->graph, b->stream) != cudaSuccess) return TRTR_ECUDA;
     }
-    if (left == 1 && launch_one(b, 0) != cudaSuccess) return TRTR_ECUDA;
+    if (left == 1) {
+        if (launch_one(b, 0) != cudaSuccess) return TRTR_ECUDA;
+        par = 1;
+    }
     b->step += n;
-    b->parity = (int)((b->parity + n) & 1);
+    b->parity = par;
     for (int k = 0; k < b->count; ++k) {
         b->ctx[k]->step = b->step;
         b->ctx[k]->cur = b->parity;
-        b->ctx[k]->ghost2_ready = false;
+        if (n > 0) b->ctx[k]->ghost2_ready = last_two;
         b->ctx[k]->launches += n;
     }
     return TRTR_OK;
@@ -537,6 +812,17 @@ trtr_status trtr_batch_create(const trtr_instance* inst, int count, void* cuda_s
         s = TRTR_ENOMEM;
     }
     if (s == TRTR_OK) s = trtr::apply_config(b, b->config);
+    // two steps per launch where every instance has the two-step kernel's packed fields
+    b->steps_per_launch = 2;
+    b->two_step = s == TRTR_OK && prec == TRTR_F32;
+    for (int k = 0; k < count && b->two_step; ++k) b->two_step = b->ctx[k]->fld2 != nullptr;
+    if (s == TRTR_OK && b->two_step &&
+        (cudaMalloc(&b->d_desc2, sizeof(trtr::InstanceDesc2) * count) != cudaSuccess ||
+         cudaMalloc(&b->d_tu2, sizeof(TimeFields2) * count) != cudaSuccess)) {
+        cudaGetLastError();
+        s = TRTR_ENOMEM;
+    }
+    if (s == TRTR_OK && b->two_step) s = trtr::setup_two_step(b);
     if (s == TRTR_OK) s = trtr::reset_clock(b);
     if (s != TRTR_OK) {
         trtr_batch_destroy(b);
@@ -550,9 +836,10 @@ trtr_status trtr_batch_destroy(trtr_batch* b) {
     if (!b) return TRTR_OK;
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->graph_valid) cudaGraphExecDestroy(b->graph);
+    if (b->graph2_valid) cudaGraphExecDestroy(b->graph2);
     for (int k = 0; k < b->count; ++k)
         if (b->ctx && b->ctx[k]) trtr_destroy(b->ctx[k]);
-    void* ptrs[] = {b->d_desc, b->d_tiles, b->d_tu, b->d_clk, b->d_flag};
+    void* ptrs[] = {b->d_desc, b->d_tiles, b->d_tu, b->d_clk, b->d_flag, b->d_desc2, b->d_tiles2, b->d_tu2};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (b->h_flag) cudaFreeHost(b->h_flag);
@@ -580,9 +867,15 @@ trtr_status trtr_batch_set_config(trtr_batch* b, int config) {
     return trtr::apply_config(b, config);
 }
 
+trtr_status trtr_batch_set_steps_per_launch(trtr_batch* b, int k) {
+    if (!b || (k != 1 && k != 2)) return TRTR_EINVAL;
+    b->steps_per_launch = k;
+    return TRTR_OK;
+}
+
 trtr_status trtr_batch_step(trtr_batch* b, long n) {
     if (!b || n < 0) return TRTR_EINVAL;
-    return trtr::advance(b, n);
+    return trtr::advance(b, n, b->steps_per_launch);
 }
 
 trtr_status trtr_batch_sync(trtr_batch* b) {
@@ -622,10 +915,10 @@ trtr_status trtr_batch_tune(trtr_batch* b, int trial_steps, int* config_out, flo
     for (int c = 0; c < trtr::kNumConfigs && s == TRTR_OK; ++c) {
         s = trtr::apply_config(b, c);
         if (s != TRTR_OK) break;
-        s = trtr::advance(b, 2);  // warm-up (graph capture, caches)
+        s = trtr::advance(b, 2, 1);  // warm-up (graph capture, caches); the one-step configs
         if (s != TRTR_OK) break;
         cudaEventRecord(e0, b->stream);
-        s = trtr::advance(b, trial_steps - trial_steps % 2);
+        s = trtr::advance(b, trial_steps - trial_steps % 2, 1);
         cudaEventRecord(e1, b->stream);
         if (s != TRTR_OK) break;
         if (cudaEventSynchronize(e1) != cudaSuccess) {

@@ -25,126 +25,36 @@
 // their fields from the packed fields' ghost frame (copies of the wrapped node, the acceleration
 // included, whatever the gradient mode), and their source from the wrapped node's coordinates,
 // so they compute exactly what the wrapped node computes.
-#include "trtr_step_core.cuh"
+#include "trtr_step2_core.cuh"
 
 namespace trtr {
 namespace {
 
 using namespace core;
 
-constexpr int kT2NF = 5;  // packed fields: uhat_x, uhat_y, a_x, a_y, Dh
-
-// Stage of one BX x BY output tile: the population box (9 planes) and the field box (5 planes).
-template <int BX, int BY>
-struct Tile2 {
-    static constexpr int X = BX, Y = BY;
-    static constexpr int W = BX + 8;                     // staged columns [i0 - 4, i0 + BX + 4)
-    static constexpr int PR = BY + 4;                    // staged population rows
-    static constexpr int FR = BY + 2;                    // staged field rows
-    static constexpr int R1 = (BY + 2) * (BX + 4) / 2;  // node pairs of step 1
-    static constexpr int R2 = BY * BX / 2;               // node pairs of step 2
-    static constexpr int PopPlane = PR * W;              // floats
-    static constexpr int FldPlane = FR * W;
-    static constexpr int PopBytes = kQ * PopPlane * 4;
-    static constexpr int FldBytes = kT2NF * FldPlane * 4;
-    static constexpr int TX = PopBytes + FldBytes;       // bytes per tile (boxes include any fill)
-    static constexpr int Stage = (TX + 127) / 128 * 128;
-    static_assert(BX % 4 == 0, "tile origins on 16-byte boundaries");
-    static_assert(PopBytes % 128 == 0, "the field box must start on a 128-byte boundary");
-    static_assert(W <= 256 && PR <= 256, "TMA box dimensions are at most 256");
-};
-
-template <int STAGES, int CTAS, int THREADS, int BX, int BY>
-struct Geom2 {
-    static constexpr int kStages = STAGES, kCtas = CTAS, kThreads = THREADS;
-    using T = Tile2<BX, BY>;
-    static_assert(STAGES * T::Stage + 256 <= 227 * 1024, "the stages must fit in shared memory");
-};
-// Geometry per source mode (stages, CTAs per SM, threads, tile width, tile height), from the
-// sweeps of rebuilds with -DTRTR_STEP2_STAGES=S -DTRTR_STEP2_CTAS=C -DTRTR_STEP2_THREADS=T
-// -DTRTR_STEP2_BX=X -DTRTR_STEP2_BY=Y (all five; they set it for both modes): a few
-// independent CTAs per SM hide each one's barrier between the two steps, the pulse source's
-// arithmetic favours more of them.
-template <int SRC>
-struct Geom2For {  // in-kernel pulse source
-    using type = Geom2<2, 3, 128, 32, 8>;
-};
-template <>
-struct Geom2For<TRTR_SRC_NONE> {
-    using type = Geom2<2, 2, 256, 32, 16>;
-};
-#ifdef TRTR_STEP2_BX
-template <int SRC>
-using Geom2Of = Geom2<TRTR_STEP2_STAGES, TRTR_STEP2_CTAS, TRTR_STEP2_THREADS, TRTR_STEP2_BX, TRTR_STEP2_BY>;
-#else
-template <int SRC>
-using Geom2Of = typename Geom2For<SRC>::type;
-#endif
-
-struct alignas(16) Step2Args {
-    StepArgs<float> a;  // tf: the pulse uniforms of the first step
-    TimeFields<float> tf2;  // of the second step
-};
-
-// Wrapped index of a node of the halo region (v in [-2, n + 1] with n >= 2 maps onto its
-// periodic image); indices of the unused nodes past that are clamped into the tables.
-__device__ __forceinline__ int wrap_clamp(int v, int n) {
-    v = v < 0 ? v + n : (v >= n ? v - n : v);
-    return v < 0 ? 0 : (v >= n ? n - 1 : v);
-}
-
-// Source term s = dt S^n + dt/2 (S^n - S^{n-1}) of the pair (xi0, xi1) in row yj: the one-step
-// kernel's expressions, node coordinates from the wrapped indices.
-template <int SRC>
-__device__ __forceinline__ F2 pair_source(const StepArgs<float>& a, const TimeFields<float>& tf, int xi0, int xi1,
-                                          int yj) {
-    if (SRC != TRTR_SRC_PULSE) return F2(0.f);
-    const int nx = a.lp.nx, ny = a.lp.ny;
-    const float* tx = reinterpret_cast<const float*>(a.tab_x);
-    const float* ty = reinterpret_cast<const float*>(a.tab_y);
-    const F2 sxm(__ldg(tx + xi0), __ldg(tx + xi1));
-    const F2 cxm(__ldg(tx + nx + xi0), __ldg(tx + nx + xi1));
-    const float sy = __ldg(ty + yj), cy = __ldg(ty + ny + yj);
-    const F2 x = vfma(F2((float)xi0, (float)xi1), F2(a.dx), F2(a.x0));
-    const F2 y(a.y0 + (float)yj * a.dx);
-    const F2 dD = F2(a.dD_amp * sy) * sxm;
-    const F2 dDx = F2(a.dD_amp * 3.14159265358979323846f * sy) * cxm;
-    const F2 dDy = F2(a.dD_amp * 3.14159265358979323846f * cy) * sxm;
-    const F2 Sn = pulse_source(x, y, F2(tf.cx_n), F2(tf.cy_n), F2(tf.inv_s2_n), F2(tf.amp_n), dD, dDx, dDy);
-    const F2 Sp = pulse_source(x, y, F2(tf.cx_p), F2(tf.cy_p), F2(tf.inv_s2_p), F2(tf.amp_p), dD, dDx, dDy);
-    return F2(a.dt) * vfma(F2(1.5f), Sn, F2(-0.5f) * Sp);
-}
-
 template <int SRC, class G>
 __global__ void __launch_bounds__(G::kThreads, G::kCtas)
     step2_kernel(const __grid_constant__ CUtensorMap mp, const __grid_constant__ CUtensorMap mf, const Step2Args args) {
-    constexpr int STAGES = G::kStages, kT2Threads = G::kThreads;
+    constexpr int STAGES = G::kStages, NT = G::kThreads;
     using T = typename G::T;
-    constexpr int kT2X = T::X, kT2Y = T::Y, kT2W = T::W, kT2R1 = T::R1, kT2R2 = T::R2;
-    constexpr int kT2PopPlane = T::PopPlane, kT2FldPlane = T::FldPlane, kT2PopBytes = T::PopBytes;
-    constexpr int kT2TX = T::TX, kT2Stage = T::Stage;
     const StepArgs<float>& a = args.a;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int s_abort;
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) &
                                                            ~static_cast<uintptr_t>(127));
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * kT2Stage);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * T::Stage);
 
     const int tid = threadIdx.x;
     const int nx = a.lp.nx, ny = a.lp.ny;
-    const int ntx = (nx + kT2X - 1) / kT2X, nty = (ny + kT2Y - 1) / kT2Y;
+    const int ntx = (nx + T::X - 1) / T::X, nty = (ny + T::Y - 1) / T::Y;
     const int ntiles = ntx * nty;
     const int first = blockIdx.x, stride = gridDim.x;
     const int my_tiles = first < ntiles ? (ntiles - 1 - first) / stride + 1 : 0;
-    auto tile_x0 = [&](int k) { return ((first + k * stride) % ntx) * kT2X; };
-    auto tile_y0 = [&](int k) { return ((first + k * stride) / ntx) * kT2Y; };
+    auto tile_x0 = [&](int k) { return ((first + k * stride) % ntx) * T::X; };
+    auto tile_y0 = [&](int k) { return ((first + k * stride) / ntx) * T::Y; };
     auto issue = [&](int k, int s) {
-        unsigned char* stage = smem + s * kT2Stage;
-        const int x = tile_x0(k) + a.lp.gx - 4, y0 = tile_y0(k);
-        mbar_expect_tx(&full[s], kT2TX);
-        if (tma_ok(stage, x, y0 + kGhostP - 2, 4)) tma_load_3d(stage, &mp, &full[s], x, y0 + kGhostP - 2, 0);
-        if (tma_ok(stage + kT2PopBytes, x, y0 + kGhostP - 1, 4))
-            tma_load_3d(stage + kT2PopBytes, &mf, &full[s], x, y0 + kGhostP - 1, 0);
+        mbar_expect_tx(&full[s], T::TX);
+        step2_issue<T>(smem + s * T::Stage, &full[s], &mp, &mf, tile_x0(k), tile_y0(k), a.lp.gx);
     };
 
     if (tid == 0) {
@@ -158,94 +68,16 @@ __global__ void __launch_bounds__(G::kThreads, G::kCtas)
     if (tid == 0)
         for (int k = 0; k < STAGES && k < my_tiles; ++k) issue(k, k);
 
-    float* dst = static_cast<float*>(a.dst);
-    const size_t pl = a.lp.plane;
-    const F2 magic(a.magic), w2f(a.omega2_fixed);
-
     for (int k = 0; k < my_tiles; ++k) {
         const int s = k % STAGES;
         const int i0 = tile_x0(k), j0 = tile_y0(k);
         const bool ok = mbar_wait_bounded(&full[s], (k / STAGES) & 1);
         if (!ok) s_abort = 1;
-        float* sp = reinterpret_cast<float*>(smem + s * kT2Stage);
-        const float* sf = reinterpret_cast<const float*>(smem + s * kT2Stage + kT2PopBytes);
-        if (ok) {
-            // step 1 over the halo region, in place
-            for (int p = tid; p < kT2R1; p += kT2Threads) {
-                const int r = p / ((kT2X + 4) / 2), c = 2 * (p - r * ((kT2X + 4) / 2));
-                F2 g[kQ];
-#pragma unroll
-                for (int q = 0; q < kQ; ++q) {
-                    const float* src = sp + q * kT2PopPlane + (r + 1 - lattice_ey(q)) * kT2W + c + 2 - lattice_ex(q);
-                    if (lattice_ex(q) == 0)
-                        g[q] = F2(*reinterpret_cast<const float2*>(src));
-                    else
-                        g[q] = F2(src[0], src[1]);
-                }
-                const float* f = sf + r * kT2W + c + 2;
-                const F2 ux(*reinterpret_cast<const float2*>(f));
-                const F2 uy(*reinterpret_cast<const float2*>(f + kT2FldPlane));
-                const F2 ax(*reinterpret_cast<const float2*>(f + 2 * kT2FldPlane));
-                const F2 ay(*reinterpret_cast<const float2*>(f + 3 * kT2FldPlane));
-                const F2 Dh(*reinterpret_cast<const float2*>(f + 4 * kT2FldPlane));
-                const int x = i0 - 2 + c, y = j0 - 1 + r;
-                const F2 src = pair_source<SRC>(a, a.tf, wrap_clamp(x, nx), wrap_clamp(x + 1, nx), wrap_clamp(y, ny));
-                F2 out[kQ];
-                collide_node<F2>(g, ux, uy, ax, ay, Dh, src, magic, w2f, a.tau2_fixed, out);
-#pragma unroll
-                for (int q = 0; q < kQ; ++q) {
-                    float* d = sp + q * kT2PopPlane + (r + 1 - lattice_ey(q)) * kT2W + c + 2 - lattice_ex(q);
-                    if (lattice_ex(q) == 0) {
-                        *reinterpret_cast<float2*>(d) = out[q].v;
-                    } else {
-                        d[0] = out[q].v.x;
-                        d[1] = out[q].v.y;
-                    }
-                }
-            }
-        }
+        float* sp = reinterpret_cast<float*>(smem + s * T::Stage);
+        const float* sf = reinterpret_cast<const float*>(smem + s * T::Stage + T::PopBytes);
+        if (ok) step2_first<SRC, T, NT>(sp, sf, i0, j0, a, a.tf, tid);
         __syncthreads();  // P1 complete (and s_abort visible)
-        if (ok && !s_abort) {
-            // step 2 on the output nodes
-            for (int p = tid; p < kT2R2; p += kT2Threads) {
-                const int r2 = p / (kT2X / 2), c2 = 2 * (p - r2 * (kT2X / 2));
-                const int i = i0 + c2, j = j0 + r2;
-                if (i >= nx || j >= ny) continue;
-                F2 g[kQ];
-#pragma unroll
-                for (int q = 0; q < kQ; ++q)
-                    g[q] = F2(*reinterpret_cast<const float2*>(sp + q * kT2PopPlane +
-                                                              (r2 + 2 - 2 * lattice_ey(q)) * kT2W + c2 + 4 -
-                                                              2 * lattice_ex(q)));
-                const float* f = sf + (r2 + 1) * kT2W + c2 + 4;
-                const F2 ux(*reinterpret_cast<const float2*>(f));
-                const F2 uy(*reinterpret_cast<const float2*>(f + kT2FldPlane));
-                const F2 ax(*reinterpret_cast<const float2*>(f + 2 * kT2FldPlane));
-                const F2 ay(*reinterpret_cast<const float2*>(f + 3 * kT2FldPlane));
-                const F2 Dh(*reinterpret_cast<const float2*>(f + 4 * kT2FldPlane));
-                const F2 src = pair_source<SRC>(a, args.tf2, i, i + 1 < nx ? i + 1 : nx - 1, j);
-                F2 out[kQ];
-                collide_node<F2>(g, ux, uy, ax, ay, Dh, src, magic, w2f, a.tau2_fixed, out);
-                const bool edge = j < kGhostP || j >= ny - kGhostP || i < kGhostP || i + 1 >= nx - kGhostP;
-                if (!edge) {
-                    float* d0 = dst + a.lp.at_g<kGhostP>(i, j);
-#if TRTR_BOUNDS_CHECK
-                    if ((reinterpret_cast<uintptr_t>(d0) & 7u) != 0u) {
-                        TRTR_BOUNDS_FAULT(kBoundsPair, i, j);
-                        continue;
-                    }
-#endif
-#pragma unroll
-                    for (int q = 0; q < kQ; ++q) *reinterpret_cast<float2*>(d0 + q * pl) = out[q].v;
-                } else {
-#pragma unroll
-                    for (int q = 0; q < kQ; ++q) {
-                        store_with_ghosts<kGhostP, kGhostP>(dst + q * pl, a.lp, i, j, out[q].v.x);
-                        if (i + 1 < nx) store_with_ghosts<kGhostP, kGhostP>(dst + q * pl, a.lp, i + 1, j, out[q].v.y);
-                    }
-                }
-            }
-        }
+        if (ok && !s_abort) step2_second<SRC, T, NT>(sp, sf, i0, j0, a, args.tf2, tid);
         __syncthreads();  // stage s fully read
         if (s_abort) {
             if (tid == 0) {

@@ -1,0 +1,198 @@
+// trtr_step2_core.cuh -- the tile of the two-step kernel (two time steps of Eq. (14) per
+// launch), shared by the single-grid kernel (trtr_step2.cu) and the batched one
+// (trtr_batch.cu): the tile geometry, its TMA boxes, and the two steps over a staged tile.
+// Not part of the public ABI.
+#pragma once
+
+#include "trtr_step_core.cuh"
+
+namespace trtr {
+namespace core {
+
+constexpr int kT2NF = 5;  // packed fields: uhat_x, uhat_y, a_x, a_y, Dh
+
+// Stage of one BX x BY output tile: the population box (9 planes) and the field box (5 planes).
+template <int BX, int BY>
+struct Tile2 {
+    static constexpr int X = BX, Y = BY;
+    static constexpr int W = BX + 8;                     // staged columns [i0 - 4, i0 + BX + 4)
+    static constexpr int PR = BY + 4;                    // staged population rows
+    static constexpr int FR = BY + 2;                    // staged field rows
+    static constexpr int R1 = (BY + 2) * (BX + 4) / 2;  // node pairs of step 1
+    static constexpr int R2 = BY * BX / 2;               // node pairs of step 2
+    static constexpr int PopPlane = PR * W;              // floats
+    static constexpr int FldPlane = FR * W;
+    static constexpr int PopBytes = kQ * PopPlane * 4;
+    static constexpr int FldBytes = kT2NF * FldPlane * 4;
+    static constexpr int TX = PopBytes + FldBytes;       // bytes per tile (boxes include any fill)
+    static constexpr int Stage = (TX + 127) / 128 * 128;
+    static_assert(BX % 4 == 0, "tile origins on 16-byte boundaries");
+    static_assert(PopBytes % 128 == 0, "the field box must start on a 128-byte boundary");
+    static_assert(W <= 256 && PR <= 256, "TMA box dimensions are at most 256");
+};
+
+template <int STAGES, int CTAS, int THREADS, int BX, int BY>
+struct Geom2 {
+    static constexpr int kStages = STAGES, kCtas = CTAS, kThreads = THREADS;
+    using T = Tile2<BX, BY>;
+    static_assert(STAGES * T::Stage + 256 <= 227 * 1024, "the stages must fit in shared memory");
+};
+// Geometry per source mode (stages, CTAs per SM, threads, tile width, tile height), from the
+// sweeps of rebuilds with -DTRTR_STEP2_STAGES=S -DTRTR_STEP2_CTAS=C -DTRTR_STEP2_THREADS=T
+// -DTRTR_STEP2_BX=X -DTRTR_STEP2_BY=Y (all five; they set it for both modes): a few
+// independent CTAs per SM hide each one's barrier between the two steps, the pulse source's
+// arithmetic favours more of them.
+template <int SRC>
+struct Geom2For {  // in-kernel pulse source
+    using type = Geom2<2, 3, 128, 32, 8>;
+};
+template <>
+struct Geom2For<TRTR_SRC_NONE> {
+    using type = Geom2<2, 2, 256, 32, 16>;
+};
+#ifdef TRTR_STEP2_BX
+template <int SRC>
+using Geom2Of = Geom2<TRTR_STEP2_STAGES, TRTR_STEP2_CTAS, TRTR_STEP2_THREADS, TRTR_STEP2_BX, TRTR_STEP2_BY>;
+#else
+template <int SRC>
+using Geom2Of = typename Geom2For<SRC>::type;
+#endif
+
+struct alignas(16) Step2Args {
+    StepArgs<float> a;  // tf: the pulse uniforms of the first step
+    TimeFields<float> tf2;  // of the second step
+};
+
+// Wrapped index of a node of the halo region (v in [-2, n + 1] with n >= 2 maps onto its
+// periodic image); indices of the unused nodes past that are clamped into the tables.
+__device__ __forceinline__ int wrap_clamp(int v, int n) {
+    v = v < 0 ? v + n : (v >= n ? v - n : v);
+    return v < 0 ? 0 : (v >= n ? n - 1 : v);
+}
+
+// Source term s = dt S^n + dt/2 (S^n - S^{n-1}) of the pair (xi0, xi1) in row yj: the one-step
+// kernel's expressions, node coordinates from the wrapped indices.
+template <int SRC>
+__device__ __forceinline__ F2 pair_source(const StepArgs<float>& a, const TimeFields<float>& tf, int xi0, int xi1,
+                                          int yj) {
+    if (SRC != TRTR_SRC_PULSE) return F2(0.f);
+    const int nx = a.lp.nx, ny = a.lp.ny;
+    const float* tx = reinterpret_cast<const float*>(a.tab_x);
+    const float* ty = reinterpret_cast<const float*>(a.tab_y);
+    const F2 sxm(__ldg(tx + xi0), __ldg(tx + xi1));
+    const F2 cxm(__ldg(tx + nx + xi0), __ldg(tx + nx + xi1));
+    const float sy = __ldg(ty + yj), cy = __ldg(ty + ny + yj);
+    const F2 x = vfma(F2((float)xi0, (float)xi1), F2(a.dx), F2(a.x0));
+    const F2 y(a.y0 + (float)yj * a.dx);
+    const F2 dD = F2(a.dD_amp * sy) * sxm;
+    const F2 dDx = F2(a.dD_amp * 3.14159265358979323846f * sy) * cxm;
+    const F2 dDy = F2(a.dD_amp * 3.14159265358979323846f * cy) * sxm;
+    const F2 Sn = pulse_source(x, y, F2(tf.cx_n), F2(tf.cy_n), F2(tf.inv_s2_n), F2(tf.amp_n), dD, dDx, dDy);
+    const F2 Sp = pulse_source(x, y, F2(tf.cx_p), F2(tf.cy_p), F2(tf.inv_s2_p), F2(tf.amp_p), dD, dDx, dDy);
+    return F2(a.dt) * vfma(F2(1.5f), Sn, F2(-0.5f) * Sp);
+}
+
+// The TMA loads of one tile into `stage` (its barrier armed by the caller): the population box of
+// depth 9 and the packed-field box of depth 5, x origin i0 - 4 (16-byte aligned), rows from
+// j0 - 2 and j0 - 1.
+template <class T>
+__device__ __forceinline__ void step2_issue(unsigned char* stage, uint64_t* bar, const CUtensorMap* mp,
+                                            const CUtensorMap* mf, int i0, int j0, int gx) {
+    const int x = i0 + gx - 4;
+    if (tma_ok(stage, x, j0 + kGhostP - 2, 4)) tma_load_3d(stage, mp, bar, x, j0 + kGhostP - 2, 0);
+    if (tma_ok(stage + T::PopBytes, x, j0 + kGhostP - 1, 4))
+        tma_load_3d(stage + T::PopBytes, mf, bar, x, j0 + kGhostP - 1, 0);
+}
+
+// Step 1 over the tile's halo region R1, in place in the stage (thread tid of NT).
+template <int SRC, class T, int NT>
+__device__ __forceinline__ void step2_first(float* sp, const float* sf, int i0, int j0, const StepArgs<float>& a,
+                                            const TimeFields<float>& tf, int tid) {
+    constexpr int kT2X = T::X, kT2W = T::W, kT2R1 = T::R1, kT2PopPlane = T::PopPlane, kT2FldPlane = T::FldPlane;
+    const int nx = a.lp.nx, ny = a.lp.ny;
+    const F2 magic(a.magic), w2f(a.omega2_fixed);
+    for (int p = tid; p < kT2R1; p += NT) {
+        const int r = p / ((kT2X + 4) / 2), c = 2 * (p - r * ((kT2X + 4) / 2));
+        F2 g[kQ];
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            const float* src = sp + q * kT2PopPlane + (r + 1 - lattice_ey(q)) * kT2W + c + 2 - lattice_ex(q);
+            if (lattice_ex(q) == 0)
+                g[q] = F2(*reinterpret_cast<const float2*>(src));
+            else
+                g[q] = F2(src[0], src[1]);
+        }
+        const float* f = sf + r * kT2W + c + 2;
+        const F2 ux(*reinterpret_cast<const float2*>(f));
+        const F2 uy(*reinterpret_cast<const float2*>(f + kT2FldPlane));
+        const F2 ax(*reinterpret_cast<const float2*>(f + 2 * kT2FldPlane));
+        const F2 ay(*reinterpret_cast<const float2*>(f + 3 * kT2FldPlane));
+        const F2 Dh(*reinterpret_cast<const float2*>(f + 4 * kT2FldPlane));
+        const int x = i0 - 2 + c, y = j0 - 1 + r;
+        const F2 src = pair_source<SRC>(a, tf, wrap_clamp(x, nx), wrap_clamp(x + 1, nx), wrap_clamp(y, ny));
+        F2 out[kQ];
+        collide_node<F2>(g, ux, uy, ax, ay, Dh, src, magic, w2f, a.tau2_fixed, out);
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            float* d = sp + q * kT2PopPlane + (r + 1 - lattice_ey(q)) * kT2W + c + 2 - lattice_ex(q);
+            if (lattice_ex(q) == 0) {
+                *reinterpret_cast<float2*>(d) = out[q].v;
+            } else {
+                d[0] = out[q].v.x;
+                d[1] = out[q].v.y;
+            }
+        }
+    }
+}
+
+// Step 2 on the tile's output nodes from the step-1 values in the stage, stored to a.dst with
+// the ghost copies of nodes within two of an edge.
+template <int SRC, class T, int NT>
+__device__ __forceinline__ void step2_second(const float* sp, const float* sf, int i0, int j0,
+                                             const StepArgs<float>& a, const TimeFields<float>& tf2, int tid) {
+    constexpr int kT2X = T::X, kT2W = T::W, kT2R2 = T::R2, kT2PopPlane = T::PopPlane, kT2FldPlane = T::FldPlane;
+    const int nx = a.lp.nx, ny = a.lp.ny;
+    const F2 magic(a.magic), w2f(a.omega2_fixed);
+    float* dst = static_cast<float*>(a.dst);
+    const size_t pl = a.lp.plane;
+    for (int p = tid; p < kT2R2; p += NT) {
+        const int r2 = p / (kT2X / 2), c2 = 2 * (p - r2 * (kT2X / 2));
+        const int i = i0 + c2, j = j0 + r2;
+        if (i >= nx || j >= ny) continue;
+        F2 g[kQ];
+#pragma unroll
+        for (int q = 0; q < kQ; ++q)
+            g[q] = F2(*reinterpret_cast<const float2*>(sp + q * kT2PopPlane + (r2 + 2 - 2 * lattice_ey(q)) * kT2W +
+                                                      c2 + 4 - 2 * lattice_ex(q)));
+        const float* f = sf + (r2 + 1) * kT2W + c2 + 4;
+        const F2 ux(*reinterpret_cast<const float2*>(f));
+        const F2 uy(*reinterpret_cast<const float2*>(f + kT2FldPlane));
+        const F2 ax(*reinterpret_cast<const float2*>(f + 2 * kT2FldPlane));
+        const F2 ay(*reinterpret_cast<const float2*>(f + 3 * kT2FldPlane));
+        const F2 Dh(*reinterpret_cast<const float2*>(f + 4 * kT2FldPlane));
+        const F2 src = pair_source<SRC>(a, tf2, i, i + 1 < nx ? i + 1 : nx - 1, j);
+        F2 out[kQ];
+        collide_node<F2>(g, ux, uy, ax, ay, Dh, src, magic, w2f, a.tau2_fixed, out);
+        const bool edge = j < kGhostP || j >= ny - kGhostP || i < kGhostP || i + 1 >= nx - kGhostP;
+        if (!edge) {
+            float* d0 = dst + a.lp.at_g<kGhostP>(i, j);
+#if TRTR_BOUNDS_CHECK
+            if ((reinterpret_cast<uintptr_t>(d0) & 7u) != 0u) {
+                TRTR_BOUNDS_FAULT(kBoundsPair, i, j);
+                continue;
+            }
+#endif
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) *reinterpret_cast<float2*>(d0 + q * pl) = out[q].v;
+        } else {
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) {
+                store_with_ghosts<kGhostP, kGhostP>(dst + q * pl, a.lp, i, j, out[q].v.x);
+                if (i + 1 < nx) store_with_ghosts<kGhostP, kGhostP>(dst + q * pl, a.lp, i + 1, j, out[q].v.y);
+            }
+        }
+    }
+}
+
+}  // namespace core
+}  // namespace trtr

@@ -103,6 +103,7 @@ _SIGNATURES = {
     "trtr_bounds_report": (_st, [ctypes.POINTER(ctypes.c_ulonglong)]),
     "trtr_check_bounds_path": (_st, [_vp]),
     "trtr_set_steps_per_launch": (_st, [_vp, ctypes.c_int]),
+    "trtr_batch_set_steps_per_launch": (_st, [_vp, ctypes.c_int]),
     "trtr_get_steps_per_launch": (_st, [_vp, ctypes.POINTER(ctypes.c_int)]),
 }
 
@@ -564,6 +565,10 @@ def trtr_batch_step(b, n: int):
     _bcheck(lib.trtr_batch_step(b, int(n)), "trtr_batch_step")
 
 
+def trtr_batch_set_steps_per_launch(b, k: int):
+    _bcheck(lib.trtr_batch_set_steps_per_launch(b, int(k)), "trtr_batch_set_steps_per_launch")
+
+
 def trtr_batch_sync(b):
     _bcheck(lib.trtr_batch_sync(b), "trtr_batch_sync")
 
@@ -637,6 +642,9 @@ class Batch:
 
     def set_config(self, c: int):
         trtr_batch_set_config(self.b, c)
+
+    def set_steps_per_launch(self, k: int):
+        trtr_batch_set_steps_per_launch(self.b, k)
 
     def step(self, n: int = 1):
         trtr_batch_step(self.b, n)

@@ -44,6 +44,7 @@ def test_every_batch_config_is_bitwise_the_single_solve(precision):
     for config in range(T.trtr_batch_config_count()):
         with T.Batch([T.pulse_instance(p, precision) for p in pulses]) as b:
             b.set_config(config)
+            b.set_steps_per_launch(1)  # every step through the configured one-step kernel
             b.step(steps)
             b.sync()
             assert b.info()["step"] == steps
@@ -96,3 +97,29 @@ def test_instances_cannot_be_stepped_alone():
         with pytest.raises(T.TrtrError) as e:
             b.step(1)
         assert e.value.status == T.TRTR_ESTATE
+
+
+@pytest.mark.parametrize("steps", [[37], [3, 5, 2, 7, 1, 9]])
+@pytest.mark.parametrize("D_amp", [0.0, 0.5])
+def test_two_steps_per_launch_batch_is_bitwise_the_single_solve(steps, D_amp):
+    """FP32 batches run pairs of steps through the two-step kernel; odd steps, and step counts
+    split over several calls, interleave it with the one-step kernel (D_amp > 0: the in-kernel
+    pulse source, whose time uniforms both kernels advance)."""
+    pulses = _uneven_pulses(D_amp=D_amp)
+    total = sum(steps)
+    ref = [_single_solution(p, T.TRTR_F32, total) for p in pulses]
+    with T.Batch([T.pulse_instance(p, T.TRTR_F32) for p in pulses]) as b:
+        for n in steps:
+            b.step(n)
+        b.sync()
+        assert b.info()["step"] == total
+        for k, p in enumerate(pulses):
+            assert np.array_equal(b.instance(k).get_populations(), ref[k]), (k, p.n)
+
+
+def test_batch_steps_per_launch_is_validated():
+    pulses = _uneven_pulses()[:2]
+    with T.Batch([T.pulse_instance(p, T.TRTR_F32) for p in pulses]) as b:
+        for bad in (0, 3):
+            with pytest.raises(T.TrtrError):
+                b.set_steps_per_launch(bad)
