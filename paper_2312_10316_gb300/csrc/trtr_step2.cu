@@ -48,8 +48,15 @@ __global__ void __launch_bounds__(G::kThreads, G::kCtas)
     const int nx = a.lp.nx, ny = a.lp.ny;
     const int ntx = (nx + T::X - 1) / T::X, nty = (ny + T::Y - 1) / T::Y;
     const int ntiles = ntx * nty;
-    const int first = blockIdx.x, stride = gridDim.x;
-    const int my_tiles = first < ntiles ? (ntiles - 1 - first) / stride + 1 : 0;
+#ifndef TRTR_STEP2_ORDER
+#define TRTR_STEP2_ORDER 0
+#endif
+    // tile order: 0 interleaved (tile = CTA + k grid), 1 a contiguous row-major run per CTA
+    const int chunk = (ntiles + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int first = TRTR_STEP2_ORDER ? (int)blockIdx.x * chunk : (int)blockIdx.x;
+    const int stride = TRTR_STEP2_ORDER ? 1 : (int)gridDim.x;
+    const int my_tiles = TRTR_STEP2_ORDER ? (first < ntiles ? min(chunk, ntiles - first) : 0)
+                                          : (first < ntiles ? (ntiles - 1 - first) / stride + 1 : 0);
     auto tile_x0 = [&](int k) { return ((first + k * stride) % ntx) * T::X; };
     auto tile_y0 = [&](int k) { return ((first + k * stride) / ntx) * T::Y; };
     auto issue = [&](int k, int s) {
