@@ -625,11 +625,13 @@ def run_adjoint(args):
     if rank != 0:
         return None
     value = steps * n * n / t_grad / 1e9
-    # algorithmic bytes per node and step of one gradient: the recorded forward step and its
-    # recomputation (84 B each in FP32) and the adjoint step (9 populations and 9 + 9 adjoint
-    # values, u, D, the FP64 gradient read and written: 136 B)
+    # algorithmic bytes per node and step of one gradient: the recorded forward step (FP32: two
+    # steps per launch, 46 B per step; else 84 / 168 B), its recomputation (84 B in FP32) and the
+    # adjoint step (9 populations and 9 + 9 adjoint values, u, D, the FP64 gradient read and
+    # written: 136 B)
     pb = 8 if prec == T.TRTR_F64 else 4
-    bpn = 2 * algorithmic_bytes_per_node(pb, pb) + (27 * pb + 3 * pb + 16)
+    forward = two_step_bytes_per_node(pb) / 2 if prec == T.TRTR_F32 else algorithmic_bytes_per_node(pb, pb)
+    bpn = forward + algorithmic_bytes_per_node(pb, pb) + (27 * pb + 3 * pb + 16)
     peak, peak_kind = measured_hbm_peak()
     achieved = bpn * n * n * steps / t_grad / 1e9
     cpu = None if args.no_cpu_baseline else adjoint_cpu_baseline(args.cpu_seconds)
@@ -650,7 +652,7 @@ def run_adjoint(args):
         "clocks": clk,
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": f"{peak_kind} copy bandwidth",
-                     "bytes_per_node": bpn, "kernel": "step_kernel + adj_step_kernel",
+                     "bytes_per_node": bpn, "kernel": "step2_kernel + step_kernel + adj_step_kernel",
                      "note": "512^2: the 22 MB per step stay in L2 and each launch is latency-bound"},
         "cpu_baseline": cpu,
     }

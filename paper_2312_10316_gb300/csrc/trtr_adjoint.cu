@@ -246,16 +246,36 @@ trtr_status trtr_forward_record(trtr_ctx* ctx, long steps, int interval) {
         trtr::free_adjoint(ctx);
         return adj_fail(ctx, TRTR_ENOMEM, "cannot allocate the checkpoints of the adjoint");
     }
-    for (long k = 0; k < steps; ++k) {
+    // the recorded run keeps only the checkpoint states, so pairs of steps between two
+    // checkpoints may run as one launch of the two-step kernel (the same states bit for bit)
+    const bool two = trtr::two_step_applies(ctx);
+    for (long k = 0; k < steps;) {
         if (k % a->interval == 0 &&
             cudaMemcpyAsync(a->ckpt[k / a->interval], ctx->pop[ctx->cur], a->state_bytes, cudaMemcpyDeviceToDevice,
                             ctx->stream) != cudaSuccess)
             return adj_fail(ctx, TRTR_ECUDA, "checkpoint copy failed");
-        if (trtr::launch_step(ctx) != cudaSuccess) return adj_fail(ctx, TRTR_ECUDA, "step launch failed");
-        ctx->launches += 1;
-        ctx->cur ^= 1;
-        ctx->ghost2_ready = false;
-        ctx->step += 1;
+        const long to_checkpoint = a->interval - k % a->interval;
+        if (two && to_checkpoint >= 2 && steps - k >= 2) {
+            if (!ctx->fld2_ready) {
+                if (trtr::launch_pack_fields2(ctx) != cudaSuccess) return adj_fail(ctx, TRTR_ECUDA, "field packing failed");
+                ctx->fld2_ready = true;
+            }
+            if (!ctx->ghost2_ready && trtr::launch_refresh_ghosts2(ctx) != cudaSuccess)
+                return adj_fail(ctx, TRTR_ECUDA, "ghost refresh failed");
+            if (trtr::launch_step2(ctx) != cudaSuccess) return adj_fail(ctx, TRTR_ECUDA, "step launch failed");
+            ctx->launches += 1;
+            ctx->cur ^= 1;
+            ctx->ghost2_ready = true;
+            ctx->step += 2;
+            k += 2;
+        } else {
+            if (trtr::launch_step(ctx) != cudaSuccess) return adj_fail(ctx, TRTR_ECUDA, "step launch failed");
+            ctx->launches += 1;
+            ctx->cur ^= 1;
+            ctx->ghost2_ready = false;
+            ctx->step += 1;
+            k += 1;
+        }
     }
     return TRTR_OK;
 }

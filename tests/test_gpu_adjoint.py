@@ -32,12 +32,13 @@ def _setup(n, steps_courant=0.5, seed=4, tau2=None, nx=None, ny=None):
     return pulse, f["ux"][:ny, :nx], f["uy"][:ny, :nx], D, f["phi0"][:ny, :nx]
 
 
-def _gpu_grad(pulse, ux, uy, D, phi0, lamN, steps, precision, interval=0, nx=None, ny=None):
+def _gpu_grad(pulse, ux, uy, D, phi0, lamN, steps, precision, interval=0, nx=None, ny=None, spl=2):
     nx = nx or pulse.nx
     ny = ny or pulse.ny
     over = {} if pulse.tau2 is None else {"tau2_mode": T.TRTR_TAU2_FIXED, "tau2": pulse.tau2}
     p = T.Params(nx=nx, ny=ny, dx=pulse.dx, dt=pulse.dt, precision=precision, **over)
     with T.Solver(p) as s:
+        s.set_steps_per_launch(spl)
         s.set_fields(ux, uy, D)
         s.init_equilibrium(phi0)
         s.forward_record(steps, interval)
@@ -82,6 +83,18 @@ def test_adjoint_ragged_grid_and_checkpoint_intervals():
         assert np.array_equal(g, grads[0])
     _, grad_o = _oracle_grad(pulse, ux, uy, D, phi0, lamN, steps, nx=37, ny=23)
     assert rel_l2(grads[0], grad_o) <= 1e-10
+
+
+def test_recorded_run_with_two_steps_per_launch_gives_the_same_gradient():
+    """FP32: the recorded forward run takes pairs of steps between checkpoints through the
+    two-step kernel; its checkpoints, hence phi and the gradient, are the one-step run's bits."""
+    pulse, ux, uy, D, phi0 = _setup(40, nx=37, ny=23)
+    lamN = np.random.default_rng(5).uniform(-1, 1, size=(23, 37))
+    for steps, iv in ((30, 7), (31, 0), (30, 1), (29, 29), (40, 8)):
+        one = _gpu_grad(pulse, ux, uy, D, phi0, lamN, steps, T.TRTR_F32, iv, nx=37, ny=23, spl=1)
+        two = _gpu_grad(pulse, ux, uy, D, phi0, lamN, steps, T.TRTR_F32, iv, nx=37, ny=23, spl=2)
+        assert np.array_equal(one[0], two[0]), (steps, iv)
+        assert np.array_equal(one[1], two[1]), (steps, iv)
 
 
 def test_adjoint_f32_against_the_oracle_adjoint_64():
