@@ -113,10 +113,7 @@ cudaError_t bounds_take_all(cudaStream_t s, unsigned long long* out);
 
 // Ghost frame widths: the population planes keep two ghost columns and rows on each side (the
 // two-step kernel pulls twice across an edge); the field planes of the one-step kernel one.
-#ifndef TRTR_GHOST_P
-#define TRTR_GHOST_P 2
-#endif
-constexpr int kGhostP = TRTR_GHOST_P;
+constexpr int kGhostP = 2;
 constexpr int kGhostF = 1;
 
 struct PlaneLayout {

@@ -108,26 +108,36 @@ __device__ __forceinline__ void step2_issue(unsigned char* stage, uint64_t* bar,
 template <int SRC, class T, int NT>
 __device__ __forceinline__ void step2_first(float* sp, const float* sf, int i0, int j0, const StepArgs<float>& a,
                                             const TimeFields<float>& tf, int tid) {
-    constexpr int kT2X = T::X, kT2W = T::W, kT2R1 = T::R1, kT2PopPlane = T::PopPlane, kT2FldPlane = T::FldPlane;
+    constexpr int kT2W = T::W, kT2PopPlane = T::PopPlane, kT2FldPlane = T::FldPlane;
+    // Node pairs (c, c + 1) of a halo row.  R1SHIFT = 1: c odd, the columns 1 .. X + 2 that step
+    // 2 reads (the planes with e_x != 0 then sit on even offsets); 0: c even from 0, including
+    // the two outermost columns (the planes with e_x = 0 and the fields on even offsets).
+#ifndef TRTR_STEP2_R1SHIFT
+#define TRTR_STEP2_R1SHIFT 0
+#endif
+    constexpr int kShift = TRTR_STEP2_R1SHIFT;
+    constexpr int kRowPairs = (T::X + 4 - 2 * kShift) / 2;
+    constexpr int kPairs = (T::Y + 2) * kRowPairs;
     const int nx = a.lp.nx, ny = a.lp.ny;
     const F2 magic(a.magic), w2f(a.omega2_fixed);
-    for (int p = tid; p < kT2R1; p += NT) {
-        const int r = p / ((kT2X + 4) / 2), c = 2 * (p - r * ((kT2X + 4) / 2));
+    auto ld2 = [](const float* v, bool aligned) {
+        return aligned ? F2(*reinterpret_cast<const float2*>(v)) : F2(v[0], v[1]);
+    };
+    for (int p = tid; p < kPairs; p += NT) {
+        const int r = p / kRowPairs, c = 2 * (p - r * kRowPairs) + kShift;
         F2 g[kQ];
 #pragma unroll
         for (int q = 0; q < kQ; ++q) {
             const float* src = sp + q * kT2PopPlane + (r + 1 - lattice_ey(q)) * kT2W + c + 2 - lattice_ex(q);
-            if (lattice_ex(q) == 0)
-                g[q] = F2(*reinterpret_cast<const float2*>(src));
-            else
-                g[q] = F2(src[0], src[1]);
+            g[q] = ld2(src, (lattice_ex(q) != 0) == (kShift == 1));
         }
         const float* f = sf + r * kT2W + c + 2;
-        const F2 ux(*reinterpret_cast<const float2*>(f));
-        const F2 uy(*reinterpret_cast<const float2*>(f + kT2FldPlane));
-        const F2 ax(*reinterpret_cast<const float2*>(f + 2 * kT2FldPlane));
-        const F2 ay(*reinterpret_cast<const float2*>(f + 3 * kT2FldPlane));
-        const F2 Dh(*reinterpret_cast<const float2*>(f + 4 * kT2FldPlane));
+        const bool fa = kShift == 0;
+        const F2 ux = ld2(f, fa);
+        const F2 uy = ld2(f + kT2FldPlane, fa);
+        const F2 ax = ld2(f + 2 * kT2FldPlane, fa);
+        const F2 ay = ld2(f + 3 * kT2FldPlane, fa);
+        const F2 Dh = ld2(f + 4 * kT2FldPlane, fa);
         const int x = i0 - 2 + c, y = j0 - 1 + r;
         const F2 src = pair_source<SRC>(a, tf, wrap_clamp(x, nx), wrap_clamp(x + 1, nx), wrap_clamp(y, ny));
         F2 out[kQ];
@@ -135,7 +145,7 @@ __device__ __forceinline__ void step2_first(float* sp, const float* sf, int i0, 
 #pragma unroll
         for (int q = 0; q < kQ; ++q) {
             float* d = sp + q * kT2PopPlane + (r + 1 - lattice_ey(q)) * kT2W + c + 2 - lattice_ex(q);
-            if (lattice_ex(q) == 0) {
+            if ((lattice_ex(q) != 0) == (kShift == 1)) {
                 *reinterpret_cast<float2*>(d) = out[q].v;
             } else {
                 d[0] = out[q].v.x;
