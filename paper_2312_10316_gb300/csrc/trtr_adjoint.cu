@@ -36,6 +36,8 @@ struct trtr_adjoint_state {
     std::vector<void*> ckpt;
     std::vector<void*> pool;
     std::vector<CUtensorMap> pool_maps;
+    std::vector<CUtensorMap> pool_maps2;  // the two-step kernel's maps of the pool (FP32)
+    bool two;                             // the recomputation takes pairs of steps per launch
     void* Q[2];
     double* grad;
     trtr::PlaneLayout lq;
@@ -231,6 +233,7 @@ trtr_status trtr_forward_record(trtr_ctx* ctx, long steps, int interval) {
         ok = cudaMalloc(&p, a->state_bytes) == cudaSuccess;
         if (ok) a->ckpt.push_back(p);
     }
+    a->two = trtr::two_step_applies(ctx);
     for (int s = 0; ok && s < a->interval; ++s) {
         void* p = nullptr;
         ok = cudaMalloc(&p, a->state_bytes) == cudaSuccess;
@@ -239,6 +242,10 @@ trtr_status trtr_forward_record(trtr_ctx* ctx, long steps, int interval) {
             CUtensorMap m;
             ok = trtr::encode_pop_map(ctx, p, &m) == cudaSuccess;
             a->pool_maps.push_back(m);
+            if (ok && a->two) {
+                ok = trtr::encode_pop_map2(ctx, p, &m) == cudaSuccess;
+                a->pool_maps2.push_back(m);
+            }
         }
     }
     if (!ok) {
@@ -313,8 +320,21 @@ trtr_status trtr_adjoint(trtr_ctx* ctx, const double* dJ_dphi, int on_device, do
         const long s0 = (long)seg * a->interval;
         const long len = a->steps - s0 < a->interval ? a->steps - s0 : a->interval;
         e = cudaMemcpyAsync(a->pool[0], a->ckpt[seg], a->state_bytes, cudaMemcpyDeviceToDevice, st);
-        for (long k = 0; k + 1 < len && e == cudaSuccess; ++k)
-            e = trtr::launch_step_from(ctx, &a->pool_maps[k], a->pool[k + 1], a->n0 + s0 + k);
+        // recompute the segment's states: pairs through the two-step kernel, which stores the
+        // intermediate state as well (FP32; the checkpoint may carry only the one-wide ghost
+        // frame, so its outer ring is refreshed first), a last odd step by the one-step kernel
+        const bool pairs = a->two && len >= 3;
+        if (pairs && e == cudaSuccess) e = trtr::launch_refresh_ghosts2_buffer(ctx, a->pool[0]);
+        long recompute_launches = 0;
+        for (long k = 0; k + 1 < len && e == cudaSuccess; ++recompute_launches) {
+            if (pairs && k + 2 < len) {
+                e = trtr::launch_step2_from(ctx, &a->pool_maps2[k], a->pool[k + 2], a->pool[k + 1], a->n0 + s0 + k);
+                k += 2;
+            } else {
+                e = trtr::launch_step_from(ctx, &a->pool_maps[k], a->pool[k + 1], a->n0 + s0 + k);
+                k += 1;
+            }
+        }
         for (long k = len - 1; k >= 0 && e == cudaSuccess; --k) {
             cudaError_t le = cudaSuccess;
             e = trtr::dispatch(ctx, [&](auto* sp, auto* cp) {
@@ -340,7 +360,7 @@ trtr_status trtr_adjoint(trtr_ctx* ctx, const double* dJ_dphi, int on_device, do
             if (e == cudaSuccess) e = le;
             qc ^= 1;
         }
-        ctx->launches += 2 * len;
+        ctx->launches += recompute_launches + len;  // the recomputation and the adjoint steps
     }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(grad_D, a->grad, n * sizeof(double),

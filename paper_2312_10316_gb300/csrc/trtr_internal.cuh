@@ -270,8 +270,14 @@ bool two_step_applies(const trtr_ctx* ctx);
 cudaError_t encode_maps2(trtr_ctx* ctx);
 cudaError_t launch_pack_fields2(trtr_ctx* ctx);
 cudaError_t launch_step2(trtr_ctx* ctx);
-// the distance-2 ghost cells of the current population buffer from its interior (periodic)
+// the distance-2 ghost cells of the current population buffer (or of buffer P) from its
+// interior (periodic)
 cudaError_t launch_refresh_ghosts2(trtr_ctx* ctx);
+cudaError_t launch_refresh_ghosts2_buffer(trtr_ctx* ctx, void* P);
+// the two-step kernel from an arbitrary population buffer (its map from encode_pop_map2) into
+// dst, as steps `step` and `step + 1`; dst1 (or null) receives the intermediate state
+cudaError_t encode_pop_map2(trtr_ctx* ctx, void* buffer, CUtensorMap* out);
+cudaError_t launch_step2_from(trtr_ctx* ctx, const CUtensorMap* src_map, void* dst, void* dst1, long step);
 // one block whose bounded wait on a barrier that nothing completes gives up after `cycles`
 cudaError_t launch_wait_timeout(trtr_ctx* ctx, long long cycles);
 // one thread that gives the bounds checks four bad arguments and accesses nothing with them

@@ -32,7 +32,7 @@ namespace {
 
 using namespace core;
 
-template <int SRC, class G>
+template <int SRC, class G, bool P1>
 __global__ void __launch_bounds__(G::kThreads, G::kCtas)
     step2_kernel(const __grid_constant__ CUtensorMap mp, const __grid_constant__ CUtensorMap mf, const Step2Args args) {
     constexpr int STAGES = G::kStages, NT = G::kThreads;
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(G::kThreads, G::kCtas)
         const float* sf = reinterpret_cast<const float*>(smem + s * T::Stage + T::PopBytes);
         if (ok) step2_first<SRC, T, NT>(sp, sf, i0, j0, a, a.tf, tid);
         __syncthreads();  // P1 complete (and s_abort visible)
-        if (ok && !s_abort) step2_second<SRC, T, NT>(sp, sf, i0, j0, a, args.tf2, tid);
+        if (ok && !s_abort) step2_second<SRC, T, NT, P1>(sp, sf, i0, j0, a, args.tf2, tid, static_cast<float*>(args.dst1));
         __syncthreads();  // stage s fully read
         if (s_abort) {
             if (tid == 0) {
@@ -147,9 +147,11 @@ __global__ void refresh_ghosts2_kernel(float* P, PlaneLayout L) {
     }
 }
 
-template <int SRC, class G>
-cudaError_t launch2_typed(trtr_ctx* ctx) {
-    auto kernel = step2_kernel<SRC, G>;
+// One launch: two steps from the buffer described by src_map into dst (dst1: the intermediate
+// state too, or null), as steps `step` and `step + 1` (the pulse source's time levels).
+template <int SRC, class G, bool P1>
+cudaError_t launch2_typed(trtr_ctx* ctx, const CUtensorMap& src_map, void* dst, void* dst1, long step) {
+    auto kernel = step2_kernel<SRC, G, P1>;
     const size_t smem = (size_t)G::kStages * G::T::Stage + 128 + G::kStages * sizeof(uint64_t);
     static int configured_device = -1;
     static int ctas_per_sm = 1;
@@ -164,7 +166,8 @@ cudaError_t launch2_typed(trtr_ctx* ctx) {
     Step2Args args;
     StepArgs<float>& a = args.a;
     memset(static_cast<void*>(&args), 0, sizeof(args));
-    a.dst = ctx->pop[ctx->cur ^ 1];
+    a.dst = dst;
+    args.dst1 = dst1;
     a.tab_x = static_cast<const float*>(ctx->tab_x);
     a.tab_y = static_cast<const float*>(ctx->tab_y);
     a.flag = ctx->dflag;
@@ -179,7 +182,7 @@ cudaError_t launch2_typed(trtr_ctx* ctx) {
     a.dx = (float)ctx->p.dx;
     a.dt = (float)ctx->p.dt;
     if (SRC == TRTR_SRC_PULSE) {
-        const long n = ctx->step;
+        const long n = step;
         const PulseTime t0 = pulse_at(ctx->pulse, (double)(n - 1) * ctx->p.dt);
         const PulseTime t1 = pulse_at(ctx->pulse, (double)n * ctx->p.dt);
         const PulseTime t2 = pulse_at(ctx->pulse, (double)(n + 1) * ctx->p.dt);
@@ -203,7 +206,7 @@ cudaError_t launch2_typed(trtr_ctx* ctx) {
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kernel, ctx->maps2[ctx->cur], ctx->maps2[2], args);
+    return cudaLaunchKernelEx(&cfg, kernel, src_map, ctx->maps2[2], args);
 }
 
 }  // namespace
@@ -211,6 +214,13 @@ cudaError_t launch2_typed(trtr_ctx* ctx) {
 bool two_step_applies(const trtr_ctx* ctx) {
     return ctx->fld2 != nullptr && ctx->steps_per_launch == 2 && ctx->p.bc_mode == TRTR_BC_PERIODIC &&
            (ctx->p.src_mode == TRTR_SRC_NONE || ctx->p.src_mode == TRTR_SRC_PULSE);
+}
+
+template <class G>
+cudaError_t encode_pop2_typed(trtr_ctx* ctx, void* buffer, CUtensorMap* out) {
+    using T = typename G::T;
+    return encode(out, tma_type<float>(), 4, buffer, ctx->lp, kQ, T::W, T::PR, kQ) ? cudaSuccess
+                                                                                  : cudaErrorInvalidValue;
 }
 
 template <class G>
@@ -239,18 +249,34 @@ cudaError_t launch_pack_fields2(trtr_ctx* ctx) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_refresh_ghosts2(trtr_ctx* ctx) {
+cudaError_t launch_refresh_ghosts2_buffer(trtr_ctx* ctx, void* P) {
     const int n = 2 * (ctx->p.nx + 2 * kGhostP) + 2 * (ctx->p.ny + 2 * kGhostP - 2);
     const int want = (kQ * n + 255) / 256, cap = ctx->num_sms * 4;
     ctx->launches += 1;
-    refresh_ghosts2_kernel<<<want < cap ? want : cap, 256, 0, ctx->stream>>>(static_cast<float*>(ctx->pop[ctx->cur]),
-                                                                            ctx->lp);
+    refresh_ghosts2_kernel<<<want < cap ? want : cap, 256, 0, ctx->stream>>>(static_cast<float*>(P), ctx->lp);
     return cudaGetLastError();
 }
 
+cudaError_t launch_refresh_ghosts2(trtr_ctx* ctx) { return launch_refresh_ghosts2_buffer(ctx, ctx->pop[ctx->cur]); }
+
+cudaError_t encode_pop_map2(trtr_ctx* ctx, void* buffer, CUtensorMap* out) {
+    return ctx->p.src_mode == TRTR_SRC_PULSE ? encode_pop2_typed<Geom2Of<TRTR_SRC_PULSE>>(ctx, buffer, out)
+                                             : encode_pop2_typed<Geom2Of<TRTR_SRC_NONE>>(ctx, buffer, out);
+}
+
+template <bool P1>
+cudaError_t launch2_src(trtr_ctx* ctx, const CUtensorMap* src_map, void* dst, void* dst1, long step) {
+    return ctx->p.src_mode == TRTR_SRC_PULSE
+               ? launch2_typed<TRTR_SRC_PULSE, Geom2Of<TRTR_SRC_PULSE>, P1>(ctx, *src_map, dst, dst1, step)
+               : launch2_typed<TRTR_SRC_NONE, Geom2Of<TRTR_SRC_NONE>, P1>(ctx, *src_map, dst, dst1, step);
+}
+
+cudaError_t launch_step2_from(trtr_ctx* ctx, const CUtensorMap* src_map, void* dst, void* dst1, long step) {
+    return dst1 ? launch2_src<true>(ctx, src_map, dst, dst1, step) : launch2_src<false>(ctx, src_map, dst, dst1, step);
+}
+
 cudaError_t launch_step2(trtr_ctx* ctx) {
-    return ctx->p.src_mode == TRTR_SRC_PULSE ? launch2_typed<TRTR_SRC_PULSE, Geom2Of<TRTR_SRC_PULSE>>(ctx)
-                                             : launch2_typed<TRTR_SRC_NONE, Geom2Of<TRTR_SRC_NONE>>(ctx);
+    return launch_step2_from(ctx, &ctx->maps2[ctx->cur], ctx->pop[ctx->cur ^ 1], nullptr, ctx->step);
 }
 
 TRTR_BOUNDS_TAKE(step2)

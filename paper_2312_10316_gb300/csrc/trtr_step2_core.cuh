@@ -61,6 +61,7 @@ using Geom2Of = typename Geom2For<SRC>::type;
 struct alignas(16) Step2Args {
     StepArgs<float> a;  // tf: the pulse uniforms of the first step
     TimeFields<float> tf2;  // of the second step
+    void* dst1;             // if not null: also store the first step's state here (one-wide ghosts)
 };
 
 // Wrapped index of a node of the halo region (v in [-2, n + 1] with n >= 2 maps onto its
@@ -156,10 +157,12 @@ __device__ __forceinline__ void step2_first(float* sp, const float* sf, int i0, 
 }
 
 // Step 2 on the tile's output nodes from the step-1 values in the stage, stored to a.dst with
-// the ghost copies of nodes within two of an edge.
-template <int SRC, class T, int NT>
+// the ghost copies of nodes within two of an edge.  P1: the step-1 state of the output nodes is
+// stored to dst1 too, with the one-wide ghost frame that one-step kernels read.
+template <int SRC, class T, int NT, bool P1 = false>
 __device__ __forceinline__ void step2_second(const float* sp, const float* sf, int i0, int j0,
-                                             const StepArgs<float>& a, const TimeFields<float>& tf2, int tid) {
+                                             const StepArgs<float>& a, const TimeFields<float>& tf2, int tid,
+                                             float* dst1 = nullptr) {
     constexpr int kT2X = T::X, kT2W = T::W, kT2R2 = T::R2, kT2PopPlane = T::PopPlane, kT2FldPlane = T::FldPlane;
     const int nx = a.lp.nx, ny = a.lp.ny;
     const F2 magic(a.magic), w2f(a.omega2_fixed);
@@ -169,6 +172,14 @@ __device__ __forceinline__ void step2_second(const float* sp, const float* sf, i
         const int r2 = p / (kT2X / 2), c2 = 2 * (p - r2 * (kT2X / 2));
         const int i = i0 + c2, j = j0 + r2;
         if (i >= nx || j >= ny) continue;
+        if constexpr (P1) {  // the step-1 value of node (r2, c2) = R1 node (r2 + 1, c2 + 2), plane by plane
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) {
+                const float* v = sp + q * kT2PopPlane + (r2 + 2 - lattice_ey(q)) * kT2W + c2 + 4 - lattice_ex(q);
+                store_with_ghosts<1, kGhostP>(dst1 + q * pl, a.lp, i, j, v[0]);
+                if (i + 1 < nx) store_with_ghosts<1, kGhostP>(dst1 + q * pl, a.lp, i + 1, j, v[1]);
+            }
+        }
         F2 g[kQ];
 #pragma unroll
         for (int q = 0; q < kQ; ++q)
