@@ -247,8 +247,9 @@ trtr_status trtr_adjoint(trtr_ctx* ctx, const double* dJ_dphi, int on_device, do
 /* ---- Batched instances ----------------------------------------------------------------
  * Many independent problems of uneven sizes advanced together, each by the same step of
  * Eq. (14).  The paper solves one problem at a time; this is a throughput mode of its step.
- * One persistent kernel launch per time step walks a work-list of (instance, tile) pairs
- * spanning every instance; trtr_batch_step replays a two-step CUDA graph of those launches.
+ * Persistent kernel launches walk a work-list of (instance, tile) pairs spanning every
+ * instance: one time step per launch, or two for FP32 instances (the two-step kernel);
+ * trtr_batch_step replays two-launch CUDA graphs of them.
  * Each instance is an ordinary context (trtr_batch_instance gives it out for queries). */
 typedef struct {
     trtr_params p;  /* the instance's lattice and options.  precision: the same for every

@@ -1,16 +1,18 @@
 // trtr_batch.cu -- many independent pulse problems of uneven sizes advanced together.
 //
 // Every instance is an ordinary context (its own ghosted planes, fields and reductions).
-// One persistent kernel launch per time step walks a work-list of (instance, tile) pairs
-// spanning all instances; per tile the producer thread issues the instance's TMA loads,
-// then copies the instance's step arguments from a device descriptor into a shared-memory
-// slot of the stage and gives the stage's mbarrier its second arrival, so the consumers
-// read the arguments after their acquire-wait.  The arithmetic per node is the single-grid
-// step's (Eq. (14)); only the work distribution differs.
+// A persistent kernel launch walks a work-list of (instance, tile) pairs spanning all
+// instances, one time step per launch (batch_kernel) or, for FP32 instances, two
+// (batch2_kernel, the two-step kernel's tile code).  Per tile the producer thread issues the
+// instance's TMA loads, then copies the instance's step arguments from a device descriptor
+// into a shared-memory slot of the stage and gives the stage's mbarrier its second arrival,
+// so the consumers read the arguments after their acquire-wait.  The arithmetic per node is
+// the single-grid step's (Eq. (14)); only the work distribution differs.
 //
-// Time-dependent uniforms (the pulse source at t_n and t_{n-1}) live in a device table
-// that the last CTA to finish a step advances, together with a device step clock, so a
-// two-step CUDA graph of the launches can be replayed with no host involvement.
+// Time-dependent uniforms (the pulse source at t_n and t_{n-1}, and for two-step launches at
+// t_{n+1}) live in device tables that the last CTA to finish a launch advances, together
+// with a device step clock, so two-launch CUDA graphs can be replayed with no host
+// involvement.
 //
 // The autotuner (trtr_batch_tune) times every tile shape x schedule and keeps the fastest.
 #include <math.h>
