@@ -139,6 +139,64 @@ def run_slab(rank, world, nx, ny, seed, steps, exchange=True):
     return g.sum(axis=0), g, float(mass[0])
 
 
+def _exchange_rows(rows_up, rows_down, prev, nxt, tag):
+    """Sends rows_up (this slab's top owned rows) to the next rank and rows_down (its bottom owned
+    rows) to the previous one; returns (rows from the previous rank, rows from the next)."""
+    from_prev = torch.empty_like(rows_up)
+    from_next = torch.empty_like(rows_down)
+    reqs = [dist.isend(rows_up, nxt, tag=tag), dist.isend(rows_down, prev, tag=tag + 1),
+            dist.irecv(from_prev, prev, tag=tag), dist.irecv(from_next, nxt, tag=tag + 1)]
+    for q in reqs:
+        q.wait()
+    return from_prev, from_next
+
+
+def run_slab_two(rank, world, nx, ny, seed, steps):
+    """Two steps per exchange (the two-step kernel's tile logic across ranks).  A slab of rows
+    [a, b) steps an extended slab [a - 3, b + 3) twice between exchanges.  Before each pair the
+    two ghost rows next to the slab on each side receive the neighbours' full pre-collision
+    state; the third ghost row holds no state (NaN), only the velocity and D rows that the
+    second ghost row's gradient of the auxiliary term reads (exchanged once, like the packed
+    acceleration field of the two-step kernel).  After two steps the owned rows are exact: an
+    owned row's second step reads first-step values of the rows up to one outside the slab,
+    and those read the exchanged rows and their exact collisions."""
+    import oracle
+
+    case = global_case(seed, nx, ny, steps)
+    a, b = slab_rows(ny, world)[rank]
+    h = b - a
+    assert h >= 3 and steps % 2 == 0
+    prev, nxt = (rank - 1) % world, (rank + 1) % world
+    own = torch.from_numpy(np.stack([case["ux"][a:b], case["uy"][a:b], case["D"][a:b]]).copy())
+    below, above = _exchange_rows(own[:, -3:].contiguous(), own[:, :3].contiguous(), prev, nxt, TAG_FIELD)
+    fields = torch.cat([below, own, above], dim=1).numpy()
+
+    def ext(field):  # a per-node field over the extended rows (the sources are local inputs)
+        return np.take(field, np.arange(a - 3, b + 3) % ny, axis=0)
+
+    S = case["S"]
+    sim = oracle.Sim(_params(nx, h + 6, case))
+    sim.set_fields(fields[0], fields[1], fields[2])
+    g = np.full((9, h + 6, nx), np.nan)
+    g[:, 3:h + 3] = case["g"][:, a:b]
+    for n in range(0, steps, 2):
+        top, bottom = _exchange_rows(torch.from_numpy(g[:, h + 1:h + 3].copy()),
+                                     torch.from_numpy(g[:, 3:5].copy()), prev, nxt, TAG_UP)
+        g[:, 1:3] = top.numpy()             # the previous rank's top two owned rows
+        g[:, h + 3:h + 5] = bottom.numpy()  # the next rank's bottom two owned rows
+        sim.set_g(g, step=n)
+        sim.set_source_prev(ext(S[n]))
+        sim.set_source(ext(S[n + 1]))
+        sim.step(1)
+        sim.set_source(ext(S[n + 2]))
+        sim.step(1)
+        g = sim.get_g()
+        g[:, :3] = np.nan
+        g[:, h + 3:] = np.nan
+    sim.close()
+    return g[:, 3:h + 3]
+
+
 def run_global(nx, ny, seed, steps):
     import oracle
 
@@ -163,7 +221,8 @@ def _worker(rank, world, port, nx, ny, seed, steps, q):
     try:
         phi, g, mass = run_slab(rank, world, nx, ny, seed, steps)
         phi_x, _, _ = run_slab(rank, world, nx, ny, seed, steps, exchange=False)
-        q.put((rank, phi, g, mass, phi_x))
+        g2 = run_slab_two(rank, world, nx, ny, seed, steps - steps % 2)
+        q.put((rank, phi, g, mass, phi_x, g2))
     finally:
         dist.destroy_process_group()
 
@@ -177,9 +236,10 @@ def test_slab_rows_cover_the_domain():
             assert max(b - a for a, b in rows) - min(b - a for a, b in rows) <= 1
 
 
-@pytest.mark.parametrize("world,nx,ny,steps", [(2, 37, 29, 6), (3, 16, 5, 5)])
+@pytest.mark.parametrize("world,nx,ny,steps", [(2, 37, 29, 6), (3, 16, 10, 5)])
 def test_slabs_equal_the_single_domain_oracle_bitwise(world, nx, ny, steps):
-    """(3, 16, 5) gives slabs of 2, 2 and 1 rows: a one-row slab receives both halos."""
+    """(3, 16, 10) gives slabs of 4, 3 and 3 rows.  One exchange per step (three populations per
+    edge node and side), and one per two steps (two full rows per side)."""
     seed = 1000 + nx + ny
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
@@ -192,8 +252,10 @@ def test_slabs_equal_the_single_domain_oracle_bitwise(world, nx, ny, steps):
         p.join(timeout=60)
         assert p.exitcode == 0
     phi_ref, g_ref, mass_ref = run_global(nx, ny, seed, steps)
+    _, g_ref2, _ = run_global(nx, ny, seed, steps - steps % 2)
     rows = slab_rows(ny, world)
-    for (rank, phi, g, mass, phi_x), (a, b) in zip(results, rows):
+    for (rank, phi, g, mass, phi_x, g2), (a, b) in zip(results, rows):
+        assert np.array_equal(g2, g_ref2[:, a:b]), rank
         assert np.array_equal(g, g_ref[:, a:b]), rank
         assert np.array_equal(phi, g_ref[:, a:b].sum(axis=0)), rank
         assert np.allclose(phi, phi_ref[a:b], rtol=0, atol=1e-13)
