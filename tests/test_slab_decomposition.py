@@ -221,7 +221,8 @@ def _worker(rank, world, port, nx, ny, seed, steps, q):
     try:
         phi, g, mass = run_slab(rank, world, nx, ny, seed, steps)
         phi_x, _, _ = run_slab(rank, world, nx, ny, seed, steps, exchange=False)
-        g2 = run_slab_two(rank, world, nx, ny, seed, steps - steps % 2)
+        thin = min(b - a for a, b in slab_rows(ny, world)) < 3  # too thin for two steps per exchange
+        g2 = None if thin else run_slab_two(rank, world, nx, ny, seed, steps - steps % 2)
         q.put((rank, phi, g, mass, phi_x, g2))
     finally:
         dist.destroy_process_group()
@@ -236,10 +237,11 @@ def test_slab_rows_cover_the_domain():
             assert max(b - a for a, b in rows) - min(b - a for a, b in rows) <= 1
 
 
-@pytest.mark.parametrize("world,nx,ny,steps", [(2, 37, 29, 6), (3, 16, 10, 5)])
+@pytest.mark.parametrize("world,nx,ny,steps", [(2, 37, 29, 6), (3, 16, 10, 5), (3, 16, 5, 5)])
 def test_slabs_equal_the_single_domain_oracle_bitwise(world, nx, ny, steps):
-    """(3, 16, 10) gives slabs of 4, 3 and 3 rows.  One exchange per step (three populations per
-    edge node and side), and one per two steps (two full rows per side)."""
+    """One exchange per step (three populations per edge node and side), and one per two steps
+    (two full rows per side).  (3, 16, 10) gives slabs of 4, 3 and 3 rows; (3, 16, 5) slabs of 2,
+    2 and 1 rows, where a one-row slab receives both halos (one step per exchange only)."""
     seed = 1000 + nx + ny
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
@@ -255,7 +257,8 @@ def test_slabs_equal_the_single_domain_oracle_bitwise(world, nx, ny, steps):
     _, g_ref2, _ = run_global(nx, ny, seed, steps - steps % 2)
     rows = slab_rows(ny, world)
     for (rank, phi, g, mass, phi_x, g2), (a, b) in zip(results, rows):
-        assert np.array_equal(g2, g_ref2[:, a:b]), rank
+        if g2 is not None:
+            assert np.array_equal(g2, g_ref2[:, a:b]), rank
         assert np.array_equal(g, g_ref[:, a:b]), rank
         assert np.array_equal(phi, g_ref[:, a:b].sum(axis=0)), rank
         assert np.allclose(phi, phi_ref[a:b], rtol=0, atol=1e-13)
