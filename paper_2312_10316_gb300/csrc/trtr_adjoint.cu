@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "trtr_internal.cuh"
+#include "trtr_trace.h"
 
 struct trtr_adjoint_state {
     long n0, steps;
@@ -208,6 +209,7 @@ trtr_status adj_fail(trtr_ctx* ctx, trtr_status s, const char* msg) {
 extern "C" {
 
 trtr_status trtr_forward_record(trtr_ctx* ctx, long steps, int interval) {
+    trtr::TraceRange trace("trtr_forward_record");
     if (!ctx) return TRTR_EINVAL;
     if (steps < 1 || interval < 0) return adj_fail(ctx, TRTR_EINVAL, "steps >= 1 and interval >= 0 required");
     if (!ctx->initialized) return adj_fail(ctx, TRTR_ESTATE, "populations not initialised");
@@ -288,6 +290,7 @@ trtr_status trtr_forward_record(trtr_ctx* ctx, long steps, int interval) {
 }
 
 trtr_status trtr_adjoint(trtr_ctx* ctx, const double* dJ_dphi, int on_device, double* grad_D, int grad_on_device) {
+    trtr::TraceRange trace("trtr_adjoint");
     if (!ctx) return TRTR_EINVAL;
     if (!dJ_dphi || !grad_D) return adj_fail(ctx, TRTR_EINVAL, "dJ_dphi and grad_D are required");
     trtr_adjoint_state* a = ctx->adj;

@@ -10,6 +10,7 @@
 #include <new>
 
 #include "trtr_internal.cuh"
+#include "trtr_trace.h"
 
 namespace trtr {
 cudaError_t bounds_take_all(cudaStream_t s, unsigned long long* out) {
@@ -137,6 +138,7 @@ trtr_status sync_and_check(trtr_ctx* ctx, const char* where) {
 }
 
 trtr_status reduce(trtr_ctx* ctx, int kind, const double* ref_dev, double out[2]) {
+    trtr::TraceRange trace("trtr reduce");
     trtr_status s = check_launch(ctx, trtr::launch_reduce(ctx, kind, ref_dev), "reduction launch");
     if (s != TRTR_OK) return s;
     TRTR_CUDA(ctx, cudaMemcpyAsync(ctx->hres, ctx->dres, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
@@ -447,6 +449,7 @@ trtr_status trtr_init_equilibrium(trtr_ctx* ctx, const double* phi0, int on_devi
 }
 
 trtr_status trtr_step(trtr_ctx* ctx, long n) {
+    trtr::TraceRange trace("trtr_step");
     if (!ctx) return TRTR_EINVAL;
     if (n < 0) return fail(ctx, TRTR_EINVAL, "negative step count");
     trtr_status s;
@@ -506,6 +509,7 @@ trtr_status trtr_step(trtr_ctx* ctx, long n) {
 }
 
 trtr_status trtr_moments(trtr_ctx* ctx, double* phi_out, int on_device) {
+    trtr::TraceRange trace("trtr_moments");
     if (!ctx) return TRTR_EINVAL;
     if (!phi_out) return fail(ctx, TRTR_EINVAL, "phi_out is NULL");
     trtr_status s;

@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "trtr_step2_core.cuh"
+#include "trtr_trace.h"
 
 namespace trtr {
 namespace {
@@ -876,6 +877,7 @@ trtr_status trtr_batch_set_steps_per_launch(trtr_batch* b, int k) {
 }
 
 trtr_status trtr_batch_step(trtr_batch* b, long n) {
+    trtr::TraceRange trace("trtr_batch_step");
     if (!b || n < 0) return TRTR_EINVAL;
     return trtr::advance(b, n, b->steps_per_launch);
 }
