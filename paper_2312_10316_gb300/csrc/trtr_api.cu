@@ -269,9 +269,13 @@ trtr_status trtr_create(const trtr_params* p, void* cuda_stream, trtr_ctx** out)
          p->bc_mode == TRTR_BC_DIRICHLET_NEE ? (size_t)trtr::edge_count(p->nx, p->ny) * sizeof(double) : 0, true},
         {&ctx->fld2, two_step ? 5 * ctx->lt.plane * sizeof(float) : 0, true},
     };
+    // fault injection for tests: TRTR_FAULT_ALLOC=k makes the k-th device allocation here fail
+    const char* fault = getenv("TRTR_FAULT_ALLOC");
+    const int fail_at = fault ? atoi(fault) : 0;
+    int nalloc = 0;
     for (auto& a : allocs) {
         if (a.bytes == 0) continue;
-        if (cudaMalloc(a.ptr, a.bytes) != cudaSuccess) {
+        if (++nalloc == fail_at || cudaMalloc(a.ptr, a.bytes) != cudaSuccess) {
             cudaGetLastError();
             trtr_destroy(ctx);
             return TRTR_ENOMEM;

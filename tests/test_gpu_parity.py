@@ -422,3 +422,27 @@ def test_precision_1024_against_oracle(prec):
         err = rel_l2(s.moments(), o.phi())
     tol = TOL_F32 if prec == "f32" else _half_tol(prec, steps)
     assert err <= tol, err
+
+
+@pytest.mark.parametrize("k", [1, 2, 5, 8, 10])  # an FP32 periodic context makes 10 allocations
+def test_allocation_failure_is_reported_and_leaves_nothing(k, monkeypatch):
+    """Host-side fault injection: TRTR_FAULT_ALLOC=k fails the k-th device allocation of
+    trtr_create, which returns TRTR_ENOMEM after freeing what it had allocated; the next
+    create succeeds and the free device memory is back where it was."""
+    p = T.Params(nx=600, ny=500, dx=0.01, dt=1e-4, precision=T.TRTR_F32)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    monkeypatch.setenv("TRTR_FAULT_ALLOC", str(k))
+    for _ in range(3):
+        with pytest.raises(T.TrtrError) as e:
+            T.Solver(p)
+        assert e.value.status == T.TRTR_ENOMEM
+    monkeypatch.delenv("TRTR_FAULT_ALLOC")
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert abs(free1 - free0) < 8 * 2**20  # no allocation left behind (driver granularity aside)
+    with T.Solver(p) as s:
+        s.set_fields(np.zeros((500, 600)), np.zeros((500, 600)), np.full((500, 600), 1e-3))
+        s.init_equilibrium(np.ones((500, 600)))
+        s.step(2)
+        assert np.abs(s.moments() - 1.0).max() <= 1e-6
