@@ -74,11 +74,14 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample length")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--parity-steps", type=int, default=1000,
-                    help="steps of the FP64 GPU comparison run that states the L2 error (0: skip)")
+    ap.add_argument("--parity-steps", type=int, default=-1,
+                    help="steps of the FP64 GPU comparison run that states the L2 error, independent of "
+                         "--steps (-1: the workload's configured length, 10000 steps; 0: skip)")
     ap.add_argument("--steps-per-launch", default="auto", choices=["auto", "1", "2"],
                     help="auto: two steps per launch where the two-step kernel applies; 1: one step per launch "
                          "(the one-step kernel); 2: as auto")
+    ap.add_argument("--rounding", default="auto", choices=["auto", "nearest", "stochastic"],
+                    help="rounding of the 2-byte storages (auto: the library's default, stochastic; FP32 ignores it)")
     ap.add_argument("--src", default="auto", choices=["auto", "none", "field", "pulse"],
                     help="source mode of the timed step kernel (auto: the workload's; 'field' uses the "
                          "manufactured source as a stationary field); other than auto skips parity and e2e")
@@ -286,7 +289,9 @@ def run_ours(args):
                     "pulse": T.TRTR_SRC_PULSE}[args.src]
     if src_override is not None:
         args.parity_steps, args.no_e2e = 0, True
-    solver = T.pulse_solver(pulse, precision=prec, stream=sh, src_mode=src_override)
+    rounding = "stochastic" if args.rounding == "auto" else args.rounding
+    rnd = T.TRTR_ROUND_STOCHASTIC if rounding == "stochastic" else T.TRTR_ROUND_NEAREST
+    solver = T.pulse_solver(pulse, precision=prec, stream=sh, src_mode=src_override, rounding=rnd)
     if src_override == T.TRTR_SRC_FIELD:
         solver.set_source(W.source(pulse, 0.0))  # the manufactured source as a stationary field
     solver.step(args.warmup)
@@ -329,13 +334,21 @@ def run_ours(args):
         bpn, kernel = two_step_bytes_per_node(pop_bytes), "step2_kernel"
     else:
         bpn, kernel = algorithmic_bytes_per_node(pop_bytes), "step_kernel"
-    if src_override == T.TRTR_SRC_FIELD:
-        bpn += 2 * (8 if prec == T.TRTR_F64 else 4)  # S^n and S^{n-1} planes in the compute type
+    # S^n and S^{n-1} planes in the compute type
+    extra = 2 * (8 if prec == T.TRTR_F64 else 4) if src_override == T.TRTR_SRC_FIELD else 0
+    bpn += extra
     peak, peak_kind = measured_hbm_peak()
     achieved = bpn * n_nodes / (avg_launch_ms * 1e-3) / 1e9
     traffic = ncu_traffic(args.workload, kernel) if src_override is None else None
+    # the same launches against the method's bytes per node-update (one step's populations and
+    # fields, whatever the kernel moves), and the DRAM bytes the committed counters measured
+    per_update_bpn = algorithmic_bytes_per_node(pop_bytes) + extra
+    per_update = per_update_bpn * n_nodes * spl / (avg_launch_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
+                "frac_per_node_update": round(per_update / peak, 4),
+                "bytes_per_node_update": per_update_bpn,
+                "frac_dram": (round(traffic / (avg_launch_ms * 1e-3) / 1e9 / peak, 4) if traffic else None),
                 "peak_kind": f"{peak_kind} copy bandwidth", "bytes_per_node": bpn,
                 "kernel": kernel, "steps_per_launch": spl,
                 "median_launch_ms": round(statistics.median(per_launch), 5)}
@@ -345,14 +358,21 @@ def run_ours(args):
     # ---- stated L2 error against the FP64 path (outside the timed region)
     parity = None
     if args.parity_steps and rank == 0:
-        ks = min(args.parity_steps, args.steps + args.warmup)
-        with T.pulse_solver(pulse, precision=prec, stream=sh) as a, \
+        ks = pulse.steps if args.parity_steps < 0 else args.parity_steps
+        at = {}
+        with T.pulse_solver(pulse, precision=prec, stream=sh, rounding=rnd) as a, \
                 T.pulse_solver(pulse, precision=T.TRTR_F64, stream=sh) as b:
-            a.step(ks)
-            b.step(ks)
-            pa, pb = a.moments(), b.moments()
-        parity = {"rel_l2_vs_f64_gpu": float(np.linalg.norm(pa - pb) / np.linalg.norm(pb)), "steps": ks,
-                  "reference": "GPU FP64 path (matches the FP64 oracle to 1e-12)"}
+            done = 0
+            for c in sorted({c for c in (100, 1000, ks) if c <= ks}):
+                a.step(c - done)
+                b.step(c - done)
+                done = c
+                pa, pb = a.moments(), b.moments()
+                at[c] = float(np.linalg.norm(pa - pb) / np.linalg.norm(pb))
+        parity = {"rel_l2_vs_f64_gpu": at[ks], "steps": ks, "rel_l2_at_steps": at,
+                  "mass_rel_diff": float(abs(pa.sum() - pb.sum()) / abs(pb.sum())),
+                  "reference": "GPU FP64 path (matches the FP64 oracle to 1e-12)",
+                  "run": "separate solve of the workload from t = 0, outside the timed region"}
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
@@ -365,6 +385,7 @@ def run_ours(args):
             pinned[k_] = t_
         out = torch.empty((pulse.ny, pulse.nx), dtype=torch.float64, pin_memory=True)
         p = T.Params(nx=pulse.nx, ny=pulse.ny, dx=pulse.dx, dt=pulse.dt, x0=pulse.x0, y0=pulse.y0, precision=prec,
+                     rounding=rnd,
                      src_mode=T.TRTR_SRC_PULSE if pulse.D_amp else T.TRTR_SRC_NONE,
                      tau2_mode=T.TRTR_TAU2_MAGIC if pulse.tau2 is None else T.TRTR_TAU2_FIXED,
                      tau2=pulse.tau2 or 1.0)
@@ -406,6 +427,7 @@ def run_ours(args):
                          "pulse": "manufactured (in-kernel, override)"}[args.src],
                    "omega": pulse.omega, "sigma0": pulse.sigma0,
                    "tau2": "magic 1/12" if pulse.tau2 is None else pulse.tau2, "parallelism": f"replicas{world}",
+                   "rounding": rounding if pop_bytes == 2 else "n/a (FP32 storage)",
                    "l2_flush": f"inputs larger than L2: {2 * 9 * pop_bytes * n_nodes / 1e9:.2f} GB of populations"},
         "roofline": roofline,
         "gpu_launches": gpu_launches,

@@ -59,7 +59,7 @@ typedef enum {
 
 /* Storage / arithmetic of the populations.  F64: stored and computed in double.  F32:
  * stored and computed in float.  F16_OFS / BF16_OFS: stored as the half-precision offset
- * g_i - w_i phi_ref (round to nearest even), computed in float. */
+ * g_i - w_i phi_ref (rounded as trtr_params.rounding says), computed in float. */
 typedef enum { TRTR_F64 = 0, TRTR_F32 = 1, TRTR_F16_OFS = 2, TRTR_BF16_OFS = 3 } trtr_precision;
 
 typedef enum { TRTR_TAU2_MAGIC = 0, TRTR_TAU2_FIXED = 1 } trtr_tau2_mode;
@@ -85,6 +85,19 @@ typedef enum { TRTR_SRC_NONE = 0, TRTR_SRC_FIELD = 1, TRTR_SRC_PULSE = 2 } trtr_
  * TRTR_GRAD_ONESIDED_EDGE for the velocity gradient at the edges. */
 typedef enum { TRTR_BC_PERIODIC = 0, TRTR_BC_DIRICHLET_NEE = 1 } trtr_bc_mode;
 
+/* Rounding of the stored F16_OFS / BF16_OFS offsets (not part of the paper's method, which is
+ * stated in exact arithmetic).  STOCHASTIC (the default, 0): round up with probability equal
+ * to the discarded fraction of the format's unit (the hardware's stochastic-rounding
+ * conversion), fed with random bits that are a fixed hash of the node, the step number and the
+ * population, so a run is reproducible bit for bit and independent of how its steps are split
+ * into calls.  NEAREST: round to nearest even.  Nearest rounding of a smooth field repeats the
+ * same error at neighbouring nodes and steps, so the error of phi grows linearly with the step
+ * count (FP16: 1.8e-1 relative L2 after 10 000 steps of the 4096^2 pulse); stochastic rounding
+ * makes each rounding error zero-mean and independent, the diffusion of the method damps them,
+ * and the error stays near its first-step level (FP16: 2.6e-4 on the same run).  Ignored by the
+ * F32 and F64 storages. */
+typedef enum { TRTR_ROUND_STOCHASTIC = 0, TRTR_ROUND_NEAREST = 1 } trtr_rounding;
+
 typedef struct {
     int nx, ny;         /* nodes, >= 1 each; ny * round_up(nx, 32) < 2^31              */
     double x0, y0;      /* coordinates of node (0, 0)                                  */
@@ -100,6 +113,7 @@ typedef struct {
     int check_every;    /* > 0: trtr_step checks every k steps that all populations are
                            finite and returns TRTR_EUNSTABLE if not (synchronises)      */
     int bc_mode;        /* trtr_bc_mode                                                 */
+    int rounding;       /* trtr_rounding of the 2-byte storages (0: stochastic)          */
 } trtr_params;
 
 typedef struct trtr_ctx trtr_ctx; /* opaque, library-owned */
@@ -117,8 +131,10 @@ trtr_status trtr_destroy(trtr_ctx* ctx);
 
 /* Copies in the coefficient fields u_x, u_y and D (= kappa(x), Eq. (1)); D may be NULL when
  * tau1_const > 0.  S (may be NULL) sets the source field for TRTR_SRC_FIELD as by
- * trtr_set_source.  tau1 = 1/2 + 3 D dt / dx^2 must exceed 1/2 at every node (checked on
- * host input only).  Fields persist until set again. */
+ * trtr_set_source.  tau1 = 1/2 + 3 D dt / dx^2 must exceed 1/2 at every node: D must be
+ * finite and > 0 everywhere, else TRTR_EINVAL with the fields unchanged (host input is checked
+ * on the host; device input by a reduction on the context's stream, so the call then
+ * synchronises).  Fields persist until set again. */
 trtr_status trtr_set_fields(trtr_ctx* ctx, const double* ux, const double* uy, const double* D,
                             const double* S, int on_device);
 
@@ -254,7 +270,8 @@ trtr_status trtr_adjoint(trtr_ctx* ctx, const double* dJ_dphi, int on_device, do
 typedef struct {
     trtr_params p;  /* the instance's lattice and options.  precision: the same for every
                        instance, TRTR_F32, TRTR_F16_OFS or TRTR_BF16_OFS; src_mode: NONE or
-                       PULSE (the manufactured source of its pulse); bc_mode: PERIODIC     */
+                       PULSE (the manufactured source of its pulse); bc_mode: PERIODIC;
+                       rounding: the same for every instance                             */
     double omega, xc, yc, sigma0, D0, D_amp; /* its pulse, as for trtr_set_pulse          */
 } trtr_instance;
 
@@ -276,8 +293,10 @@ const char* trtr_batch_config_name(int config);
 /* Autotuner: times every configuration (of the one-step kernel, one step per launch) over
  * trial_steps (>= 2) steps with CUDA events and keeps the fastest; *config_out (may be NULL) receives it and ms_out (may be NULL, else
  * trtr_batch_config_count() floats) the milliseconds per step of each.  A batch tuned at
- * step 0 is reset to its initial condition afterwards; otherwise the trial steps advance
- * every instance.  Synchronises. */
+ * step 0 gets its step-0 state back afterwards, whatever set it (the pulse, a phi0 or the
+ * caller's populations): the tuner keeps a temporary device copy of every instance's
+ * populations for the trials (TRTR_ENOMEM if that copy cannot be allocated, nothing changed).
+ * At a later step the trial steps advance every instance.  Synchronises. */
 trtr_status trtr_batch_tune(trtr_batch* b, int trial_steps, int* config_out, float* ms_out);
 
 /* Selects a configuration explicitly. */
@@ -330,7 +349,11 @@ trtr_status trtr_batch_info(const trtr_batch* b, int* count, long long* nodes, l
  * device memory, which every device that loads the library holds until the process exits.
  * ny > TRTR_NOALLOC_MAX_ROWS, nx < 1, ny < 1 or a NULL g / out return TRTR_EINVAL with
  * nothing enqueued.  The first call on a device (with that device current) looks up the
- * array's device address; make that first call before any stream capture.  Every call
+ * array's device address and keeps it for the life of the process; make that first call
+ * before any stream capture, and make no call on a device after resetting it
+ * (cudaDeviceReset frees the array and leaves the kept address stale).  An error already
+ * pending in the CUDA runtime when the call starts is returned as TRTR_ECUDA, left pending,
+ * with nothing enqueued.  Every call
  * shares the array and it keeps the last call's contents (each call overwrites rows
  * [0, ny) before reading them, so nothing needs clearing); calls that overlap on the GPU --
  * on different streams, or from several host threads -- race on it and must be serialised

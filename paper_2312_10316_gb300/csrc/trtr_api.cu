@@ -33,7 +33,7 @@ cudaError_t bounds_take_all(cudaStream_t s, unsigned long long* out) {
 
 namespace {
 
-constexpr int kAbiVersion = 2;
+constexpr int kAbiVersion = 3;
 constexpr uint64_t kSaveMagic = 0x3152545254ULL;  // "TRTR1"
 
 struct SaveHeader {
@@ -217,6 +217,7 @@ trtr_status trtr_create(const trtr_params* p, void* cuda_stream, trtr_ctx** out)
     if (p->src_mode < TRTR_SRC_NONE || p->src_mode > TRTR_SRC_PULSE) return TRTR_EINVAL;
     if (p->check_every < 0 || !isfinite(p->phi_ref)) return TRTR_EINVAL;
     if (p->bc_mode != TRTR_BC_PERIODIC && p->bc_mode != TRTR_BC_DIRICHLET_NEE) return TRTR_EINVAL;
+    if (p->rounding != TRTR_ROUND_NEAREST && p->rounding != TRTR_ROUND_STOCHASTIC) return TRTR_EINVAL;
     if (p->bc_mode == TRTR_BC_DIRICHLET_NEE && (p->nx < 3 || p->ny < 3)) return TRTR_EINVAL;
     const trtr::PlaneLayout lp = trtr::make_layout(p->nx, p->ny, (int)es, trtr::kGhostP);
     const trtr::PlaneLayout lf = trtr::make_layout(p->nx, p->ny, p->precision == TRTR_F64 ? 8 : 4, trtr::kGhostF);
@@ -394,6 +395,13 @@ trtr_status trtr_set_fields(trtr_ctx* ctx, const double* ux, const double* uy, c
     if (s == TRTR_OK) s = stage_in(ctx, uy, n, on_device, 1, &duy);
     if (s == TRTR_OK && D) s = stage_in(ctx, D, n, on_device, 2, &dD);
     if (s != TRTR_OK) return s;
+    if (on_device && D && !(ctx->p.tau1_const > 0.0)) {  // the host check above, on the device
+        double r[2];
+        s = reduce(ctx, trtr::kReduceBadField, dD, r);
+        if (s != TRTR_OK) return s;
+        if (r[0] > 0.0)
+            return fail(ctx, TRTR_EINVAL, "D must be > 0 and finite at every node (%.0f nodes are not)", r[0]);
+    }
     s = check_launch(ctx, trtr::launch_convert_fields(ctx, dux, duy, dD), "field conversion");
     if (s != TRTR_OK) return s;
     ctx->fields_set = true;

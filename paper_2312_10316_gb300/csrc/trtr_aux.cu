@@ -244,7 +244,7 @@ __device__ __forceinline__ void block_sum2(double& a, double& b) {
 
 // Per-block FP64 partial sums into scratch[2 * block + {0, 1}]:
 //  kind 0: sum phi;  1: sum (phi - phi_a)^2, sum phi_a^2;  2: same against phi_ref field;
-//  3: number of non-finite populations.
+//  3: number of non-finite populations;  4: number of values of ref that are not finite and > 0.
 template <typename S, typename C>
 __global__ void reduce_kernel(double* partial, const S* P, PlaneLayout L, C phi_ref, int kind, PulseTime pt,
                               double x0, double y0, double dx, const double* ref) {
@@ -252,6 +252,11 @@ __global__ void reduce_kernel(double* partial, const S* P, PlaneLayout L, C phi_
     double a = 0.0, b = 0.0;
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
         const int j = (int)(k / L.nx), i = (int)(k - (size_t)j * L.nx);
+        if (kind == kReduceBadField) {
+            const double v = ref[k];
+            a += (v > 0.0 && isfinite(v)) ? 0.0 : 1.0;
+            continue;
+        }
         if (kind == kReduceNonFinite) {
             for (int q = 0; q < kQ; ++q) {
                 const double v = (double)pulled<S, C>(P, q, i, j, L, phi_ref);

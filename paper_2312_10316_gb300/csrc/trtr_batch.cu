@@ -111,7 +111,7 @@ template <typename S, int SRC, int BX, int BY, int STAGES>
 __global__ void __launch_bounds__(32 * BY, min_blocks<BY>())
     batch_kernel(const InstanceDesc<typename Store<S>::C>* __restrict__ desc, const int4* __restrict__ tiles,
                  int ntiles, TimeFields<float>* tu, TimeFields2* tu2, BatchClock* clk, int count, int parity,
-                 int interleaved) {
+                 int interleaved, int sr) {
     using C = typename Store<S>::C;
     using T = Tile<S, SRC, BX, BY>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -163,6 +163,9 @@ __global__ void __launch_bounds__(32 * BY, min_blocks<BY>())
     __syncthreads();
     if (tid == 0)
         for (int k = 0; k < STAGES && k < my_tiles; ++k) issue(k, k);
+    // stochastic rounding of the 2-byte storages: the key of this step (the clock is advanced
+    // only after every CTA of the launch has finished its tiles)
+    const uint32_t rkey = sr ? sr_step_key((long)*reinterpret_cast<volatile long long*>(&clk->n)) : 0u;
 
     // the work-list entry of the next tile is fetched one iteration ahead (its latency hides
     // behind the current tile)
@@ -198,8 +201,18 @@ __global__ void __launch_bounds__(32 * BY, min_blocks<BY>())
         if (!ok) s_abort = 1;
         if (ok && j < sargs[s].lp.ny) {
             // a private copy: the row's global stores cannot alias it, so its fields are read once
-            const StepArgs<C> args = sargs[s];
-            tile_row_pairs<S, SRC, BX, BY>(smem + s * T::STAGE, r, lane, i0, j, args, sx, cx, sy, cy);
+            StepArgs<C> args = sargs[s];
+            if constexpr (sizeof(S) == 2) {
+                if (sr) {
+                    args.rkey = rkey;
+                    tile_row_pairs<S, SRC, BX, BY, BX / 64, false, 1, true>(smem + s * T::STAGE, r, lane, i0, j, args,
+                                                                          sx, cx, sy, cy);
+                } else {
+                    tile_row_pairs<S, SRC, BX, BY>(smem + s * T::STAGE, r, lane, i0, j, args, sx, cx, sy, cy);
+                }
+            } else {
+                tile_row_pairs<S, SRC, BX, BY>(smem + s * T::STAGE, r, lane, i0, j, args, sx, cx, sy, cy);
+            }
         }
         __syncthreads();
         if (s_abort) {
@@ -367,6 +380,7 @@ struct trtr_batch {
     long step;
     int parity;
     long long nodes;
+    bool sr;  // 2-byte instances rounded stochastically (TRTR_ROUND_STOCHASTIC)
     std::vector<trtr::Pulse> pulses;
 };
 
@@ -402,7 +416,7 @@ struct BatchLaunch {
         auto kernel = batch_kernel<S, SRC, BX, BY, kStages>;
         kernel<<<b->grid, 32 * BY, smem(), b->stream>>>(static_cast<const InstanceDesc<C>*>(b->d_desc), b->d_tiles,
                                                          b->ntiles, b->d_tu, b->d_tu2, b->d_clk, b->count, parity,
-                                                         interleaved);
+                                                         interleaved, b->sr ? 1 : 0);
         return cudaGetLastError();
     }
     static bool encode_desc(trtr_batch* b, InstanceDesc<C>* h) {
@@ -771,12 +785,16 @@ trtr_status trtr_batch_create(const trtr_instance* inst, int count, void* cuda_s
     for (int k = 0; k < count; ++k) {
         if (inst[k].p.precision != prec) return TRTR_EINVAL;
         if (inst[k].p.src_mode == TRTR_SRC_FIELD || inst[k].p.bc_mode != TRTR_BC_PERIODIC) return TRTR_EINVAL;
+        if (inst[k].p.rounding != inst[0].p.rounding ||
+            (inst[k].p.rounding != TRTR_ROUND_STOCHASTIC && inst[k].p.rounding != TRTR_ROUND_NEAREST))
+            return TRTR_EINVAL;
         if (inst[k].p.src_mode == TRTR_SRC_PULSE) src = TRTR_SRC_PULSE;
     }
     trtr_batch* b = new (std::nothrow) trtr_batch();
     if (!b) return TRTR_ENOMEM;
     b->count = count;
     b->precision = prec;
+    b->sr = prec != TRTR_F32 && inst[0].p.rounding == TRTR_ROUND_STOCHASTIC;
     b->src = src;
     b->config = trtr::kDefaultConfig;
     b->ctx = static_cast<trtr_ctx**>(calloc(count, sizeof(trtr_ctx*)));
@@ -911,8 +929,38 @@ trtr_status trtr_batch_sync(trtr_batch* b) {
 trtr_status trtr_batch_tune(trtr_batch* b, int trial_steps, int* config_out, float* ms_out) {
     if (!b || trial_steps < 2) return TRTR_EINVAL;
     const bool restart = b->step == 0;
+    // At step 0 the trials run from the caller's state, whatever set it (the pulse, phi0 or
+    // populations): every instance's current buffer, ghost frame included, is kept in one
+    // temporary device copy and put back afterwards.
+    std::vector<size_t> off(b->count + 1, 0);
+    std::vector<int> cur0(b->count);
+    std::vector<char> ghost0(b->count);
+    unsigned char* keep = nullptr;
+    if (restart) {
+        for (int k = 0; k < b->count; ++k) {
+            const trtr_ctx* c = b->ctx[k];
+            off[k + 1] = off[k] + (size_t)trtr::kQ * c->lp.plane * (size_t)c->esize;
+            cur0[k] = c->cur;
+            ghost0[k] = c->ghost2_ready;
+        }
+        if (cudaMalloc(&keep, off[b->count]) != cudaSuccess) {
+            cudaGetLastError();
+            return TRTR_ENOMEM;
+        }
+        for (int k = 0; k < b->count; ++k)
+            if (cudaMemcpyAsync(keep + off[k], b->ctx[k]->pop[cur0[k]], off[k + 1] - off[k], cudaMemcpyDeviceToDevice,
+                                b->stream) != cudaSuccess) {
+                cudaGetLastError();
+                cudaFree(keep);
+                return TRTR_ECUDA;
+            }
+    }
     cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return TRTR_ECUDA;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        if (keep) cudaFree(keep);
+        return TRTR_ECUDA;
+    }
     int best = b->config;
     float best_ms = 1e30f;
     trtr_status s = TRTR_OK;
@@ -940,16 +988,30 @@ trtr_status trtr_batch_tune(trtr_batch* b, int trial_steps, int* config_out, flo
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (s != TRTR_OK) return s;
-    s = trtr::apply_config(b, best);
-    if (s == TRTR_OK && restart) {  // trials started from the initial condition: restore it
+    if (s == TRTR_OK) s = trtr::apply_config(b, best);
+    if (restart) {  // trials started from the state at step 0: put it back
         for (int k = 0; k < b->count && s == TRTR_OK; ++k) {
-            b->ctx[k]->cur = 0;
-            s = trtr_init_equilibrium(b->ctx[k], nullptr, 0);
+            trtr_ctx* c = b->ctx[k];
+            if (cudaMemcpyAsync(c->pop[cur0[k]], keep + off[k], off[k + 1] - off[k], cudaMemcpyDeviceToDevice,
+                                b->stream) != cudaSuccess) {
+                cudaGetLastError();
+                s = TRTR_ECUDA;
+                break;
+            }
+            c->cur = cur0[k];
+            c->ghost2_ready = ghost0[k] != 0;
+            c->step = 0;
         }
-        b->step = 0;
-        b->parity = 0;
-        if (s == TRTR_OK) s = trtr::reset_clock(b);
+        if (s == TRTR_OK && cudaStreamSynchronize(b->stream) != cudaSuccess) {
+            cudaGetLastError();
+            s = TRTR_ECUDA;
+        }
+        cudaFree(keep);
+        if (s == TRTR_OK) {
+            b->step = 0;
+            b->parity = cur0.empty() ? 0 : cur0[0];
+            s = trtr::reset_clock(b);
+        }
     }
     if (s == TRTR_OK && config_out) *config_out = best;
     return s;

@@ -203,8 +203,26 @@ struct alignas(16) StepArgs {
     // pulse source (TRTR_SRC_PULSE), physical units
     C x0, y0, dx, dt;
     C dD_amp;               // D0 * D_amp
+    uint32_t rkey;          // stochastic rounding of the 2-byte storages: the step's key (sr_step_key)
     TimeFields<C> tf;       // pulse source uniforms of this step (a separate 16-byte block)
 };
+
+// Random bits of the stochastic rounding (TRTR_ROUND_STOCHASTIC): Wellons' "lowbias32"
+// integer hash (two multiply / xor-shift rounds, published with its measured avalanche bias).
+// The step's key hashes the step number; a node pair's key hashes its first node's index with
+// the step key, and population q of the pair takes that key rotated by 7 q bits.  The bits
+// depend on nothing but (node, step, q), so a run is the same however its steps are launched.
+__host__ __device__ __forceinline__ uint32_t sr_hash(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352dU;
+    x ^= x >> 15;
+    x *= 0x846ca68bU;
+    x ^= x >> 16;
+    return x;
+}
+__host__ __device__ __forceinline__ uint32_t sr_step_key(long step) {
+    return sr_hash((uint32_t)step * 0x9E3779B9U + (uint32_t)((unsigned long long)step >> 32) + 0x632BE5ABU);
+}
 
 enum MapId { kMapPop0 = 0, kMapPop1 = 1, kMapU = 2, kMapD = 3, kMapS = 4, kNumMaps = 5 };
 
@@ -297,7 +315,9 @@ cudaError_t launch_sample(trtr_ctx* ctx, const long* nodes_dev, int count, doubl
 cudaError_t launch_gather_edges(trtr_ctx* ctx, const double* phi_b_dev);
 cudaError_t launch_dirichlet(trtr_ctx* ctx, void* P);
 
-enum ReduceKind { kReduceMass = 0, kReducePulse = 1, kReduceField = 2, kReduceNonFinite = 3 };
+// kReduceBadField: the number of values of the device array `ref` (one per node) that are not
+// finite and positive (the check of a device-resident D).
+enum ReduceKind { kReduceMass = 0, kReducePulse = 1, kReduceField = 2, kReduceNonFinite = 3, kReduceBadField = 4 };
 
 PulseTime pulse_at(const Pulse& p, double t);
 

@@ -96,7 +96,9 @@ __global__ void __launch_bounds__(kThreads) rows_finish_kernel(double* out, cons
     }
 }
 
-// Device address of g_row_partials on the current device (resolved once per device).
+// Device address of g_row_partials on the current device, looked up once per device and kept
+// for the life of the process.  A cudaDeviceReset of that device (or any other end of its
+// primary context) frees the static array and leaves the kept address stale.
 cudaError_t partials_address(double** addr) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -119,15 +121,18 @@ extern "C" trtr_status trtr_phi_sums_noalloc(const double* g, int nx, int ny, co
                                              void* cuda_stream) {
     if (!g || !out || nx < 1 || ny < 1) return TRTR_EINVAL;
     if (ny > kMaxRows) return TRTR_EINVAL;
+    // An error left pending by earlier work of the caller is not this call's to take: report
+    // it without clearing it and enqueue nothing.
+    if (cudaPeekAtLastError() != cudaSuccess) return TRTR_ECUDA;
     double* partials = nullptr;
     if (partials_address(&partials) != cudaSuccess) {
-        cudaGetLastError();
+        cudaGetLastError();  // the lookup's own error (none was pending before it)
         return TRTR_ECUDA;
     }
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
     const int blocks = ny < 4096 ? ny : 4096;
     row_sums_kernel<<<blocks, kThreads, 0, stream>>>(partials, g, phi_ref, nx, ny);
     rows_finish_kernel<<<1, kThreads, 0, stream>>>(out, partials, ny);
-    if (cudaGetLastError() != cudaSuccess) return TRTR_ECUDA;
+    if (cudaGetLastError() != cudaSuccess) return TRTR_ECUDA;  // a launch error of this call
     return TRTR_OK;
 }

@@ -134,7 +134,7 @@ struct SmallPipe {
 #define TRTR_STEP_PDL 1  // launch the step with programmatic dependent launch
 #endif
 
-template <typename S, int SRC, int STAGES, class G>
+template <typename S, int SRC, int STAGES, class G, bool SR>
 __global__ void __launch_bounds__(G::THREADS, G::CTAS)
     step_kernel(const __grid_constant__ CUtensorMap mp, const __grid_constant__ CUtensorMap mu,
                 const __grid_constant__ CUtensorMap md, const __grid_constant__ CUtensorMap ms,
@@ -217,8 +217,8 @@ __global__ void __launch_bounds__(G::THREADS, G::CTAS)
         if (ok && j < ny) {
             const unsigned char* st = smem + s * T::STAGE;
             if constexpr (kPairs)
-                tile_row_pairs<S, SRC, kBX, kBY, kPairsPerLane, kTST, G::UNR>(st, r, lane, i0, j, a, sx, cx, sy, cy,
-                                                                              c0);
+                tile_row_pairs<S, SRC, kBX, kBY, kPairsPerLane, kTST, G::UNR, SR>(st, r, lane, i0, j, a, sx, cx, sy,
+                                                                                  cy, c0);
             else
                 tile_row_f64<SRC, kBX, kBY, 2 * kPairsPerLane, kTST>(st, r, lane, i0, j, a, c0);
         }
@@ -296,14 +296,14 @@ cudaError_t encode_typed(trtr_ctx* ctx) {
 }
 
 // One step from the population buffer described by src_map into dst, as step `step` (its
-// source terms and first-step rule).
-template <typename S, int SRC, class G>
+// source terms and first-step rule).  SR: stochastic rounding of the 2-byte storages.
+template <typename S, int SRC, class G, bool SR = false>
 cudaError_t launch_typed(trtr_ctx* ctx, const CUtensorMap& src_map, void* dst, long step) {
     using C = typename Store<S>::C;
     constexpr int kBX = G::BX, kBY = G::BY, kThreads = G::THREADS;
     using T = Tile<S, SRC, kBX, kBY>;
     constexpr int kStages = stages_for<S, SRC, G>();
-    auto kernel = step_kernel<S, SRC, kStages, G>;
+    auto kernel = step_kernel<S, SRC, kStages, G, SR>;
     const size_t smem = (size_t)kStages * T::STAGE + 128 + kStages * sizeof(uint64_t);
     static int configured_device = -1;
     static int ctas_per_sm = 1;
@@ -332,6 +332,7 @@ cudaError_t launch_typed(trtr_ctx* ctx, const CUtensorMap& src_map, void* dst, l
     a.y0 = C(ctx->p.y0);
     a.dx = C(ctx->p.dx);
     a.dt = C(ctx->p.dt);
+    a.rkey = sr_step_key(step);
     if (SRC == TRTR_SRC_PULSE) {
         const PulseTime tn = pulse_at(ctx->pulse, (double)step * ctx->p.dt);
         const PulseTime tp = pulse_at(ctx->pulse, (double)(step - 1) * ctx->p.dt);
@@ -363,6 +364,11 @@ cudaError_t launch_typed(trtr_ctx* ctx, const CUtensorMap& src_map, void* dst, l
 
 template <typename S, int SRC>
 cudaError_t launch_geom(trtr_ctx* ctx, const CUtensorMap& src_map, void* dst, long step) {
+    if constexpr (sizeof(S) == 2) {
+        if (ctx->p.rounding == TRTR_ROUND_STOCHASTIC)
+            return ctx->small_tiles ? launch_typed<S, SRC, SmallPipe<S, SRC>, true>(ctx, src_map, dst, step)
+                                    : launch_typed<S, SRC, Pipe<S, SRC>, true>(ctx, src_map, dst, step);
+    }
     return ctx->small_tiles ? launch_typed<S, SRC, SmallPipe<S, SRC>>(ctx, src_map, dst, step)
                             : launch_typed<S, SRC, Pipe<S, SRC>>(ctx, src_map, dst, step);
 }

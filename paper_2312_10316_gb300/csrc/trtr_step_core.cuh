@@ -7,6 +7,8 @@
 
 #include <cudaTypedefs.h>
 
+#include <string.h>
+
 #include <type_traits>
 
 #include "trtr_internal.cuh"
@@ -235,7 +237,6 @@ __device__ __forceinline__ void collide_node(const V g[kQ], V ux, V uy, V ax, V 
     const V E7 = vfma(V(T(-0.25)), Axy, Ed);
     const V O5 = vfma(V(T(0.25)), Txxy + Txyy, (m1x + m1y) * V(T(1.0 / 12.0)));
     const V O7 = vfma(V(T(0.25)), Txyy - Txxy, (m1x - m1y) * V(T(1.0 / 12.0)));
-    out[0] = vfma(V(T(-2.0 / 3.0)), Asum, m0 * V(T(4.0 / 9.0)));
     out[1] = E1 + O1;
     out[2] = E1 - O1;
     out[3] = E3 + O3;
@@ -244,6 +245,17 @@ __device__ __forceinline__ void collide_node(const V g[kQ], V ux, V uy, V ax, V 
     out[6] = E5 - O5;
     out[7] = E7 + O7;
     out[8] = E7 - O7;
+    if constexpr (OFS) {
+        out[0] = vfma(V(T(-2.0 / 3.0)), Asum, m0 * V(T(4.0 / 9.0)));
+    } else {
+        // The nine rebuilt values sum to m0 (the collision keeps phi + s, Sec. 2.2); the other
+        // eight are the pairs E +- O, so the rest population is m0 - 2 (E1 + E3 + E5 + E7), which
+        // equals w_0 m0 - (2/3)(A_xx + A_yy).  Formed the latter way the sum drifts: the rounded
+        // weights 4/9, 1/9, 1/36 add up to 1 + 7.5e-9 in FP32, which multiplied the mass by that
+        // every step.  Subtracting the four terms from m0 one at a time leaves a drift of a few
+        // 1e-11 per step (summing the eight stored values first: 3e-10).
+        out[0] = vfma(V(T(-2)), E1, vfma(V(T(-2)), E3, vfma(V(T(-2)), E5, vfma(V(T(-2)), E7, m0))));
+    }
 }
 
 template <typename C>
@@ -278,6 +290,7 @@ struct Pair<float> {
     static __device__ __forceinline__ F2 raw(float2 v) { return F2(v); }
     static __device__ __forceinline__ F2 raw(float a, float b) { return F2(a, b); }
     static __device__ __forceinline__ float2 encode_raw(F2 v) { return v.v; }
+    static __device__ __forceinline__ float2 encode_sr(F2 v, uint32_t) { return v.v; }
 };
 template <>
 struct Pair<__half> {
@@ -296,6 +309,14 @@ struct Pair<__half> {
     static __device__ __forceinline__ F2 raw(__half2 v) { return F2(__half22float2(v)); }
     static __device__ __forceinline__ F2 raw(__half a, __half b) { return F2(__half2float(a), __half2float(b)); }
     static __device__ __forceinline__ __half2 encode_raw(F2 v) { return __floats2half2_rn(v.v.x, v.v.y); }
+    // stochastic rounding of both offsets, 32 random bits (the first node in the low half)
+    static __device__ __forceinline__ __half2 encode_sr(F2 v, uint32_t rbits) {
+        uint32_t d;
+        asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(v.v.y), "f"(v.v.x), "r"(rbits));
+        __half2 h;
+        memcpy(&h, &d, sizeof(h));
+        return h;
+    }
 };
 template <>
 struct Pair<__nv_bfloat16> {
@@ -315,6 +336,13 @@ struct Pair<__nv_bfloat16> {
         return F2(__bfloat162float(a), __bfloat162float(b));
     }
     static __device__ __forceinline__ __nv_bfloat162 encode_raw(F2 v) { return __floats2bfloat162_rn(v.v.x, v.v.y); }
+    static __device__ __forceinline__ __nv_bfloat162 encode_sr(F2 v, uint32_t rbits) {
+        uint32_t d;
+        asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(v.v.y), "f"(v.v.x), "r"(rbits));
+        __nv_bfloat162 h;
+        memcpy(&h, &d, sizeof(h));
+        return h;
+    }
 };
 
 template <typename S, int SRC, int BX, int BY>
@@ -354,7 +382,9 @@ __device__ __forceinline__ void issue_tile(unsigned char* stage, uint64_t* bar, 
 // 16-byte aligned in both memories).  The lanes store the few columns past those, and the ghost
 // copies of edge nodes, directly.
 // UNR: the unroll factor of the pair loop (1: one pair at a time; NM: all pairs interleaved).
-template <typename S, int SRC, int BX, int BY, int NM = BX / 64, bool TST = false, int UNR = 1>
+// SR: the 2-byte storages round stochastically (TRTR_ROUND_STOCHASTIC), with the random bits of
+// sr_hash keyed by the node pair and a.rkey.
+template <typename S, int SRC, int BX, int BY, int NM = BX / 64, bool TST = false, int UNR = 1, bool SR = false>
 __device__ __forceinline__ void tile_row_pairs(const unsigned char* st, int r, int lane, int i0, int j,
                                                const StepArgs<float>& a, const F2* sx, const F2* cx, float sy,
                                                float cy, int c0 = 0) {
@@ -429,6 +459,12 @@ __device__ __forceinline__ void tile_row_pairs(const unsigned char* st, int r, i
         F2 out[kQ];
         // 2-byte storages: g and out stay offsets (the offset is folded into the moments)
         collide_node<F2, kOfs>(g, ux, uy, ax, ay, Dh, src, magic, w2f, a.tau2_fixed, out, F2(phi_ref));
+        uint32_t rk = 0;
+        if constexpr (SR) rk = sr_hash(((uint32_t)j * (uint32_t)nx + (uint32_t)i) ^ a.rkey);
+        auto enc = [&](int q) -> S2 {
+            if constexpr (SR) return P::encode_sr(out[q], __funnelshift_l(rk, rk, 7 * q));
+            else return P::encode_raw(out[q]);
+        };
 
         // a8: store P_i(x); edge nodes also write their periodic ghost copies (the one-wide frame
         // that the one-step kernel reads)
@@ -438,12 +474,12 @@ __device__ __forceinline__ void tile_row_pairs(const unsigned char* st, int r, i
             S* srow = const_cast<S*>(sp);
 #pragma unroll
             for (int q = 0; q < kQ; ++q)
-                *reinterpret_cast<S2*>(srow + q * T::PLANE_ELEMS + c) = P::encode_raw(out[q]);
+                *reinterpret_cast<S2*>(srow + q * T::PLANE_ELEMS + c) = enc(q);
             const int nb = bulk_cols<S>(nx - i0);
             if ((edge || c + 1 >= nb) && i < nx) {  // ghost copies, and the columns past the bulk copy
 #pragma unroll
                 for (int q = 0; q < kQ; ++q) {
-                    const S2 v = P::encode_raw(out[q]);
+                    const S2 v = enc(q);
                     const S v0 = reinterpret_cast<const S*>(&v)[0], v1 = reinterpret_cast<const S*>(&v)[1];
                     if (c >= nb) dst[q * pl + a.lp.at_g<kGhostP>(i, j)] = v0;
                     if (c + 1 >= nb && i + 1 < nx) dst[q * pl + a.lp.at_g<kGhostP>(i + 1, j)] = v1;
@@ -461,11 +497,11 @@ __device__ __forceinline__ void tile_row_pairs(const unsigned char* st, int r, i
 #endif
 #pragma unroll
             for (int q = 0; q < kQ; ++q)
-                *reinterpret_cast<S2*>(d0 + q * pl) = P::encode_raw(out[q]);
+                *reinterpret_cast<S2*>(d0 + q * pl) = enc(q);
         } else {
 #pragma unroll
             for (int q = 0; q < kQ; ++q) {
-                const S2 v = P::encode_raw(out[q]);
+                const S2 v = enc(q);
                 store_with_ghosts<1, kGhostP>(dst + q * pl, a.lp, i, j, reinterpret_cast<const S*>(&v)[0]);
                 if (i + 1 < nx) store_with_ghosts<1, kGhostP>(dst + q * pl, a.lp, i + 1, j, reinterpret_cast<const S*>(&v)[1]);
             }

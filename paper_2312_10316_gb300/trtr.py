@@ -25,6 +25,7 @@ TRTR_TAU2_MAGIC, TRTR_TAU2_FIXED = range(2)
 TRTR_GRAD_PERIODIC, TRTR_GRAD_ONESIDED_EDGE = range(2)
 TRTR_SRC_NONE, TRTR_SRC_FIELD, TRTR_SRC_PULSE = range(3)
 TRTR_BC_PERIODIC, TRTR_BC_DIRICHLET_NEE = range(2)
+TRTR_ROUND_STOCHASTIC, TRTR_ROUND_NEAREST = range(2)
 
 PRECISIONS = {"f64": TRTR_F64, "f32": TRTR_F32, "f16": TRTR_F16_OFS, "bf16": TRTR_BF16_OFS}
 
@@ -46,6 +47,7 @@ class trtr_params(ctypes.Structure):
         ("grad_mode", ctypes.c_int), ("src_mode", ctypes.c_int),
         ("check_every", ctypes.c_int),
         ("bc_mode", ctypes.c_int),
+        ("rounding", ctypes.c_int),
     ]
 
 
@@ -294,15 +296,26 @@ def trtr_launch_count(ctx) -> int:
 def trtr_phi_sums_noalloc(g, nx: int, ny: int, phi_ref, out, cuda_stream: int | None = None) -> int:
     """FP64 sums of phi over caller-owned device populations with no device allocation:
     g (9*ny*nx float64 CUDA tensor), phi_ref (ny*nx float64 CUDA tensor or None), out (3
-    float64 CUDA tensor).  Returns the status code (no exception), since callers of this
-    entry point often run where raising is not wanted."""
-    for name, t, count in (("g", g, 9 * nx * ny), ("out", out, 3)):
+    float64 CUDA tensor), each contiguous.
+
+    Arguments the kernels could not read safely (not a CUDA tensor, not float64, not
+    contiguous, or too few values) raise ValueError before anything reaches the library.
+    Otherwise the library's status code is returned as it is (TRTR_EINVAL for sizes beyond the
+    static scratch, TRTR_ECUDA for a failed launch), with no exception."""
+    import torch
+
+    def _ok(name, t, count):
         if not getattr(t, "is_cuda", False):
             raise ValueError(f"{name} must be a CUDA tensor")
+        if t.dtype != torch.float64 or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous float64 tensor (got {t.dtype})")
         if t.numel() < count:
             raise ValueError(f"{name} holds {t.numel()} values, needs {count}")
-    if phi_ref is not None and (not getattr(phi_ref, "is_cuda", False) or phi_ref.numel() < nx * ny):
-        raise ValueError("phi_ref must be a CUDA tensor of ny*nx values or None")
+
+    _ok("g", g, 9 * max(nx, 0) * max(ny, 0))
+    _ok("out", out, 3)
+    if phi_ref is not None:
+        _ok("phi_ref", phi_ref, max(nx, 0) * max(ny, 0))
     return int(lib.trtr_phi_sums_noalloc(g.data_ptr(), int(nx), int(ny),
                                          None if phi_ref is None else phi_ref.data_ptr(), out.data_ptr(), cuda_stream))
 
@@ -397,6 +410,7 @@ class Params:
     src_mode: int = TRTR_SRC_NONE
     check_every: int = 0
     bc_mode: int = TRTR_BC_PERIODIC
+    rounding: int = TRTR_ROUND_STOCHASTIC  # 2-byte storages only
 
     def to_c(self) -> trtr_params:
         return trtr_params(**{f.name: getattr(self, f.name) for f in dc_fields(self)})

@@ -46,3 +46,42 @@ def random_case(seed: int, nx: int, ny: int, dx: float = 0.1, dt: float = 0.02):
     S1 = rng.uniform(-1.0, 1.0, size=(ny, nx))
     S2 = rng.uniform(-1.0, 1.0, size=(ny, nx))
     return dict(g=g, ux=ux, uy=uy, D=D, S1=S1, S2=S2, dx=dx, dt=dt)
+
+
+def regions(nx: int, ny: int, tile=(128, 16), edge: int = 2):
+    """Boolean [ny][nx] masks of the node sets that break differently: the nodes within `edge` of
+    a grid edge (they pull across the periodic seam from the ghost frame and store ghost copies),
+    the last, ragged tile column and tile row of a `tile`-sized tiling, and the rest."""
+    j, i = np.mgrid[0:ny, 0:nx]
+    near = (i < edge) | (i >= nx - edge) | (j < edge) | (j >= ny - edge)
+    tx, ty = tile
+    ragged = np.zeros((ny, nx), dtype=bool)
+    if nx % tx:
+        ragged |= i >= nx - nx % tx
+    if ny % ty:
+        ragged |= j >= ny - ny % ty
+    return {"edge": near, "ragged tile": ragged & ~near, "interior": ~near & ~ragged}
+
+
+def assert_elementwise(got, ref, tol: float, what: str = "", tile=(128, 16)):
+    """Element by element: |got - ref| <= tol * max|ref| on every node of every plane, reported
+    separately for the edge nodes, the ragged last tile column/row and the interior (arrays
+    [ny][nx] or [planes][ny][nx]).  One wrong node, or a wrong edge row, fails this where a
+    relative L2 norm over the whole field could still pass."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    scale = float(np.max(np.abs(ref))) or 1.0
+    err = np.abs(got - ref) / scale
+    if err.ndim == 2:
+        err = err[None]
+    ny, nx = err.shape[-2:]
+    worst = {}
+    for name, mask in regions(nx, ny, tile).items():
+        if mask.any():
+            worst[name] = float(err[:, mask].max())
+    bad = {k: v for k, v in worst.items() if not v <= tol}
+    if bad:
+        q, jj, ii = np.unravel_index(int(np.nanargmax(err)), err.shape)
+        raise AssertionError(f"{what}: per-element error above {tol:g} x max|ref| in {bad}; "
+                             f"worst at plane {q}, node ({ii}, {jj}); all regions: {worst}")
+    return worst

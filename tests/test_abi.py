@@ -55,7 +55,9 @@ def test_binding_covers_the_header(T):
 
 
 def test_host_only_calls(T):
-    assert T.trtr_abi_version() == 2
+    assert T.trtr_abi_version() == 3
+    # zero-initialised parameters round the 2-byte storages stochastically
+    assert T.trtr_params().rounding == T.TRTR_ROUND_STOCHASTIC == 0 and T.Params(1, 1, 1.0, 1.0).rounding == 0
     ex, ey, w = T.trtr_d2q9()
     assert np.isclose(w.sum(), 1.0)
     assert np.array_equal(ex + 0, [0, 1, -1, 0, 0, 1, -1, 1, -1])
@@ -98,6 +100,7 @@ BAD = [
     dict(tau2_mode=2), dict(magic=0.0), dict(tau2_mode=1, tau2=0.5), dict(tau1_const=0.4),
     dict(grad_mode=5), dict(src_mode=3), dict(check_every=-1), dict(phi_ref=float("inf")),
     dict(nx=70000, ny=40000), dict(bc_mode=2), dict(bc_mode=1, nx=2), dict(bc_mode=1, ny=1),
+    dict(rounding=2), dict(rounding=-1),
 ]
 
 
@@ -130,9 +133,49 @@ def test_batch_rejects_bad_instances_before_touching_cuda(T):
     b = T.pulse_instance(W.Pulse(n=40), T.TRTR_F16_OFS)
     c = T.pulse_instance(W.Pulse(n=32), T.TRTR_F32)
     c.p.bc_mode = T.TRTR_BC_DIRICHLET_NEE
-    for bad in ([a, b], [T.pulse_instance(W.Pulse(n=32), T.TRTR_F64)], [], [a, c]):
+    d = T.pulse_instance(W.Pulse(n=40), T.TRTR_F16_OFS)
+    e = T.pulse_instance(W.Pulse(n=40), T.TRTR_F16_OFS, rounding=T.TRTR_ROUND_NEAREST)
+    f = T.pulse_instance(W.Pulse(n=40), T.TRTR_F16_OFS, rounding=5)
+    for bad in ([a, b], [T.pulse_instance(W.Pulse(n=32), T.TRTR_F64)], [], [a, c], [d, e], [f]):
         with pytest.raises(T.TrtrError) as e:
             T.trtr_batch_create(bad)
         assert e.value.status == T.TRTR_EINVAL
     assert T.trtr_batch_config_count() == 15
     assert "128x8" in T.trtr_batch_config_name(0) and T.trtr_batch_config_name(99) == "invalid"
+
+
+class _FakeDeviceTensor:
+    """Stands in for a CUDA tensor on a machine without a GPU: the binding's checks read only
+    these attributes; reaching the library (data_ptr) fails the test."""
+
+    is_cuda = True
+
+    def __init__(self, dtype, n, contiguous=True):
+        self.dtype, self._n, self._c = dtype, n, contiguous
+
+    def is_contiguous(self):
+        return self._c
+
+    def numel(self):
+        return self._n
+
+    def data_ptr(self):
+        raise AssertionError("an unchecked argument reached the library")
+
+
+def test_noalloc_binding_rejects_what_its_kernels_cannot_read(T):
+    torch = pytest.importorskip("torch")
+    nx, ny = 8, 4
+    good_g = _FakeDeviceTensor(torch.float64, 9 * nx * ny)
+    good_out = _FakeDeviceTensor(torch.float64, 3)
+    cases = [
+        (_FakeDeviceTensor(torch.float32, 9 * nx * ny), good_out, None),   # float32 populations
+        (good_g, _FakeDeviceTensor(torch.float32, 3), None),               # float32 out
+        (good_g, good_out, _FakeDeviceTensor(torch.float32, nx * ny)),     # float32 reference
+        (_FakeDeviceTensor(torch.float64, 9 * nx * ny, contiguous=False), good_out, None),
+        (_FakeDeviceTensor(torch.float64, 9 * nx * ny - 1), good_out, None),  # too short
+        (np.zeros(9 * nx * ny), good_out, None),                           # host array
+    ]
+    for g, out, ref in cases:
+        with pytest.raises(ValueError):
+            T.trtr_phi_sums_noalloc(g, nx, ny, ref, out)

@@ -1,0 +1,77 @@
+"""Accuracy of the reduced-precision storages over the configured run lengths (Eq. (14) of
+Sec. 2.2 advanced 10 000 steps), against the FP64 paths: the FP64 CPU oracle at 1024^2 and the
+GPU FP64 path (itself held to the oracle at 1e-12) at 4096^2.
+
+FP32 storage is held to a relative L2 error of 1e-5 in phi.  The errors measured on these
+workloads before the rest population closed the mass balance grew linearly with the step
+count (8.5e-6 after 1000 steps, 8.9e-5 after 10 000): the FP32 lattice weights sum to
+1 + 7.5e-9, and every step multiplied the mass by that."""
+import numpy as np
+import pytest
+
+from paper_2312_10316_gb300 import workloads as W
+
+from ._gpu_util import TOL_F32, TOL_F64, oracle_for_pulse, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2312_10316_gb300 import trtr as T  # noqa: E402
+
+
+def _pair_run(pulse, prec, steps, checkpoints=()):
+    """phi of `prec` and of the GPU FP64 path after `steps` (and at each checkpoint)."""
+    out = []
+    with T.pulse_solver(pulse, precision=prec) as s, T.pulse_solver(pulse, precision=T.TRTR_F64) as r:
+        m0 = r.mass()
+        done = 0
+        for c in list(checkpoints) + [steps]:
+            s.step(c - done)
+            r.step(c - done)
+            done = c
+            out.append((c, s.moments(), r.moments(), s.steps_per_launch))
+        return out, m0
+
+
+def test_f32_two_step_kernel_4096_against_the_f64_path():
+    """The bench's workload in its launch configuration (two steps per launch of the two-step
+    kernel): 4096^2, Courant 0.8, variable D, in-kernel manufactured source, 2000 steps."""
+    pulse = W.C2B_F32_4096
+    runs, _ = _pair_run(pulse, T.TRTR_F32, 2000, checkpoints=[200])
+    for steps, a, b, spl in runs:
+        assert spl == 2
+        err = rel_l2(a, b)
+        assert err <= TOL_F32 * steps / 2000, (steps, err)
+        # and node by node: no node off by more than a few times the global error
+        assert np.max(np.abs(a - b)) <= 10 * TOL_F32 * np.max(np.abs(b)), steps
+
+
+def test_f32_1024_ten_thousand_steps_against_the_f64_path():
+    """The 1024^2 workload at its configured length: 10 000 FP32 steps (two per launch), magic
+    tau2, variable D, manufactured source."""
+    pulse = W.C2A_F32_1024
+    runs, m0 = _pair_run(pulse, T.TRTR_F32, pulse.steps, checkpoints=[1000, 3000])
+    for steps, a, b, _ in runs:
+        err = rel_l2(a, b)
+        assert err <= TOL_F32, (steps, err)
+        # the total drifts by a few 1e-10 per step (2.7e-6 after 10 000 steps; 9.4e-5 with the
+        # rounded weights' 1 + 7.5e-9): well inside the L2 bound
+        assert abs(a.sum() - b.sum()) <= 0.5 * TOL_F32 * abs(b.sum()), steps
+
+
+@pytest.mark.slow
+def test_f32_and_f64_1024_ten_thousand_steps_against_the_oracle():
+    """The same 10 000 steps on the FP64 CPU oracle (all host cores, a few minutes): FP32
+    within 1e-5 and the GPU FP64 path within 1e-12 of it."""
+    pulse = W.C2A_F32_1024
+    o = oracle_for_pulse(pulse)
+    o.step(pulse.steps)
+    phi_o = o.phi()
+    with T.pulse_solver(pulse, precision=T.TRTR_F32) as s, T.pulse_solver(pulse, precision=T.TRTR_F64) as r:
+        s.step(pulse.steps)
+        r.step(pulse.steps)
+        assert rel_l2(r.moments(), phi_o) <= TOL_F64
+        assert rel_l2(s.moments(), phi_o) <= TOL_F32

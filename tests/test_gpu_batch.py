@@ -7,7 +7,7 @@ import pytest
 
 from paper_2312_10316_gb300 import workloads as W
 
-from ._gpu_util import TOL_F32, oracle_for_pulse, rel_l2
+from ._gpu_util import TOL_F32, assert_elementwise, oracle_for_pulse, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -64,6 +64,7 @@ def test_batch_with_pulse_source_against_oracle_and_single():
             o = oracle_for_pulse(p)
             o.step(steps)
             assert rel_l2(phi, o.phi()) <= TOL_F32
+            assert_elementwise(phi, o.phi(), TOL_F32, f"instance {k}")
             with T.pulse_solver(p, precision=T.TRTR_F32) as s:
                 s.step(steps)
                 # the time uniforms come from the device clock (double cos/sin) here and
@@ -85,6 +86,28 @@ def test_tune_restores_the_initial_state_and_picks_a_config():
         b.step(10)
         ref = _single_solution(pulses[1], T.TRTR_F32, 10)
         assert np.array_equal(b.instance(1).get_populations(), ref)
+
+
+def test_tune_at_step_zero_keeps_the_callers_own_state():
+    """Instances set by the caller (populations of their own, not the pulse's initial condition)
+    come back from the tuner's trial steps unchanged, and then step as single solves do."""
+    pulses = _uneven_pulses(seed=11, sizes=(64, 96))
+    own = [W.random_populations(40 + k, p.ny, p.nx, base=0.5, amp=0.2) for k, p in enumerate(pulses)]
+    with T.Batch([T.pulse_instance(p, T.TRTR_F32) for p in pulses]) as b:
+        for k in range(len(pulses)):
+            b.instance(k).set_populations(own[k])
+        g0 = [b.instance(k).get_populations().copy() for k in range(len(pulses))]
+        b.tune(4)
+        assert b.info()["step"] == 0
+        for k in range(len(pulses)):
+            assert np.array_equal(b.instance(k).get_populations(), g0[k]), k
+        b.step(9)
+        b.sync()
+        for k, p in enumerate(pulses):
+            with T.pulse_solver(p, precision=T.TRTR_F32) as s:
+                s.set_populations(own[k])
+                s.step(9)
+                assert np.array_equal(b.instance(k).get_populations(), s.get_populations()), k
 
 
 def test_instances_cannot_be_stepped_alone():

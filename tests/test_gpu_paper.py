@@ -9,7 +9,7 @@ import oracle
 from paper_2312_10316_gb300 import workloads as W
 
 from . import oracle_pins as P
-from ._gpu_util import TOL_F32, TOL_F64, random_case, rel_l2
+from ._gpu_util import TOL_F32, TOL_F64, assert_elementwise, random_case, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -94,12 +94,15 @@ def test_dirichlet_random_states(nx, ny, prec):
             s.set_dirichlet(phi_b if k % 2 else torch.from_numpy(phi_b).cuda())
             o.step(1)
             s.step(1)
-            assert rel_l2(s.get_populations(), o.get_g()) <= BC_TOL[prec], (k, prec)
+            gp, og = s.get_populations(), o.get_g()
+            assert rel_l2(gp, og) <= BC_TOL[prec], (k, prec)
+            assert_elementwise(gp, og, BC_TOL[prec], f"step {k} {prec}", tile=(64, 8))
             Sn = rng.uniform(-1.0, 1.0, size=(ny, nx))
             o.set_source(Sn)
             s.set_source(Sn)
         phi = s.moments()
         assert rel_l2(phi, o.phi()) <= BC_TOL[prec]
+        assert_elementwise(phi, o.phi(), BC_TOL[prec], "phi", tile=(64, 8))
         # the edge nodes hold the imposed values exactly (up to storage rounding)
         edge = np.zeros((ny, nx), dtype=bool)
         edge[0, :] = edge[-1, :] = edge[:, 0] = edge[:, -1] = True

@@ -5,13 +5,15 @@ Its node update is the one-step kernel's, so the populations after any number of
 equal those of one launch per step bit for bit; the one-step path is checked against the FP64
 oracle elsewhere, and one case here checks the two-step path against the oracle directly.
 """
+import math
+
 import numpy as np
 import pytest
 
 import oracle
 from paper_2312_10316_gb300 import workloads as W
 
-from ._gpu_util import TOL_F32, oracle_for_pulse, random_case, rel_l2
+from ._gpu_util import TOL_F32, assert_elementwise, oracle_for_pulse, random_case, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -112,7 +114,64 @@ def test_two_step_path_against_the_oracle():
     o = oracle_for_pulse(pulse)
     o.step(8)
     assert rel_l2(phi, o.phi()) <= TOL_F32
+    assert_elementwise(phi, o.phi(), TOL_F32, "phi", tile=(32, 8))
     assert launches == 1 + 4  # field packing, four two-step launches
+
+
+def _sampled_two_step_check(pulse, warm, nsamples, tol, seed=1):
+    """Full-size check of one two-step launch in the bench's launch configuration: after `warm`
+    steps (two per launch), the populations that one more launch writes at sampled nodes equal
+    two applications of the oracle's single-node update (Eq. (14)) to the GPU's own state: the
+    first to the pre-collision state of the 3 x 3 block around the node, the second to what the
+    node then pulls from that block (rotation u: d_y u_x = -omega, d_x u_y = omega exactly on
+    the lattice, the one-sided edge differences included)."""
+    rng = np.random.default_rng(seed)
+    n = pulse.nx
+    ex, ey, _ = T.trtr_d2q9()
+    edges = [0, 1, n - 2, n - 1]
+    centres = [(int(j), int(i)) for j, i in rng.integers(0, n, size=(nsamples, 2))]
+    centres += [(j, i) for j in edges for i in edges] + [(j, n // 2) for j in edges] + [(n // 2, i) for i in edges]
+    centres = sorted(set(centres))
+    block = [((j + dj) % n, (i + di) % n) for (j, i) in centres for dj in (-1, 0, 1) for di in (-1, 0, 1)]
+    bnodes = np.array([j * n + i for j, i in block])
+    op = oracle.SimParams(nx=n, ny=n, dx=pulse.dx, dt=pulse.dt, grad_mode=1, src_mode=2, omega=pulse.omega,
+                          xc=pulse.xc, yc=pulse.yc, sigma0=pulse.sigma0, D0=pulse.D0, D_amp=pulse.D_amp,
+                          tau2_mode=0 if pulse.tau2 is None else 1, tau2=pulse.tau2 or 1.0)
+    osim = oracle.Sim(oracle.SimParams(nx=1, ny=1, dx=pulse.dx, dt=pulse.dt, src_mode=2, omega=pulse.omega,
+                                       xc=pulse.xc, yc=pulse.yc, sigma0=pulse.sigma0, D0=pulse.D0,
+                                       D_amp=pulse.D_amp))
+    with T.pulse_solver(pulse, precision=T.TRTR_F32) as s:
+        assert s.steps_per_launch == 2 and warm % 2 == 0
+        s.step(warm)
+        g_n = s.sample(bnodes)
+        step_n, t_n = s.time()
+        l0 = s.launches
+        s.step(2)
+        assert s.launches - l0 == 1  # one launch of the two-step kernel
+        after = np.stack([s.sample([((j + ey[q]) % n) * n + (i + ex[q]) % n for (j, i) in centres])[:, q]
+                          for q in range(9)], axis=1)
+    du = [0.0, -pulse.omega, pulse.omega, 0.0]
+
+    def post(j, i, g, t):
+        x, y = pulse.x0 + i * pulse.dx, pulse.y0 + j * pulse.dx
+        D = pulse.D0 * (1 + pulse.D_amp * math.sin(math.pi * x) * math.sin(math.pi * y))
+        Sn, Sp = osim.pulse_source_at(x, y, t), osim.pulse_source_at(x, y, t - pulse.dt)
+        return oracle.node_post(op, g, -pulse.omega * y, pulse.omega * x, du, D, Sn, Sp)
+
+    ref = np.zeros_like(after)
+    for c, (j, i) in enumerate(centres):
+        p1 = {block[9 * c + k]: post(*block[9 * c + k], g_n[9 * c + k], t_n) for k in range(9)}
+        pre2 = np.array([p1[((j - ey[q]) % n, (i - ex[q]) % n)][q] for q in range(9)])
+        ref[c] = post(j, i, pre2, t_n + pulse.dt)
+    err = rel_l2(after, ref)
+    assert err <= tol, err
+    assert np.max(np.abs(after - ref)) <= tol * np.max(np.abs(ref))
+    return err
+
+
+@pytest.mark.parametrize("pulse", [W.C2A_F32_1024, W.C2B_F32_4096], ids=lambda p: p.name)
+def test_fullsize_sampled_two_step_launch(pulse):
+    _sampled_two_step_check(pulse, 100, 1500, 2e-6)
 
 
 def test_save_load_and_recorded_runs_keep_the_two_step_path_exact():
