@@ -50,7 +50,10 @@ DEFAULT_WORKLOAD = "pulse4096_f32_varD_mms"
 # batched workloads: 256 seeded pulses, square grids drawn from {64 ... 1024}, one launch per step
 BATCH_WORKLOADS = {"batch256_f32": ("f32", 4), "batch256_f16": ("f16", 2)}
 # gradient of the L2 misfit w.r.t. D through 2000 steps of a 512^2 pulse (discrete adjoint)
-ADJOINT_WORKLOADS = {"adjoint512_f32": "f32"}
+# (and the same at 2048^2, whose 151 MB per state do not fit in L2)
+ADJOINT_WORKLOADS = {"adjoint512_f32": "f32", "adjoint2048_f32": "f32"}
+ADJOINT_PULSES = {"adjoint512_f32": W.C5_ADJ_512,
+                  "adjoint2048_f32": W.Pulse(n=2048, courant=0.8, steps=2000, name="pulse2048_adjoint")}
 # the paper's Table 2 (Sec. 3.1): the fifteen present-model runs (N = 20..100, three kappa) of the
 # rotating pulse on [-2 pi, 2 pi]^2 with Dirichlet edges, through the library
 TABLE2_WORKLOADS = {"table2_f64": "f64", "table2_f32": "f32"}
@@ -549,6 +552,29 @@ def run_batch(args):
         s_.close()
     base_value = nodes * args.baseline_steps / (base_ms * 1e-3) / 1e9
 
+    # end to end through the C ABI: the batch built from host-side instance descriptions (the
+    # fields and initial conditions are the pulses' closed forms, made on the device), K steps,
+    # and every instance's phi read back into pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        import ctypes
+
+        out_host = [torch.empty((p.ny, p.nx), dtype=torch.float64, pin_memory=True) for p in pulses]
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        with T.Batch([T.pulse_instance(p, prec) for p in pulses], sh) as b2:
+            b2.set_config(best)
+            b2.step(args.steps)
+            for k in range(len(pulses)):
+                b2.instance(k).moments(out_host[k].numpy())
+        el = max_over_ranks(time.perf_counter() - t0, world)
+        e2e = {"value": nodes * args.steps * world / el / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": ctypes.sizeof(T.trtr_instance) * len(pulses) / args.steps,
+               "d2h_bytes_per_step": 8 * nodes / args.steps,
+               "scope": f"batch creation from host instance descriptions, {args.steps} steps, every "
+                        f"instance's phi device-to-host (pinned); bytes amortised over the steps"}
+
     if rank != 0:
         if world > 1:
             import torch.distributed as dist
@@ -576,6 +602,7 @@ def run_batch(args):
                      "bytes_per_node": bpn, "kernel": kernel, "steps_per_launch": spl},
         "gpu_launches": args.steps // spl + args.steps % spl,
         "clocks": clk,
+        "e2e": e2e,
         "cpu_baseline": None if args.no_cpu_baseline else cpu_baseline(
             max(pulses, key=lambda p: p.nx * p.ny), args.cpu_seconds),
         "batch": {"solves_per_s": round(solves_per_s, 3), "steps_per_solve": pulses[0].steps,
@@ -604,7 +631,7 @@ def run_adjoint(args):
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     prec = T.PRECISIONS[ADJOINT_WORKLOADS[args.workload]]
-    pulse = W.C5_ADJ_512
+    pulse = ADJOINT_PULSES[args.workload]
     n, steps = pulse.n, pulse.steps
     evals = max(1, min(args.steps, 10))
     f = W.fields(pulse)
@@ -675,7 +702,8 @@ def run_adjoint(args):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": f"{peak_kind} copy bandwidth",
                      "bytes_per_node": bpn, "kernel": "step2_kernel + step_kernel + adj_step_kernel",
-                     "note": "512^2: the 22 MB per step stay in L2 and each launch is latency-bound"},
+                     "note": ("512^2: the 22 MB per step stay in L2 and each launch is latency-bound" if n <= 512
+                              else f"{n}^2: {9 * 4 * n * n / 1e6:.0f} MB of populations per state, beyond L2")},
         "cpu_baseline": cpu,
     }
 

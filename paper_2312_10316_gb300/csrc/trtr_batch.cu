@@ -76,20 +76,7 @@ constexpr int kDefaultConfig = 9;  // 128 x 16 tiles, interleaved: what the tune
 
 // Pulse source uniforms of step n (t_n = n dt and t_{n-1}), in double, stored as float.
 __host__ __device__ inline TimeFields<float> time_fields(const Pulse& p, double dt, long long n) {
-    TimeFields<float> u;
-    const double tn = (double)n * dt, tp = (double)(n - 1) * dt;
-    const double cn = cos(p.omega * tn), sn = sin(p.omega * tn);
-    const double cp = cos(p.omega * tp), sp = sin(p.omega * tp);
-    const double s2n = p.sigma0 * p.sigma0 + 2.0 * p.D0 * tn, s2p = p.sigma0 * p.sigma0 + 2.0 * p.D0 * tp;
-    u.cx_n = (float)(p.xc * cn - p.yc * sn);
-    u.cy_n = (float)(p.xc * sn + p.yc * cn);
-    u.inv_s2_n = (float)(1.0 / s2n);
-    u.amp_n = (float)(p.sigma0 * p.sigma0 / s2n);
-    u.cx_p = (float)(p.xc * cp - p.yc * sp);
-    u.cy_p = (float)(p.xc * sp + p.yc * cp);
-    u.inv_s2_p = (float)(1.0 / s2p);
-    u.amp_p = (float)(p.sigma0 * p.sigma0 / s2p);
-    return u;
+    return pulse_time_fields<float>(p, dt, n);
 }
 
 // Asynchronous copy of `bytes` (a multiple of 16) from global to shared memory.

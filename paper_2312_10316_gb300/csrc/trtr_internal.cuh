@@ -177,12 +177,40 @@ struct Store<__nv_bfloat16> {
     static __device__ __forceinline__ __nv_bfloat16 encode(float v, float off) { return __float2bfloat16_rn(v - off); }
 };
 
-// Time-dependent uniforms of the pulse source (centre, 1/s^2, amplitude at t_n and t_{n-1}).
+// Time-dependent uniforms of the pulse source (centre, 1/s^2, amplitude term at t_n and
+// t_{n-1}); pulse_time_fields fills them.
 template <typename C>
 struct alignas(16) TimeFields {
-    C cx_n, cy_n, inv_s2_n, amp_n;     // at t_n
-    C cx_p, cy_p, inv_s2_p, amp_p;     // at t_{n-1} (t = -dt at the first step: the closed form)
+    C cx_n, cy_n, inv_s2_n, a_n;     // at t_n
+    C cx_p, cy_p, inv_s2_p, a_p;     // at t_{n-1} (t = -dt at the first step: the closed form)
 };
+
+// The uniforms of step n (t_n = n dt, t_{n-1} = t_n - dt), computed in double.  The amplitude
+// term: FP64 kernels a = s0^2 / s^2; FP32-computing kernels a_n = log2(1.5 dt s0^2 / s_n^4) and
+// a_p = log2(0.5 dt s0^2 / s_p^4), the step's weights of S^n and S^{n-1} in
+// dt S^n + dt/2 (S^n - S^{n-1}) and the 1/s^2 of S folded into the exponent (pulse_source_dt).
+template <typename C>
+__host__ __device__ inline TimeFields<C> pulse_time_fields(const Pulse& p, double dt, long long n) {
+    TimeFields<C> u;
+    const double tn = (double)n * dt, tp = (double)(n - 1) * dt;
+    const double cn = cos(p.omega * tn), sn = sin(p.omega * tn);
+    const double cp = cos(p.omega * tp), sp = sin(p.omega * tp);
+    const double s2n = p.sigma0 * p.sigma0 + 2.0 * p.D0 * tn, s2p = p.sigma0 * p.sigma0 + 2.0 * p.D0 * tp;
+    u.cx_n = (C)(p.xc * cn - p.yc * sn);
+    u.cy_n = (C)(p.xc * sn + p.yc * cn);
+    u.inv_s2_n = (C)(1.0 / s2n);
+    u.cx_p = (C)(p.xc * cp - p.yc * sp);
+    u.cy_p = (C)(p.xc * sp + p.yc * cp);
+    u.inv_s2_p = (C)(1.0 / s2p);
+    if (sizeof(C) == 8) {
+        u.a_n = (C)(p.sigma0 * p.sigma0 / s2n);
+        u.a_p = (C)(p.sigma0 * p.sigma0 / s2p);
+    } else {
+        u.a_n = (C)log2(1.5 * dt * p.sigma0 * p.sigma0 / (s2n * s2n));
+        u.a_p = (C)log2(0.5 * dt * p.sigma0 * p.sigma0 / (s2p * s2p));
+    }
+    return u;
+}
 
 // Uniform arguments of the fused step kernel (one launch per time step).  The static part
 // precedes tf and is a whole number of 16-byte chunks, so the batched kernel can copy the

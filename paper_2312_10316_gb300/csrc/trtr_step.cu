@@ -76,7 +76,9 @@ struct Geom<float, TRTR_SRC_FIELD> {
 template <int SRC>
 struct Geom<__half, SRC> {
     static constexpr int BY = 16, WPR = 1, CTAS = 1, STAGES = 3, ORDER = 0, TST = 0, SMALL_BELOW = 2;
-    static constexpr bool UNROLL = SRC == TRTR_SRC_NONE;  // both pairs at once: +5 % without a source
+    // both pairs at once: +5 % without a source; with the pulse source +5.5 % at 4096^2 once the
+    // source's weights went into its exponent and the offsets were rounded stochastically
+    static constexpr bool UNROLL = SRC != TRTR_SRC_FIELD;
 };
 template <int SRC>
 struct Geom<__nv_bfloat16, SRC> : Geom<__half, SRC> {};
@@ -88,6 +90,9 @@ struct Geom<__nv_bfloat16, SRC> : Geom<__half, SRC> {};
 #ifndef TRTR_STEP_TMA_STORE
 #define TRTR_STEP_TMA_STORE 0
 #endif
+#ifndef TRTR_STEP_UNROLL
+#define TRTR_STEP_UNROLL 0
+#endif
 template <typename S, int SRC>
 struct Sweep {
     static constexpr bool on = sizeof(S) == TRTR_STEP_SIZE && (TRTR_STEP_SRC < 0 || SRC == TRTR_STEP_SRC);
@@ -97,6 +102,7 @@ struct Sweep {
     static constexpr int STAGES = on ? TRTR_STEP_STAGES : Geom<S, SRC>::STAGES;
     static constexpr int ORDER = on ? TRTR_STEP_ORDER : Geom<S, SRC>::ORDER;
     static constexpr int TST = on ? TRTR_STEP_TMA_STORE : Geom<S, SRC>::TST;
+    static constexpr bool UNROLL = on ? TRTR_STEP_UNROLL != 0 : Geom<S, SRC>::UNROLL;
 };
 #else
 template <typename S, int SRC>
@@ -111,7 +117,7 @@ struct Pipe {
     static constexpr bool TST = Sweep<S, SRC>::TST != 0 && WPR == 1;
     static constexpr int THREADS = 32 * BY * WPR;
     static constexpr int PAIRS = BX / 64 / WPR;  // node pairs per lane (FP64: 2 PAIRS nodes)
-    static constexpr int UNR = Geom<S, SRC>::UNROLL ? PAIRS : 1;
+    static constexpr int UNR = Sweep<S, SRC>::UNROLL ? PAIRS : 1;
     static_assert(BY >= 1 && CTAS >= 1 && STAGES >= 1 && THREADS <= 1024, "pipeline geometry");
     static_assert((WPR == 1 || WPR == 2) && PAIRS >= 1, "warps per row");
 };
@@ -334,15 +340,12 @@ cudaError_t launch_typed(trtr_ctx* ctx, const CUtensorMap& src_map, void* dst, l
     a.dt = C(ctx->p.dt);
     a.rkey = sr_step_key(step);
     if (SRC == TRTR_SRC_PULSE) {
-        const PulseTime tn = pulse_at(ctx->pulse, (double)step * ctx->p.dt);
-        const PulseTime tp = pulse_at(ctx->pulse, (double)(step - 1) * ctx->p.dt);
         a.dD_amp = C(ctx->pulse.D0 * ctx->pulse.D_amp);
-        a.tf.cx_n = C(tn.cx); a.tf.cy_n = C(tn.cy); a.tf.inv_s2_n = C(tn.inv_s2); a.tf.amp_n = C(tn.amp);
-        a.tf.cx_p = C(tp.cx); a.tf.cy_p = C(tp.cy); a.tf.inv_s2_p = C(tp.inv_s2); a.tf.amp_p = C(tp.amp);
+        a.tf = pulse_time_fields<C>(ctx->pulse, ctx->p.dt, step);
     } else {
         a.dD_amp = C(0);
-        a.tf.cx_n = a.tf.cy_n = a.tf.inv_s2_n = a.tf.amp_n = C(0);
-        a.tf.cx_p = a.tf.cy_p = a.tf.inv_s2_p = a.tf.amp_p = C(0);
+        a.tf.cx_n = a.tf.cy_n = a.tf.inv_s2_n = a.tf.a_n = C(0);
+        a.tf.cx_p = a.tf.cy_p = a.tf.inv_s2_p = a.tf.a_p = C(0);
     }
     const long ntiles = (long)((ctx->lp.nx + kBX - 1) / kBX) * ((ctx->lp.ny + kBY - 1) / kBY);
     const long cap = (long)ctx->num_sms * ctas_per_sm;

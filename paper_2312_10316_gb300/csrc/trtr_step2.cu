@@ -182,17 +182,9 @@ cudaError_t launch2_typed(trtr_ctx* ctx, const CUtensorMap& src_map, void* dst, 
     a.dx = (float)ctx->p.dx;
     a.dt = (float)ctx->p.dt;
     if (SRC == TRTR_SRC_PULSE) {
-        const long n = step;
-        const PulseTime t0 = pulse_at(ctx->pulse, (double)(n - 1) * ctx->p.dt);
-        const PulseTime t1 = pulse_at(ctx->pulse, (double)n * ctx->p.dt);
-        const PulseTime t2 = pulse_at(ctx->pulse, (double)(n + 1) * ctx->p.dt);
         a.dD_amp = (float)(ctx->pulse.D0 * ctx->pulse.D_amp);
-        auto put = [](TimeFields<float>& tf, const PulseTime& tn, const PulseTime& tp) {
-            tf.cx_n = (float)tn.cx; tf.cy_n = (float)tn.cy; tf.inv_s2_n = (float)tn.inv_s2; tf.amp_n = (float)tn.amp;
-            tf.cx_p = (float)tp.cx; tf.cy_p = (float)tp.cy; tf.inv_s2_p = (float)tp.inv_s2; tf.amp_p = (float)tp.amp;
-        };
-        put(a.tf, t1, t0);
-        put(args.tf2, t2, t1);
+        a.tf = pulse_time_fields<float>(ctx->pulse, ctx->p.dt, step);
+        args.tf2 = pulse_time_fields<float>(ctx->pulse, ctx->p.dt, step + 1);
     }
     const long ntiles = (long)((ctx->lp.nx + G::T::X - 1) / G::T::X) * ((ctx->lp.ny + G::T::Y - 1) / G::T::Y);
     const long cap = (long)ctx->num_sms * ctas_per_sm;

@@ -88,21 +88,31 @@ __device__ __forceinline__ F2 pair_source(const StepArgs<float>& a, const TimeFi
     const F2 dD = F2(a.dD_amp * sy) * sxm;
     const F2 dDx = F2(a.dD_amp * 3.14159265358979323846f * sy) * cxm;
     const F2 dDy = F2(a.dD_amp * 3.14159265358979323846f * cy) * sxm;
-    const F2 Sn = pulse_source(x, y, F2(tf.cx_n), F2(tf.cy_n), F2(tf.inv_s2_n), F2(tf.amp_n), dD, dDx, dDy);
-    const F2 Sp = pulse_source(x, y, F2(tf.cx_p), F2(tf.cy_p), F2(tf.inv_s2_p), F2(tf.amp_p), dD, dDx, dDy);
-    return F2(a.dt) * vfma(F2(1.5f), Sn, F2(-0.5f) * Sp);
+    return pulse_source_dt(x, y, tf, dD, dDx, dDy);
 }
 
 // The TMA loads of one tile into `stage` (its barrier armed by the caller): the population box of
 // depth 9 and the packed-field box of depth 5, x origin i0 - 4 (16-byte aligned), rows from
 // j0 - 2 and j0 - 1.
+// TRTR_STEP2_L2HINT = 1: the tile loads ask L2 to keep their lines (the neighbouring tiles read
+// the halo again) and the result stores to evict theirs first (sweeps; default off).
+#ifndef TRTR_STEP2_L2HINT
+#define TRTR_STEP2_L2HINT 0
+#endif
 template <class T>
 __device__ __forceinline__ void step2_issue(unsigned char* stage, uint64_t* bar, const CUtensorMap* mp,
                                             const CUtensorMap* mf, int i0, int j0, int gx) {
     const int x = i0 + gx - 4;
+#if TRTR_STEP2_L2HINT
+    const uint64_t keep = l2_evict_last();
+    if (tma_ok(stage, x, j0 + kGhostP - 2, 4)) tma_load_3d_hint(stage, mp, bar, x, j0 + kGhostP - 2, 0, keep);
+    if (tma_ok(stage + T::PopBytes, x, j0 + kGhostP - 1, 4))
+        tma_load_3d_hint(stage + T::PopBytes, mf, bar, x, j0 + kGhostP - 1, 0, keep);
+#else
     if (tma_ok(stage, x, j0 + kGhostP - 2, 4)) tma_load_3d(stage, mp, bar, x, j0 + kGhostP - 2, 0);
     if (tma_ok(stage + T::PopBytes, x, j0 + kGhostP - 1, 4))
         tma_load_3d(stage + T::PopBytes, mf, bar, x, j0 + kGhostP - 1, 0);
+#endif
 }
 
 // Step 1 over the tile's halo region R1, in place in the stage (thread tid of NT).
@@ -203,8 +213,14 @@ __device__ __forceinline__ void step2_second(const float* sp, const float* sf, i
                 continue;
             }
 #endif
+#if TRTR_STEP2_L2HINT
+            const uint64_t leave = l2_evict_first();
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) st_global_f2_hint(d0 + q * pl, out[q].v, leave);
+#else
 #pragma unroll
             for (int q = 0; q < kQ; ++q) *reinterpret_cast<float2*>(d0 + q * pl) = out[q].v;
+#endif
         } else {
 #pragma unroll
             for (int q = 0; q < kQ; ++q) {

@@ -92,6 +92,31 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
+// L2 eviction priorities (createpolicy): loads whose tiles neighbouring CTAs read again (the
+// halo) can ask to stay, stores that nothing in the launch reads again to leave first.
+__device__ __forceinline__ uint64_t l2_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void tma_load_3d_hint(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z,
+                                                 uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, "
+        "{%3, %4, %5}], [%2], %6;" ::"r"(smem_addr(dst)),
+        "l"(map), "r"(smem_addr(bar)), "r"(x), "r"(y), "r"(z), "l"(policy)
+        : "memory");
+}
+__device__ __forceinline__ void st_global_f2_hint(float* p, float2 v, uint64_t policy) {
+    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(v.x), "f"(v.y), "l"(policy)
+                 : "memory");
+}
+
 // Bulk copy of `bytes` (a multiple of 16) from shared to global memory, both addresses 16-byte
 // aligned; the async proxy reads the source, completion is tracked per thread in bulk
 // async-groups.
@@ -179,6 +204,32 @@ __device__ __forceinline__ V pulse_source(V x, V y, V cx, V cy, V inv_s2, V amp,
     const V e = amp * vexp(r2 * (V(T(-0.5)) * inv_s2));
     const V br = vfma(dD, vfma(r2, V(T(0)) - inv_s2, V(T(2))), vfma(dDx, rx, dDy * ry));
     return (e * inv_s2) * br;
+}
+
+// 2^a (the hardware's base-2 exponential; results below the normal range flush to zero).
+__device__ __forceinline__ float ex2(float a) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+
+// One time level of the source term, w S(x, t) with the level's weight w folded into lg (see
+// pulse_time_fields): by exp(z) = 2^(z log2 e),
+//   w S = 2^(lg - |r|^2 log2(e) / (2 s^2)) [grad D . r + (D - D0)(2 - |r|^2 / s^2)].
+__device__ __forceinline__ F2 pulse_level(F2 x, F2 y, float cx, float cy, float inv_s2, float lg, F2 dD, F2 dDx,
+                                          F2 dDy) {
+    const F2 rx = x - F2(cx), ry = y - F2(cy);
+    const F2 r2 = vfma(rx, rx, ry * ry);
+    const F2 z = vfma(r2, F2(-0.72134752044448170368f * inv_s2), F2(lg));  // -log2(e) / 2 = -0.7213...
+    const F2 br = vfma(dD, vfma(r2, F2(-inv_s2), F2(2.f)), vfma(dDx, rx, dDy * ry));
+    return F2(ex2(z.v.x), ex2(z.v.y)) * br;
+}
+
+// s = dt S^n + dt/2 (S^n - S^{n-1}) = 1.5 dt S^n - 0.5 dt S^{n-1} of the manufactured source
+// (a7, Eqs. (3) and (14)) for the FP32-computing kernels.
+__device__ __forceinline__ F2 pulse_source_dt(F2 x, F2 y, const TimeFields<float>& tf, F2 dD, F2 dDx, F2 dDy) {
+    return pulse_level(x, y, tf.cx_n, tf.cy_n, tf.inv_s2_n, tf.a_n, dD, dDx, dDy) -
+           pulse_level(x, y, tf.cx_p, tf.cy_p, tf.inv_s2_p, tf.a_p, dD, dDx, dDy);
 }
 
 // The node update of Eq. (14) in moment space; g: pre-collision populations, out: P_i(x).
@@ -451,9 +502,7 @@ __device__ __forceinline__ void tile_row_pairs(const unsigned char* st, int r, i
             const F2 dD = F2(a.dD_amp * sy) * sxm;
             const F2 dDx = F2(a.dD_amp * 3.14159265358979323846f * sy) * cxm;
             const F2 dDy = F2(a.dD_amp * 3.14159265358979323846f * cy) * sxm;
-            const F2 Sn = pulse_source(x, y, F2(a.tf.cx_n), F2(a.tf.cy_n), F2(a.tf.inv_s2_n), F2(a.tf.amp_n), dD, dDx, dDy);
-            const F2 Sp = pulse_source(x, y, F2(a.tf.cx_p), F2(a.tf.cy_p), F2(a.tf.inv_s2_p), F2(a.tf.amp_p), dD, dDx, dDy);
-            src = F2(a.dt) * vfma(F2(1.5f), Sn, F2(-0.5f) * Sp);
+            src = pulse_source_dt(x, y, a.tf, dD, dDx, dDy);
         }
 
         F2 out[kQ];
@@ -566,8 +615,8 @@ __device__ __forceinline__ void tile_row_f64(const unsigned char* st, int r, int
             const double dD = a.dD_amp * sx * sy;
             const double dDx = a.dD_amp * 3.14159265358979323846 * cx * sy;
             const double dDy = a.dD_amp * 3.14159265358979323846 * sx * cy;
-            const double Sn = pulse_source(x, y, a.tf.cx_n, a.tf.cy_n, a.tf.inv_s2_n, a.tf.amp_n, dD, dDx, dDy);
-            const double Sp = pulse_source(x, y, a.tf.cx_p, a.tf.cy_p, a.tf.inv_s2_p, a.tf.amp_p, dD, dDx, dDy);
+            const double Sn = pulse_source(x, y, a.tf.cx_n, a.tf.cy_n, a.tf.inv_s2_n, a.tf.a_n, dD, dDx, dDy);
+            const double Sp = pulse_source(x, y, a.tf.cx_p, a.tf.cy_p, a.tf.inv_s2_p, a.tf.a_p, dD, dDx, dDy);
             src = a.dt * fma(1.5, Sn, -0.5 * Sp);
         }
         double out[kQ];

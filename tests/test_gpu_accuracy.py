@@ -75,3 +75,27 @@ def test_f32_and_f64_1024_ten_thousand_steps_against_the_oracle():
         r.step(pulse.steps)
         assert rel_l2(r.moments(), phi_o) <= TOL_F64
         assert rel_l2(s.moments(), phi_o) <= TOL_F32
+
+
+HALF = {"f16": T.TRTR_F16_OFS, "bf16": T.TRTR_BF16_OFS}
+# stated relative L2 tolerances of the 2-byte storages (stochastic rounding, the default): the
+# error stays near its first-step level (measured 3.5e-4 / 2.4e-3 after 10 000 steps at 1024^2)
+HALF_TOL = {"f16": 1e-3, "bf16": 5e-3}
+
+
+@pytest.mark.parametrize("prec", ["f16", "bf16"])
+def test_half_1024_ten_thousand_steps_against_the_f64_path(prec):
+    pulse = W.C2A_F32_1024
+    runs, _ = _pair_run(pulse, HALF[prec], pulse.steps, checkpoints=[1000])
+    for steps, a, b, _ in runs:
+        assert rel_l2(a, b) <= HALF_TOL[prec], (steps, rel_l2(a, b))
+        assert np.max(np.abs(a - b)) <= 10 * HALF_TOL[prec] * np.max(np.abs(b)), steps
+
+
+@pytest.mark.parametrize("prec", ["f16", "bf16"])
+def test_half_8192_full_size_multistep_against_the_f64_path(prec):
+    """The 8192^2 precision workload in the bench's launch configuration, 1000 steps."""
+    pulse = W.C3_HALF_8192
+    runs, _ = _pair_run(pulse, HALF[prec], 1000)
+    for steps, a, b, _ in runs:
+        assert rel_l2(a, b) <= HALF_TOL[prec], (steps, rel_l2(a, b))
