@@ -132,9 +132,9 @@ trtr_status trtr_destroy(trtr_ctx* ctx);
 /* Copies in the coefficient fields u_x, u_y and D (= kappa(x), Eq. (1)); D may be NULL when
  * tau1_const > 0.  S (may be NULL) sets the source field for TRTR_SRC_FIELD as by
  * trtr_set_source.  tau1 = 1/2 + 3 D dt / dx^2 must exceed 1/2 at every node: D must be
- * finite and > 0 everywhere, else TRTR_EINVAL with the fields unchanged (host input is checked
- * on the host; device input by a reduction on the context's stream, so the call then
- * synchronises).  Fields persist until set again. */
+ * finite and > 0 everywhere, else TRTR_EINVAL with the fields unchanged (checked by a reduction
+ * over the device copy on the context's stream, so the call synchronises when D is given).
+ * Fields persist until set again. */
 trtr_status trtr_set_fields(trtr_ctx* ctx, const double* ux, const double* uy, const double* D,
                             const double* S, int on_device);
 

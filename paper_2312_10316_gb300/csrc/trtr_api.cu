@@ -384,18 +384,13 @@ trtr_status trtr_set_fields(trtr_ctx* ctx, const double* ux, const double* uy, c
     if (!D && !(ctx->p.tau1_const > 0.0)) return fail(ctx, TRTR_EINVAL, "D is required unless tau1_const > 0");
     if (S && ctx->p.src_mode != TRTR_SRC_FIELD) return fail(ctx, TRTR_EINVAL, "S given but src_mode is not FIELD");
     const size_t n = n_nodes(ctx);
-    if (!on_device && D && !(ctx->p.tau1_const > 0.0)) {
-        for (size_t k = 0; k < n; ++k)
-            if (!(D[k] > 0.0) || !isfinite(D[k]))
-                return fail(ctx, TRTR_EINVAL, "D must be > 0 and finite at every node (node %zu: %g)", k, D[k]);
-    }
     const double *dux, *duy, *dD = nullptr;
     trtr_status s = on_device ? TRTR_OK : ensure_tmp(ctx, 3 * n);
     if (s == TRTR_OK) s = stage_in(ctx, ux, n, on_device, 0, &dux);
     if (s == TRTR_OK) s = stage_in(ctx, uy, n, on_device, 1, &duy);
     if (s == TRTR_OK && D) s = stage_in(ctx, D, n, on_device, 2, &dD);
     if (s != TRTR_OK) return s;
-    if (on_device && D && !(ctx->p.tau1_const > 0.0)) {  // the host check above, on the device
+    if (D && !(ctx->p.tau1_const > 0.0)) {  // D > 0 and finite everywhere, checked on the device copy
         double r[2];
         s = reduce(ctx, trtr::kReduceBadField, dD, r);
         if (s != TRTR_OK) return s;

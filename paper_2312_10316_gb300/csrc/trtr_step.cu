@@ -168,6 +168,8 @@ __global__ void __launch_bounds__(G::THREADS, G::CTAS)
     const int stride = kOrder == 0 ? gridDim.x : 1;
     const int my_tiles = kOrder == 0 ? (first < ntiles ? (ntiles - 1 - first) / stride + 1 : 0)
                                      : (first < ntiles ? min(chunk, ntiles - first) : 0);
+    // tile k of this CTA (a division per tile measured 2 % faster here than the two-step
+    // kernel's TileCursor, which wins there)
     auto tile_x0 = [&](int k) {
         const int t = first + k * stride;
         return (kOrder == 1 ? t / nty : t % ntx) * kBX;
@@ -241,7 +243,7 @@ __global__ void __launch_bounds__(G::THREADS, G::CTAS)
         }
         if (tid == 0 && k + STAGES < my_tiles)
             issue_tile<S, SRC, kBX, kBY>(smem + s * T::STAGE, &full[s], &mp, &mu, &md, &ms, tile_x0(k + STAGES),
-                               tile_y0(k + STAGES), a);
+                                         tile_y0(k + STAGES), a);
     }
     if (kTST && lane == 0) bulk_wait_all();  // this warp's row copies have completed
 }

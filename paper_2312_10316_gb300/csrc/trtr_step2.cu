@@ -57,11 +57,15 @@ __global__ void __launch_bounds__(G::kThreads, G::kCtas)
     const int stride = TRTR_STEP2_ORDER ? 1 : (int)gridDim.x;
     const int my_tiles = TRTR_STEP2_ORDER ? (first < ntiles ? min(chunk, ntiles - first) : 0)
                                           : (first < ntiles ? (ntiles - 1 - first) / stride + 1 : 0);
-    auto tile_x0 = [&](int k) { return ((first + k * stride) % ntx) * T::X; };
-    auto tile_y0 = [&](int k) { return ((first + k * stride) / ntx) * T::Y; };
-    auto issue = [&](int k, int s) {
+    // tile k of this CTA: t = first + k stride at (t mod ntx, t div ntx), walked without a
+    // division per tile; `ahead` is the issuing thread's cursor (tile k + STAGES)
+    TileCursor cur, ahead;
+    cur.init(first, stride, ntx);
+    ahead.init(first, stride, ntx);
+    auto issue = [&](int s) {
         mbar_expect_tx(&full[s], T::TX);
-        step2_issue<T>(smem + s * T::Stage, &full[s], &mp, &mf, tile_x0(k), tile_y0(k), a.lp.gx);
+        step2_issue<T>(smem + s * T::Stage, &full[s], &mp, &mf, ahead.a * T::X, ahead.b * T::Y, a.lp.gx);
+        ahead.next();
     };
 
     if (tid == 0) {
@@ -73,11 +77,11 @@ __global__ void __launch_bounds__(G::kThreads, G::kCtas)
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     asm volatile("griddepcontrol.wait;" ::: "memory");
     if (tid == 0)
-        for (int k = 0; k < STAGES && k < my_tiles; ++k) issue(k, k);
+        for (int k = 0; k < STAGES && k < my_tiles; ++k) issue(k);
 
-    for (int k = 0; k < my_tiles; ++k) {
+    for (int k = 0; k < my_tiles; ++k, cur.next()) {
         const int s = k % STAGES;
-        const int i0 = tile_x0(k), j0 = tile_y0(k);
+        const int i0 = cur.a * T::X, j0 = cur.b * T::Y;
         const bool ok = mbar_wait_bounded(&full[s], (k / STAGES) & 1);
         if (!ok) s_abort = 1;
         float* sp = reinterpret_cast<float*>(smem + s * T::Stage);
@@ -94,7 +98,7 @@ __global__ void __launch_bounds__(G::kThreads, G::kCtas)
             }
             return;
         }
-        if (tid == 0 && k + STAGES < my_tiles) issue(k + STAGES, s);
+        if (tid == 0 && k + STAGES < my_tiles) issue(s);
     }
 }
 
@@ -147,6 +151,10 @@ __global__ void refresh_ghosts2_kernel(float* P, PlaneLayout L) {
     }
 }
 
+#ifndef TRTR_STEP2_PDL
+#define TRTR_STEP2_PDL 1  // launch with programmatic dependent launch (0: plain stream order; sweeps)
+#endif
+
 // One launch: two steps from the buffer described by src_map into dst (dst1: the intermediate
 // state too, or null), as steps `step` and `step + 1` (the pulse source's time levels).
 template <int SRC, class G, bool P1>
@@ -195,7 +203,7 @@ cudaError_t launch2_typed(trtr_ctx* ctx, const CUtensorMap& src_map, void* dst, 
     cfg.stream = ctx->stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    attr[0].val.programmaticStreamSerializationAllowed = TRTR_STEP2_PDL;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kernel, src_map, ctx->maps2[2], args);

@@ -94,10 +94,11 @@ __device__ __forceinline__ F2 pair_source(const StepArgs<float>& a, const TimeFi
 // The TMA loads of one tile into `stage` (its barrier armed by the caller): the population box of
 // depth 9 and the packed-field box of depth 5, x origin i0 - 4 (16-byte aligned), rows from
 // j0 - 2 and j0 - 1.
-// TRTR_STEP2_L2HINT = 1: the tile loads ask L2 to keep their lines (the neighbouring tiles read
-// the halo again) and the result stores to evict theirs first (sweeps; default off).
+// TRTR_STEP2_L2HINT = 1 (the default): the tile loads ask L2 to keep their lines (the
+// neighbouring tiles read the halo again) and the result stores to evict theirs first; measured
+// on the 4096^2 pulse: DRAM reads -2.3 %, launch -0.7 %.
 #ifndef TRTR_STEP2_L2HINT
-#define TRTR_STEP2_L2HINT 0
+#define TRTR_STEP2_L2HINT 1
 #endif
 template <class T>
 __device__ __forceinline__ void step2_issue(unsigned char* stage, uint64_t* bar, const CUtensorMap* mp,

@@ -163,6 +163,28 @@ __device__ __forceinline__ bool bulk_ok(const S* gdst, const void* src, int i0, 
     return true;
 }
 
+// Walks the linear tile indices t, t + stride, t + 2 stride, ... of a persistent CTA as
+// (t mod m, t div m) without a division per tile: one division at the start, then an add and a
+// carry per step (m: tiles per row of the order's rows).
+struct TileCursor {
+    int a, b, da, db, m;
+    __device__ __forceinline__ void init(int t, int stride, int m_) {
+        m = m_;
+        a = t % m;
+        b = t / m;
+        da = stride % m;
+        db = stride / m;
+    }
+    __device__ __forceinline__ void next() {
+        a += da;
+        b += db;
+        if (a >= m) {
+            a -= m;
+            ++b;
+        }
+    }
+};
+
 // ---- arithmetic types --------------------------------------------------------------------
 // FP32-computing storages work on pairs of adjacent nodes with the packed FP32 instructions
 // of sm_100-family SMs (two lanes of FP32 per FADD2 / FMUL2 / FFMA2); FP64 works per node.
@@ -510,9 +532,20 @@ __device__ __forceinline__ void tile_row_pairs(const unsigned char* st, int r, i
         collide_node<F2, kOfs>(g, ux, uy, ax, ay, Dh, src, magic, w2f, a.tau2_fixed, out, F2(phi_ref));
         uint32_t rk = 0;
         if constexpr (SR) rk = sr_hash(((uint32_t)j * (uint32_t)nx + (uint32_t)i) ^ a.rkey);
+#ifndef TRTR_SR_WORDS
+#define TRTR_SR_WORDS 9
+#endif
         auto enc = [&](int q) -> S2 {
-            if constexpr (SR) return P::encode_sr(out[q], __funnelshift_l(rk, rk, 7 * q));
-            else return P::encode_raw(out[q]);
+            if constexpr (SR) {
+                // random bits of population q: 9 words (the key rotated by 7 q), or 3 or 1 words shared
+                // by groups of populations (sweeps)
+                if (TRTR_SR_WORDS == 9) return P::encode_sr(out[q], __funnelshift_l(rk, rk, 7 * q));
+                if (TRTR_SR_WORDS == 3)
+                    return P::encode_sr(out[q], q < 3 ? rk : (q < 6 ? rk * 0x85EBCA6Bu : rk * 0xC2B2AE35u));
+                return P::encode_sr(out[q], rk);
+            } else {
+                return P::encode_raw(out[q]);
+            }
         };
 
         // a8: store P_i(x); edge nodes also write their periodic ghost copies (the one-wide frame
