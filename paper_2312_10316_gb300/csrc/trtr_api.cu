@@ -265,7 +265,7 @@ trtr_status trtr_create(const trtr_params* p, void* cuda_stream, trtr_ctx** out)
         {&ctx->tab_y, 2 * (size_t)p->ny * ctx->csize, true},
         {(void**)&ctx->scratch, 2 * (size_t)ctx->red_blocks * sizeof(double), false},
         {(void**)&ctx->dres, 4 * sizeof(double), false},
-        {(void**)&ctx->dflag, sizeof(int), true},
+        {(void**)&ctx->dflag, 4 * sizeof(int), true},  // the timeout flag, then the tile counters
         {(void**)&ctx->phib,
          p->bc_mode == TRTR_BC_DIRICHLET_NEE ? (size_t)trtr::edge_count(p->nx, p->ny) * sizeof(double) : 0, true},
         {&ctx->fld2, two_step ? 5 * ctx->lt.plane * sizeof(float) : 0, true},

@@ -221,6 +221,7 @@ struct alignas(16) StepArgs {
     const C* tab_x;         // [2][nx]: sin(pi x_i), cos(pi x_i)
     const C* tab_y;         // [2][ny]: sin(pi y_j), cos(pi y_j)
     int* flag;              // set when a bounded wait gives up
+    unsigned* tile_ctr;     // [next tile, CTAs done] of kernels that hand out tiles dynamically (zero between launches)
     PlaneLayout lp;         // populations
     PlaneLayout lf;         // fields
     int s_cur, s_prev;      // source buffer indices (TRTR_SRC_FIELD)
@@ -252,6 +253,13 @@ __host__ __device__ __forceinline__ uint32_t sr_step_key(long step) {
     return sr_hash((uint32_t)step * 0x9E3779B9U + (uint32_t)((unsigned long long)step >> 32) + 0x632BE5ABU);
 }
 
+// Programmatic dependent launch of the step kernels: only for launches of a few tiles per CTA,
+// where the launch latency it hides is a large part of the step.  On long launches it costs time
+// (measured on GB300 without events between the launches: the two-step kernel at 4096^2 0.360
+// against 0.346 ms, at 8192^2 1.97 against 1.41 ms; the one-step FP16 kernel at 8192^2 0.634
+// against 0.612 ms), and a launch that records an event after it does not overlap anyway.
+constexpr long kPdlMaxTilesPerCta = 8;
+
 enum MapId { kMapPop0 = 0, kMapPop1 = 1, kMapU = 2, kMapD = 3, kMapS = 4, kNumMaps = 5 };
 
 }  // namespace trtr
@@ -281,7 +289,7 @@ struct trtr_ctx {
     int red_blocks;
     double* dres;     // device result of the reductions (4 doubles)
     double* hres;     // pinned host copy
-    int* dflag;       // device timeout flag
+    int* dflag;       // device timeout flag; dflag[2], dflag[3]: tile counters of the step kernels
     double* dtmp;     // device staging for double I/O
     size_t dtmp_len;  // in doubles
     double* phib;     // Dirichlet values of the edge nodes (TRTR_BC_DIRICHLET_NEE)

@@ -57,15 +57,60 @@ __global__ void __launch_bounds__(G::kThreads, G::kCtas)
     const int stride = TRTR_STEP2_ORDER ? 1 : (int)gridDim.x;
     const int my_tiles = TRTR_STEP2_ORDER ? (first < ntiles ? min(chunk, ntiles - first) : 0)
                                           : (first < ntiles ? (ntiles - 1 - first) / stride + 1 : 0);
-    // tile k of this CTA: t = first + k stride at (t mod ntx, t div ntx), walked without a
-    // division per tile; `ahead` is the issuing thread's cursor (tile k + STAGES)
-    TileCursor cur, ahead;
-    cur.init(first, stride, ntx);
-    ahead.init(first, stride, ntx);
+    // The tile of each stage.  TRTR_STEP2_DYN = G > 0: thread 0 takes runs of G consecutive tiles
+    // of the row-major order from the context's counter whenever it needs the next tile, so that
+    // faster CTAs take more and the launch ends evenly; 0: tile k of this CTA is first + k stride,
+    // walked without a division per tile.  s_org[s] holds the origin of the tile loaded into
+    // stage s (x = -1: none left), written by thread 0 before the loads are issued and read by
+    // every thread STAGES - 1 barriers later.
+#ifndef TRTR_STEP2_DYN
+#define TRTR_STEP2_DYN 4  // measured on GB300 (4096^2 / 8192^2 pulse): static 97.0 / 95.2 GLUPS, runs
+                          // of 1: 108.9 / 113.5, 2: 112.2 / 117.7, 4: 112.4 / 120.7, 8: 109.4 / 119.3
+#endif
+    constexpr int kRun = TRTR_STEP2_DYN;
+    __shared__ int2 s_org[STAGES];
+    TileCursor ahead;  // thread 0: the next tile to load
+    int run_left = 0;  // thread 0 (dynamic): tiles left in the current run
+    bool more = true;  // thread 0 (dynamic): the counter has tiles left
+    int taken = 0;     // thread 0 (static): tiles of this CTA loaded so far
+    auto take = [&]() -> int2 {
+        if constexpr (kRun > 0) {
+            if (run_left == 0) {
+                if (!more) return make_int2(-1, 0);
+                const unsigned t = atomicAdd(a.tile_ctr, (unsigned)kRun);
+                if (t >= (unsigned)ntiles) {
+                    more = false;
+                    return make_int2(-1, 0);
+                }
+                ahead.init((int)t, 1, ntx);
+                run_left = min(kRun, ntiles - (int)t);
+            } else {
+                ahead.next();
+            }
+            --run_left;
+            return make_int2(ahead.a * T::X, ahead.b * T::Y);
+        } else {
+            if (taken == my_tiles) return make_int2(-1, 0);
+            if (taken++ > 0) ahead.next();
+            return make_int2(ahead.a * T::X, ahead.b * T::Y);
+        }
+    };
+    auto finish = [&]() {  // the last CTA of the launch sets the counter back to zero
+        if (kRun > 0 && tid == 0) {
+            __threadfence();
+            if (atomicAdd(a.tile_ctr + 1, 1u) == gridDim.x - 1) {
+                atomicExch(a.tile_ctr, 0u);
+                atomicExch(a.tile_ctr + 1, 0u);
+            }
+        }
+    };
     auto issue = [&](int s) {
-        mbar_expect_tx(&full[s], T::TX);
-        step2_issue<T>(smem + s * T::Stage, &full[s], &mp, &mf, ahead.a * T::X, ahead.b * T::Y, a.lp.gx);
-        ahead.next();
+        const int2 o = take();
+        s_org[s] = o;
+        if (o.x >= 0) {
+            mbar_expect_tx(&full[s], T::TX);
+            step2_issue<T>(smem + s * T::Stage, &full[s], &mp, &mf, o.x, o.y, a.lp.gx);
+        }
     };
 
     if (tid == 0) {
@@ -76,12 +121,17 @@ __global__ void __launch_bounds__(G::kThreads, G::kCtas)
     __syncthreads();
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    if (tid == 0)
-        for (int k = 0; k < STAGES && k < my_tiles; ++k) issue(k);
+    if (tid == 0) {
+        if (kRun == 0) ahead.init(first, stride, ntx);
+        for (int s = 0; s < STAGES; ++s) issue(s);
+    }
+    __syncthreads();
 
-    for (int k = 0; k < my_tiles; ++k, cur.next()) {
+    for (int k = 0;; ++k) {
         const int s = k % STAGES;
-        const int i0 = cur.a * T::X, j0 = cur.b * T::Y;
+        const int2 o = s_org[s];
+        if (o.x < 0) break;
+        const int i0 = o.x, j0 = o.y;
         const bool ok = mbar_wait_bounded(&full[s], (k / STAGES) & 1);
         if (!ok) s_abort = 1;
         float* sp = reinterpret_cast<float*>(smem + s * T::Stage);
@@ -93,13 +143,16 @@ __global__ void __launch_bounds__(G::kThreads, G::kCtas)
         if (s_abort) {
             if (tid == 0) {
                 atomicExch(a.flag, 1);
-                for (int kk = k + 1; kk < my_tiles && kk < k + STAGES; ++kk)
-                    mbar_wait_bounded(&full[kk % STAGES], (kk / STAGES) & 1);
+                for (int kk = k + 1; kk < k + STAGES; ++kk)
+                    if (s_org[kk % STAGES].x >= 0) mbar_wait_bounded(&full[kk % STAGES], (kk / STAGES) & 1);
             }
+            finish();
             return;
         }
-        if (tid == 0 && k + STAGES < my_tiles) issue(s);
+        if (tid == 0) issue(s);
+        if constexpr (STAGES == 1) __syncthreads();  // s_org[0] is read again at once
     }
+    finish();
 }
 
 // Packed fields of the two-step kernel at every node of the two-wide ghost frame, from the
@@ -152,7 +205,7 @@ __global__ void refresh_ghosts2_kernel(float* P, PlaneLayout L) {
 }
 
 #ifndef TRTR_STEP2_PDL
-#define TRTR_STEP2_PDL 1  // launch with programmatic dependent launch (0: plain stream order; sweeps)
+#define TRTR_STEP2_PDL 1  // 0: never launch with programmatic dependent launch (sweeps)
 #endif
 
 // One launch: two steps from the buffer described by src_map into dst (dst1: the intermediate
@@ -179,6 +232,7 @@ cudaError_t launch2_typed(trtr_ctx* ctx, const CUtensorMap& src_map, void* dst, 
     a.tab_x = static_cast<const float*>(ctx->tab_x);
     a.tab_y = static_cast<const float*>(ctx->tab_y);
     a.flag = ctx->dflag;
+    a.tile_ctr = reinterpret_cast<unsigned*>(ctx->dflag + 2);
     a.lp = ctx->lp;
     a.lf = ctx->lt;
     a.tau2_fixed = ctx->p.tau2_mode == TRTR_TAU2_FIXED;
@@ -196,14 +250,15 @@ cudaError_t launch2_typed(trtr_ctx* ctx, const CUtensorMap& src_map, void* dst, 
     }
     const long ntiles = (long)((ctx->lp.nx + G::T::X - 1) / G::T::X) * ((ctx->lp.ny + G::T::Y - 1) / G::T::Y);
     const long cap = (long)ctx->num_sms * ctas_per_sm;
+    const long grid = ntiles < cap ? ntiles : cap;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(ntiles < cap ? ntiles : cap));
+    cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(G::kThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = ctx->stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = TRTR_STEP2_PDL;
+    attr[0].val.programmaticStreamSerializationAllowed = TRTR_STEP2_PDL && ntiles <= kPdlMaxTilesPerCta * grid;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kernel, src_map, ctx->maps2[2], args);
