@@ -33,9 +33,9 @@ namespace {
 using namespace core;
 
 struct BatchClock {
-    long long n;
-    unsigned int done;
-    unsigned int pad;
+    long long n;        // step of the instances
+    unsigned int done;  // CTAs of the running launch that have finished
+    unsigned int next;  // next work-list entry of a dynamically scheduled launch
 };
 
 template <typename C>
@@ -70,9 +70,14 @@ struct Geometry {
 // (the single-grid step's geometry).
 constexpr Geometry kGeoms[] = {{128, 8}, {64, 8}, {128, 4}, {128, 16}, {64, 16}};
 constexpr int kNumGeoms = 5;
-constexpr int kNumSchedules = 3;  // 0 interleaved, 1 chunked, 2 chunked with the largest instances first
+// 0 interleaved, 1 chunked, 2 chunked with the largest instances first, 3 dynamic (the CTAs take
+// the entries of the instance-by-instance work-list from a counter)
+constexpr int kNumSchedules = 4;
 constexpr int kNumConfigs = kNumGeoms * kNumSchedules;
-constexpr int kDefaultConfig = 9;  // 128 x 16 tiles, interleaved: what the tuner picked on GB300
+constexpr int kDefaultConfig = 3 * kNumSchedules + 3;  // 128 x 16 tiles, dynamic
+constexpr int kBatch2Run = 4;  // work-list entries per take of the two-step batch kernel
+// kernel mode of a schedule: 0 chunked, 1 interleaved, 2 dynamic
+constexpr int schedule_mode(int schedule) { return schedule == 0 ? 1 : (schedule == 3 ? 2 : 0); }
 
 // Pulse source uniforms of step n (t_n = n dt and t_{n-1}), in double, stored as float.
 __host__ __device__ inline TimeFields<float> time_fields(const Pulse& p, double dt, long long n) {
@@ -98,29 +103,49 @@ template <typename S, int SRC, int BX, int BY, int STAGES>
 __global__ void __launch_bounds__(32 * BY, min_blocks<BY>())
     batch_kernel(const InstanceDesc<typename Store<S>::C>* __restrict__ desc, const int4* __restrict__ tiles,
                  int ntiles, TimeFields<float>* tu, TimeFields2* tu2, BatchClock* clk, int count, int parity,
-                 int interleaved, int sr) {
+                 int mode, int sr) {
     using C = typename Store<S>::C;
     using T = Tile<S, SRC, BX, BY>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(16) StepArgs<C> sargs[STAGES];
-    __shared__ int s_abort, s_last;
+    __shared__ int4 s_t[STAGES];  // the work-list entry loaded into each stage (x = -1: none)
+    __shared__ int s_abort, s_last, s_more;
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) &
                                                            ~static_cast<uintptr_t>(127));
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * T::STAGE);
     const int tid = threadIdx.x, lane = tid & 31, r = tid >> 5;
 
+    // mode 0: a contiguous chunk of the work-list per CTA; 1: entries CTA + k grid; 2: thread 0
+    // takes the next entry from the batch's counter whenever it refills a stage (faster CTAs take
+    // more; the last CTA of the launch resets the counter)
     const int chunk = (ntiles + gridDim.x - 1) / gridDim.x;
-    const int first = interleaved ? blockIdx.x : blockIdx.x * chunk;
-    const int stride = interleaved ? gridDim.x : 1;
-    const int my_tiles = interleaved ? (first < ntiles ? (ntiles - 1 - first) / stride + 1 : 0)
-                                     : (first < ntiles ? min(chunk, ntiles - first) : 0);
+    const int first = mode == 1 ? blockIdx.x : blockIdx.x * chunk;
+    const int stride = mode == 1 ? gridDim.x : 1;
+    const int my_tiles = mode == 1 ? (first < ntiles ? (ntiles - 1 - first) / stride + 1 : 0)
+                                   : (first < ntiles ? min(chunk, ntiles - first) : 0);
+    auto take = [&](int k) -> int {  // thread 0: the work-list index of the CTA's k-th stage fill
+        if (mode == 2) {
+            if (!s_more) return -1;
+            const unsigned i = atomicAdd(&clk->next, 1u);
+            if (i < (unsigned)ntiles) return (int)i;
+            s_more = 0;
+            return -1;
+        }
+        return k < my_tiles ? first + k * stride : -1;
+    };
 
     // A stage's barrier completes after two arrivals and the TMA bytes: the producer's
     // arrival with the byte count goes out right before the tile loads; the second arrives
     // when its asynchronous copies of the instance's arguments into the stage's shared slot
     // land (cp.async.mbarrier.arrive), so the producer never waits on global memory.
     auto issue = [&](int k, int s) {
-        const int4 t = tiles[first + k * stride];  // (instance, i0, j0, gx_p | gx_f << 16)
+        const int idx = take(k);
+        if (idx < 0) {
+            s_t[s] = make_int4(-1, 0, 0, 0);
+            return;
+        }
+        const int4 t = tiles[idx];  // (instance, i0, j0, gx_p | gx_f << 16)
+        s_t[s] = t;
         const InstanceDesc<C>* d = desc + t.x;
         const int gxp = t.w & 0xffff, gxf = t.w >> 16;
         unsigned char* stage = smem + s * T::STAGE;
@@ -144,23 +169,22 @@ __global__ void __launch_bounds__(32 * BY, min_blocks<BY>())
 
     if (tid == 0) {
         s_abort = 0;
+        s_more = 1;
         for (int s = 0; s < STAGES; ++s) mbar_init(&full[s], 2);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     if (tid == 0)
-        for (int k = 0; k < STAGES && k < my_tiles; ++k) issue(k, k);
+        for (int k = 0; k < STAGES; ++k) issue(k, k);
     // stochastic rounding of the 2-byte storages: the key of this step (the clock is advanced
     // only after every CTA of the launch has finished its tiles)
     const uint32_t rkey = sr ? sr_step_key((long)*reinterpret_cast<volatile long long*>(&clk->n)) : 0u;
+    __syncthreads();  // s_t of the first stages
 
-    // the work-list entry of the next tile is fetched one iteration ahead (its latency hides
-    // behind the current tile)
-    int4 t_next = my_tiles > 0 ? tiles[first] : make_int4(0, 0, 0, 0);
-    for (int k = 0; k < my_tiles; ++k) {
+    for (int k = 0;; ++k) {
         const int s = k % STAGES;
-        const int4 t = t_next;
-        if (k + 1 < my_tiles) t_next = tiles[first + (k + 1) * stride];
+        const int4 t = s_t[s];
+        if (t.x < 0) break;
         const int i0 = t.y, j0 = t.z, j = j0 + r;
 
         F2 sx[BX / 64 > 0 ? BX / 64 : 1], cx[BX / 64 > 0 ? BX / 64 : 1];
@@ -205,12 +229,19 @@ __global__ void __launch_bounds__(32 * BY, min_blocks<BY>())
         if (s_abort) {
             if (tid == 0) {
                 atomicExch(desc[t.x].base[0].flag, 1);
-                for (int kk = k + 1; kk < my_tiles && kk < k + STAGES; ++kk)
-                    mbar_wait_bounded(&full[kk % STAGES], (kk / STAGES) & 1);
+                for (int kk = k + 1; kk < k + STAGES; ++kk)
+                    if (s_t[kk % STAGES].x >= 0) mbar_wait_bounded(&full[kk % STAGES], (kk / STAGES) & 1);
+                // the counters go back to zero when the last CTA is out (the step's results are void)
+                __threadfence();
+                if (atomicAdd(&clk->done, 1u) == gridDim.x - 1) {
+                    atomicExch(&clk->next, 0u);
+                    atomicExch(&clk->done, 0u);
+                }
             }
             return;
         }
-        if (tid == 0 && k + STAGES < my_tiles) issue(k + STAGES, s);
+        if (tid == 0) issue(k + STAGES, s);
+        if constexpr (STAGES == 1) __syncthreads();  // s_t[0] is read again at once
     }
 
     // The last CTA to finish advances the step clock and every instance's time uniforms.
@@ -230,6 +261,7 @@ __global__ void __launch_bounds__(32 * BY, min_blocks<BY>())
         __syncthreads();
         if (tid == 0) {
             clk->n = n1;
+            clk->next = 0;
             clk->done = 0;
             __threadfence();
         }
@@ -255,11 +287,34 @@ __global__ void __launch_bounds__(G::kThreads, G::kCtas)
                                                            ~static_cast<uintptr_t>(127));
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * T::Stage);
     const int tid = threadIdx.x;
-    const int first = blockIdx.x, stride = gridDim.x;
-    const int my_tiles = first < ntiles ? (ntiles - 1 - first) / stride + 1 : 0;
+    // thread 0 takes runs of kBatch2Run consecutive work-list entries from the batch's counter
+    // whenever it refills a stage (faster CTAs take more; the last CTA resets the counter)
+    __shared__ int4 s_t[STAGES];  // the entry loaded into each stage (x = -1: none)
+    int run_at = 0, run_left = 0;  // thread 0
+    bool more = true;              // thread 0
+    auto take = [&]() -> int {
+        if (run_left == 0) {
+            if (!more) return -1;
+            const unsigned i = atomicAdd(&clk->next, (unsigned)kBatch2Run);
+            if (i >= (unsigned)ntiles) {
+                more = false;
+                return -1;
+            }
+            run_at = (int)i;
+            run_left = min(kBatch2Run, ntiles - (int)i);
+        }
+        --run_left;
+        return run_at++;
+    };
 
-    auto issue = [&](int k, int s) {
-        const int4 t = tiles[first + k * stride];  // (instance, i0, j0, gx_p)
+    auto issue = [&](int s) {
+        const int idx = take();
+        if (idx < 0) {
+            s_t[s] = make_int4(-1, 0, 0, 0);
+            return;
+        }
+        const int4 t = tiles[idx];  // (instance, i0, j0, gx_p)
+        s_t[s] = t;
         const InstanceDesc2* d = desc + t.x;
         uint64_t* bar = &full[s];
         mbar_expect_tx(bar, T::TX);
@@ -280,13 +335,13 @@ __global__ void __launch_bounds__(G::kThreads, G::kCtas)
     }
     __syncthreads();
     if (tid == 0)
-        for (int k = 0; k < STAGES && k < my_tiles; ++k) issue(k, k);
+        for (int s = 0; s < STAGES; ++s) issue(s);
+    __syncthreads();  // s_t of the first stages
 
-    int4 t_next = my_tiles > 0 ? tiles[first] : make_int4(0, 0, 0, 0);
-    for (int k = 0; k < my_tiles; ++k) {
+    for (int k = 0;; ++k) {
         const int s = k % STAGES;
-        const int4 t = t_next;
-        if (k + 1 < my_tiles) t_next = tiles[first + (k + 1) * stride];
+        const int4 t = s_t[s];
+        if (t.x < 0) break;
         const bool ok = mbar_wait_bounded(&full[s], (k / STAGES) & 1);
         if (!ok) s_abort = 1;
         float* sp = reinterpret_cast<float*>(smem + s * T::Stage);
@@ -298,12 +353,18 @@ __global__ void __launch_bounds__(G::kThreads, G::kCtas)
         if (s_abort) {
             if (tid == 0) {
                 atomicExch(desc[t.x].base[0].flag, 1);
-                for (int kk = k + 1; kk < my_tiles && kk < k + STAGES; ++kk)
-                    mbar_wait_bounded(&full[kk % STAGES], (kk / STAGES) & 1);
+                for (int kk = k + 1; kk < k + STAGES; ++kk)
+                    if (s_t[kk % STAGES].x >= 0) mbar_wait_bounded(&full[kk % STAGES], (kk / STAGES) & 1);
+                __threadfence();
+                if (atomicAdd(&clk->done, 1u) == gridDim.x - 1) {
+                    atomicExch(&clk->next, 0u);
+                    atomicExch(&clk->done, 0u);
+                }
             }
             return;
         }
-        if (tid == 0 && k + STAGES < my_tiles) issue(k + STAGES, s);
+        if (tid == 0) issue(s);
+        if constexpr (STAGES == 1) __syncthreads();  // s_t[0] is read again at once
     }
 
     if (tid == 0) {
@@ -322,6 +383,7 @@ __global__ void __launch_bounds__(G::kThreads, G::kCtas)
         __syncthreads();
         if (tid == 0) {
             clk->n = n2;
+            clk->next = 0;
             clk->done = 0;
             __threadfence();
         }
@@ -399,11 +461,11 @@ struct BatchLaunch {
         (void)device;
         return cudaSuccess;
     }
-    static cudaError_t launch(trtr_batch* b, int parity, int interleaved) {
+    static cudaError_t launch(trtr_batch* b, int parity, int mode) {
         auto kernel = batch_kernel<S, SRC, BX, BY, kStages>;
         kernel<<<b->grid, 32 * BY, smem(), b->stream>>>(static_cast<const InstanceDesc<C>*>(b->d_desc), b->d_tiles,
                                                          b->ntiles, b->d_tu, b->d_tu2, b->d_clk, b->count, parity,
-                                                         interleaved, b->sr ? 1 : 0);
+                                                         mode, b->sr ? 1 : 0);
         return cudaGetLastError();
     }
     static bool encode_desc(trtr_batch* b, InstanceDesc<C>* h) {
@@ -456,13 +518,13 @@ cudaError_t with_geom(int geom, F&& f) {
 }
 
 template <typename S, int SRC>
-cudaError_t dispatch_geom(trtr_batch* b, int geom, int what, int parity, int interleaved, bool* enc_ok) {
+cudaError_t dispatch_geom(trtr_batch* b, int geom, int what, int parity, int mode, bool* enc_ok) {
     // what: 0 configure, 1 launch, 2 encode descriptors (built host-side, then copied)
     using C = typename Store<S>::C;
     return with_geom<S, SRC>(geom, [&](auto L) -> cudaError_t {
         using Launch = decltype(L);
         if (what == 0) return Launch::configure(b->ctx[0]->device, b->ctx[0]->num_sms, &b->grid);
-        if (what == 1) return Launch::launch(b, parity, interleaved);
+        if (what == 1) return Launch::launch(b, parity, mode);
         std::vector<InstanceDesc<C>> h(b->count);
         *enc_ok = Launch::encode_desc(b, h.data());
         if (!*enc_ok) return cudaErrorInvalidValue;
@@ -473,19 +535,19 @@ cudaError_t dispatch_geom(trtr_batch* b, int geom, int what, int parity, int int
     });
 }
 
-cudaError_t dispatch(trtr_batch* b, int geom, int what, int parity = 0, int interleaved = 0) {
+cudaError_t dispatch(trtr_batch* b, int geom, int what, int parity = 0, int mode = 0) {
     bool enc_ok = true;
     const bool pulse = b->src == TRTR_SRC_PULSE;
     switch (b->precision) {
         case TRTR_F32:
-            return pulse ? dispatch_geom<float, TRTR_SRC_PULSE>(b, geom, what, parity, interleaved, &enc_ok)
-                         : dispatch_geom<float, TRTR_SRC_NONE>(b, geom, what, parity, interleaved, &enc_ok);
+            return pulse ? dispatch_geom<float, TRTR_SRC_PULSE>(b, geom, what, parity, mode, &enc_ok)
+                         : dispatch_geom<float, TRTR_SRC_NONE>(b, geom, what, parity, mode, &enc_ok);
         case TRTR_F16_OFS:
-            return pulse ? dispatch_geom<__half, TRTR_SRC_PULSE>(b, geom, what, parity, interleaved, &enc_ok)
-                         : dispatch_geom<__half, TRTR_SRC_NONE>(b, geom, what, parity, interleaved, &enc_ok);
+            return pulse ? dispatch_geom<__half, TRTR_SRC_PULSE>(b, geom, what, parity, mode, &enc_ok)
+                         : dispatch_geom<__half, TRTR_SRC_NONE>(b, geom, what, parity, mode, &enc_ok);
         case TRTR_BF16_OFS:
-            return pulse ? dispatch_geom<__nv_bfloat16, TRTR_SRC_PULSE>(b, geom, what, parity, interleaved, &enc_ok)
-                         : dispatch_geom<__nv_bfloat16, TRTR_SRC_NONE>(b, geom, what, parity, interleaved, &enc_ok);
+            return pulse ? dispatch_geom<__nv_bfloat16, TRTR_SRC_PULSE>(b, geom, what, parity, mode, &enc_ok)
+                         : dispatch_geom<__nv_bfloat16, TRTR_SRC_NONE>(b, geom, what, parity, mode, &enc_ok);
         default:
             return cudaErrorInvalidValue;
     }
@@ -547,7 +609,7 @@ struct Batch2Launch {
         }
         return true;
     }
-    // descriptors and the work-list of two-step tiles (interleaved over the CTAs)
+    // descriptors and the work-list of two-step tiles (taken by the CTAs in runs, from a counter)
     static trtr_status setup(trtr_batch* b) {
         if (configure(b) != cudaSuccess) return TRTR_ECUDA;
         std::vector<InstanceDesc2> h(b->count);
@@ -628,7 +690,7 @@ trtr_status apply_config(trtr_batch* b, int config) {
 
 cudaError_t launch_one(trtr_batch* b, int parity) {
     const int geom = b->config / kNumSchedules, schedule = b->config % kNumSchedules;
-    return dispatch(b, geom, 1, parity, schedule == 0);
+    return dispatch(b, geom, 1, parity, schedule_mode(schedule));
 }
 
 // Two-step graph: parity 0 then parity 1.
@@ -663,7 +725,7 @@ trtr_status reset_clock(trtr_batch* b) {
     BatchClock c;
     c.n = b->step;
     c.done = 0;
-    c.pad = 0;
+    c.next = 0;
     if (cudaMemcpyAsync(b->d_tu, u.data(), u.size() * sizeof(TimeUniforms), cudaMemcpyHostToDevice, b->stream) !=
             cudaSuccess ||
         cudaMemcpyAsync(b->d_clk, &c, sizeof(c), cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
@@ -862,11 +924,11 @@ int trtr_batch_config_count(void) { return trtr::kNumConfigs; }
 
 const char* trtr_batch_config_name(int config) {
     static const char* names[trtr::kNumConfigs] = {
-        "tile 128x8, interleaved",  "tile 128x8, chunked", "tile 128x8, chunked largest-first",
-        "tile 64x8, interleaved",   "tile 64x8, chunked",  "tile 64x8, chunked largest-first",
-        "tile 128x4, interleaved",  "tile 128x4, chunked", "tile 128x4, chunked largest-first",
-        "tile 128x16, interleaved", "tile 128x16, chunked", "tile 128x16, chunked largest-first",
-        "tile 64x16, interleaved",  "tile 64x16, chunked",  "tile 64x16, chunked largest-first"};
+        "tile 128x8, interleaved",  "tile 128x8, chunked",  "tile 128x8, chunked largest-first",  "tile 128x8, dynamic",
+        "tile 64x8, interleaved",   "tile 64x8, chunked",   "tile 64x8, chunked largest-first",   "tile 64x8, dynamic",
+        "tile 128x4, interleaved",  "tile 128x4, chunked",  "tile 128x4, chunked largest-first",  "tile 128x4, dynamic",
+        "tile 128x16, interleaved", "tile 128x16, chunked", "tile 128x16, chunked largest-first", "tile 128x16, dynamic",
+        "tile 64x16, interleaved",  "tile 64x16, chunked",  "tile 64x16, chunked largest-first",  "tile 64x16, dynamic"};
     return config >= 0 && config < trtr::kNumConfigs ? names[config] : "invalid";
 }
 

@@ -233,6 +233,7 @@ struct alignas(16) StepArgs {
     C x0, y0, dx, dt;
     C dD_amp;               // D0 * D_amp
     uint32_t rkey;          // stochastic rounding of the 2-byte storages: the step's key (sr_step_key)
+    int dyn;                // the CTAs take their tiles from tile_ctr (long launches; kDynMinTilesPerCta)
     TimeFields<C> tf;       // pulse source uniforms of this step (a separate 16-byte block)
 };
 
@@ -259,6 +260,10 @@ __host__ __device__ __forceinline__ uint32_t sr_step_key(long step) {
 // against 0.346 ms, at 8192^2 1.97 against 1.41 ms; the one-step FP16 kernel at 8192^2 0.634
 // against 0.612 ms), and a launch that records an event after it does not overlap anyway.
 constexpr long kPdlMaxTilesPerCta = 8;
+// Tiles handed out from a counter: only for launches of more than this many tiles per CTA.  On
+// short launches the CTAs' few sequential atomic round trips cost more than the balancing gains
+// (the 512^2 adjoint's forward steps: 11 -> 18 us per two-step launch).
+constexpr long kDynMinTilesPerCta = 8;
 
 enum MapId { kMapPop0 = 0, kMapPop1 = 1, kMapU = 2, kMapD = 3, kMapS = 4, kNumMaps = 5 };
 

@@ -197,8 +197,9 @@ __global__ void __launch_bounds__(G::THREADS, G::CTAS)
     // the loads into stage s are issued and read by every thread STAGES - 1 barriers later.
     __shared__ int s_tile[STAGES];
     __shared__ int s_more;
+    const bool dyn = G::DYN && a.dyn;
     auto take = [&](int k) -> int {  // thread 0: the tile that the CTA's k-th stage fill loads
-        if constexpr (G::DYN) {
+        if (dyn) {
             if (!s_more) return -1;
             const unsigned t = atomicAdd(a.tile_ctr, 1u);
             if (t < (unsigned)ntiles) return (int)t;
@@ -214,7 +215,7 @@ __global__ void __launch_bounds__(G::THREADS, G::CTAS)
     auto tile_y0 = [&](int t) { return (kOrder == 1 ? t % nty : t / ntx) * kBY; };
     // the end of the CTA's work: the last CTA of the launch sets the counter back to zero
     auto finish = [&]() {
-        if (G::DYN && tid == 0) {
+        if (dyn && tid == 0) {
             __threadfence();
             if (atomicAdd(a.tile_ctr + 1, 1u) == gridDim.x - 1) {
                 atomicExch(a.tile_ctr, 0u);
@@ -400,6 +401,7 @@ cudaError_t launch_typed(trtr_ctx* ctx, const CUtensorMap& src_map, void* dst, l
     const long ntiles = (long)((ctx->lp.nx + kBX - 1) / kBX) * ((ctx->lp.ny + kBY - 1) / kBY);
     const long cap = (long)ctx->num_sms * ctas_per_sm;
     const int grid = (int)(ntiles < cap ? ntiles : cap);
+    a.dyn = ntiles > kDynMinTilesPerCta * grid;
     // launched with programmatic stream serialisation: the launch overlaps the tail of the
     // kernel before it, whose results the kernel waits for (griddepcontrol.wait)
     cudaLaunchConfig_t cfg = {};

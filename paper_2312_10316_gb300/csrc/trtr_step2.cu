@@ -68,13 +68,14 @@ __global__ void __launch_bounds__(G::kThreads, G::kCtas)
                           // of 1: 108.9 / 113.5, 2: 112.2 / 117.7, 4: 112.4 / 120.7, 8: 109.4 / 119.3
 #endif
     constexpr int kRun = TRTR_STEP2_DYN;
+    const bool dyn = kRun > 0 && a.dyn;
     __shared__ int2 s_org[STAGES];
     TileCursor ahead;  // thread 0: the next tile to load
     int run_left = 0;  // thread 0 (dynamic): tiles left in the current run
     bool more = true;  // thread 0 (dynamic): the counter has tiles left
     int taken = 0;     // thread 0 (static): tiles of this CTA loaded so far
     auto take = [&]() -> int2 {
-        if constexpr (kRun > 0) {
+        if (dyn) {
             if (run_left == 0) {
                 if (!more) return make_int2(-1, 0);
                 const unsigned t = atomicAdd(a.tile_ctr, (unsigned)kRun);
@@ -96,7 +97,7 @@ __global__ void __launch_bounds__(G::kThreads, G::kCtas)
         }
     };
     auto finish = [&]() {  // the last CTA of the launch sets the counter back to zero
-        if (kRun > 0 && tid == 0) {
+        if (dyn && tid == 0) {
             __threadfence();
             if (atomicAdd(a.tile_ctr + 1, 1u) == gridDim.x - 1) {
                 atomicExch(a.tile_ctr, 0u);
@@ -122,7 +123,7 @@ __global__ void __launch_bounds__(G::kThreads, G::kCtas)
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     asm volatile("griddepcontrol.wait;" ::: "memory");
     if (tid == 0) {
-        if (kRun == 0) ahead.init(first, stride, ntx);
+        if (!dyn) ahead.init(first, stride, ntx);
         for (int s = 0; s < STAGES; ++s) issue(s);
     }
     __syncthreads();
@@ -251,6 +252,7 @@ cudaError_t launch2_typed(trtr_ctx* ctx, const CUtensorMap& src_map, void* dst, 
     const long ntiles = (long)((ctx->lp.nx + G::T::X - 1) / G::T::X) * ((ctx->lp.ny + G::T::Y - 1) / G::T::Y);
     const long cap = (long)ctx->num_sms * ctas_per_sm;
     const long grid = ntiles < cap ? ntiles : cap;
+    a.dyn = ntiles > kDynMinTilesPerCta * grid;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(G::kThreads);

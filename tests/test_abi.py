@@ -140,7 +140,7 @@ def test_batch_rejects_bad_instances_before_touching_cuda(T):
         with pytest.raises(T.TrtrError) as e:
             T.trtr_batch_create(bad)
         assert e.value.status == T.TRTR_EINVAL
-    assert T.trtr_batch_config_count() == 15
+    assert T.trtr_batch_config_count() == 20
     assert "128x8" in T.trtr_batch_config_name(0) and T.trtr_batch_config_name(99) == "invalid"
 
 

@@ -139,10 +139,11 @@ def test_adjoint_512_2000_steps_against_central_differences():
     * FP64 path: the adjoint gradient equals central differences of the FP64 forward run
       (h = 1e-3 D) at 16 random nodes to 1e-5 relative (it is exact up to FD truncation).
     * FP32 path: its gradient differs from the FP64 one by the FP32 forward trajectory's
-      error, which is ~1e-5 of phi but enters through the misfit phi - phi_obs, itself only
-      ~1e-3 of phi here; relative L2 <= 1e-2 against the FP64 gradient, and <= 3e-2 per node
-      against the differences.  (FP64 arithmetic in the adjoint sweep over the same FP32
-      states gives the same error: the adjoint arithmetic is not the limit.)"""
+      error, 2.7e-7 of phi after 2000 steps, which enters through the misfit phi - phi_obs,
+      itself only 3e-3 of phi here: measured 2.0e-5 relative L2 against the FP64 gradient and
+      5.4e-5 per node against the differences, held to 2e-4 and 5e-4.  (Before the FP32 rest
+      population closed the mass balance, the trajectory drifted by ~1e-5 and these were ~1e-3
+      and ~1e-2.)"""
     pulse = W.C5_ADJ_512
     n, steps = pulse.n, pulse.steps
     f = W.fields(pulse)
@@ -168,7 +169,7 @@ def test_adjoint_512_2000_steps_against_central_differences():
             phi = s.moments()
             grads[prec] = s.adjoint(phi - phi_obs)
     g64, g32 = grads[T.TRTR_F64], grads[T.TRTR_F32]
-    assert rel_l2(g32, g64) <= 1e-2
+    assert rel_l2(g32, g64) <= 2e-4
 
     def J(Dv):
         return 0.5 * float(np.sum((forward(Dv, T.TRTR_F64) - phi_obs) ** 2))
@@ -186,4 +187,4 @@ def test_adjoint_512_2000_steps_against_central_differences():
         e64.append(abs(g64[j, i] - fd) / abs(fd))
         e32.append(abs(g32[j, i] - fd) / abs(fd))
     assert max(e64) <= 1e-5, e64
-    assert max(e32) <= 3e-2, e32
+    assert max(e32) <= 5e-4, e32
