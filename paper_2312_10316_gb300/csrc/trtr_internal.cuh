@@ -212,6 +212,12 @@ __host__ __device__ inline TimeFields<C> pulse_time_fields(const Pulse& p, doubl
     return u;
 }
 
+// Tile schedule bits of a step launch.  kSchedDynamic: the CTAs take their tiles from tile_ctr
+// (long launches; kDynMinTilesPerCta).  kSchedReverse: the launch walks the tile order from the
+// last tile to the first.  Consecutive launches on a context alternate the direction, so each
+// starts on the tiles that the launch before it wrote last, whose lines are still in L2.
+constexpr int kSchedDynamic = 1, kSchedReverse = 2;
+
 // Uniform arguments of the fused step kernel (one launch per time step).  The static part
 // precedes tf and is a whole number of 16-byte chunks, so the batched kernel can copy the
 // two parts into shared memory with asynchronous 16-byte copies.
@@ -233,7 +239,7 @@ struct alignas(16) StepArgs {
     C x0, y0, dx, dt;
     C dD_amp;               // D0 * D_amp
     uint32_t rkey;          // stochastic rounding of the 2-byte storages: the step's key (sr_step_key)
-    int dyn;                // the CTAs take their tiles from tile_ctr (long launches; kDynMinTilesPerCta)
+    int sched;              // kSchedDynamic | kSchedReverse (below)
     TimeFields<C> tf;       // pulse source uniforms of this step (a separate 16-byte block)
 };
 
@@ -310,6 +316,7 @@ struct trtr_ctx {
     trtr::Pulse pulse;
     long step;
     long launches;
+    unsigned sweeps;        // step launches so far: the parity sets their tile direction (kSchedReverse)
     trtr_adjoint_state* adj;  // recorded forward run (trtr_forward_record), or NULL
     char err[512];
 };

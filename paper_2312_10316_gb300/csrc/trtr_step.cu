@@ -193,21 +193,27 @@ __global__ void __launch_bounds__(G::THREADS, G::CTAS)
 
     // The tile of each stage: G::DYN hands out the tiles of the interleaved order from the
     // context's counter (thread 0 takes the next one whenever it refills a stage; -1: none left);
-    // otherwise tile k of this CTA is first + k stride.  s_tile[s] is written by thread 0 before
+    // otherwise tile k of this CTA is first + k stride.  A reversed launch takes tile
+    // ntiles - 1 - t in place of t.  s_tile[s] is written by thread 0 before
     // the loads into stage s are issued and read by every thread STAGES - 1 barriers later.
     __shared__ int s_tile[STAGES];
     __shared__ int s_more;
-    const bool dyn = G::DYN && a.dyn;
+    const bool dyn = G::DYN && (a.sched & kSchedDynamic);
+    const bool rev = (a.sched & kSchedReverse) != 0;
     auto take = [&](int k) -> int {  // thread 0: the tile that the CTA's k-th stage fill loads
+        int t = -1;
         if (dyn) {
-            if (!s_more) return -1;
-            const unsigned t = atomicAdd(a.tile_ctr, 1u);
-            if (t < (unsigned)ntiles) return (int)t;
-            s_more = 0;
-            return -1;
-        } else {
-            return k < my_tiles ? first + k * stride : -1;
+            if (s_more) {
+                const unsigned c = atomicAdd(a.tile_ctr, 1u);
+                if (c < (unsigned)ntiles)
+                    t = (int)c;
+                else
+                    s_more = 0;
+            }
+        } else if (k < my_tiles) {
+            t = first + k * stride;
         }
+        return t >= 0 && rev ? ntiles - 1 - t : t;
     };
     // tile t's origin (a division per tile measured 2 % faster here than the two-step kernel's
     // TileCursor, which wins there)
@@ -401,7 +407,7 @@ cudaError_t launch_typed(trtr_ctx* ctx, const CUtensorMap& src_map, void* dst, l
     const long ntiles = (long)((ctx->lp.nx + kBX - 1) / kBX) * ((ctx->lp.ny + kBY - 1) / kBY);
     const long cap = (long)ctx->num_sms * ctas_per_sm;
     const int grid = (int)(ntiles < cap ? ntiles : cap);
-    a.dyn = ntiles > kDynMinTilesPerCta * grid;
+    a.sched = (ntiles > kDynMinTilesPerCta * grid ? kSchedDynamic : 0) | (ctx->sweeps++ & 1u ? kSchedReverse : 0);
     // launched with programmatic stream serialisation: the launch overlaps the tail of the
     // kernel before it, whose results the kernel waits for (griddepcontrol.wait)
     cudaLaunchConfig_t cfg = {};

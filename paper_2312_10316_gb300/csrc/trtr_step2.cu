@@ -68,7 +68,8 @@ __global__ void __launch_bounds__(G::kThreads, G::kCtas)
                           // of 1: 108.9 / 113.5, 2: 112.2 / 117.7, 4: 112.4 / 120.7, 8: 109.4 / 119.3
 #endif
     constexpr int kRun = TRTR_STEP2_DYN;
-    const bool dyn = kRun > 0 && a.dyn;
+    const bool dyn = kRun > 0 && (a.sched & kSchedDynamic);
+    const bool rev = (a.sched & kSchedReverse) != 0;  // tile (a, b) stands for (ntx-1-a, nty-1-b)
     __shared__ int2 s_org[STAGES];
     TileCursor ahead;  // thread 0: the next tile to load
     int run_left = 0;  // thread 0 (dynamic): tiles left in the current run
@@ -89,12 +90,12 @@ __global__ void __launch_bounds__(G::kThreads, G::kCtas)
                 ahead.next();
             }
             --run_left;
-            return make_int2(ahead.a * T::X, ahead.b * T::Y);
         } else {
             if (taken == my_tiles) return make_int2(-1, 0);
             if (taken++ > 0) ahead.next();
-            return make_int2(ahead.a * T::X, ahead.b * T::Y);
         }
+        return rev ? make_int2((ntx - 1 - ahead.a) * T::X, (nty - 1 - ahead.b) * T::Y)
+                   : make_int2(ahead.a * T::X, ahead.b * T::Y);
     };
     auto finish = [&]() {  // the last CTA of the launch sets the counter back to zero
         if (dyn && tid == 0) {
@@ -252,7 +253,7 @@ cudaError_t launch2_typed(trtr_ctx* ctx, const CUtensorMap& src_map, void* dst, 
     const long ntiles = (long)((ctx->lp.nx + G::T::X - 1) / G::T::X) * ((ctx->lp.ny + G::T::Y - 1) / G::T::Y);
     const long cap = (long)ctx->num_sms * ctas_per_sm;
     const long grid = ntiles < cap ? ntiles : cap;
-    a.dyn = ntiles > kDynMinTilesPerCta * grid;
+    a.sched = (ntiles > kDynMinTilesPerCta * grid ? kSchedDynamic : 0) | (ctx->sweeps++ & 1u ? kSchedReverse : 0);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(G::kThreads);
