@@ -171,12 +171,13 @@ trtr_status trtr_init_equilibrium(trtr_ctx* ctx, const double* phi0, int on_devi
 
 /* Advances n >= 0 time steps of Eq. (14): one fused pull-stream + collide kernel per step on
  * the context's stream (plus the boundary pass with TRTR_BC_DIRICHLET_NEE), ping-pong buffers,
- * no host synchronisation (unless check_every).  With FP32 storage, periodic boundaries and
- * src_mode NONE or PULSE, pairs of steps run as one launch of the two-step kernel (the same
- * arithmetic, the same results bit for bit; populations read and written once per two steps;
- * see trtr_set_steps_per_launch); an odd last step, or a pair whose middle step is a
- * check_every point, runs one step per launch.  The step kernels use programmatic dependent
- * launch: each waits for the work before it on the stream before reading its results. */
+ * no host synchronisation (unless check_every).  With FP32 storage, or FP16 / BF16 offset
+ * storage on a grid of even nx, periodic boundaries and src_mode NONE or PULSE, pairs of steps
+ * run as one launch of the two-step kernel (the same arithmetic and roundings, the same results
+ * bit for bit; populations read and written once per two steps; see
+ * trtr_set_steps_per_launch); an odd last step, or a pair whose middle step is a check_every
+ * point, runs one step per launch.  Short launches use programmatic dependent launch: each
+ * waits for the work before it on the stream before reading its results. */
 trtr_status trtr_step(trtr_ctx* ctx, long n);
 
 /* k = 2 (the default): trtr_step uses the two-step kernel where it applies; k = 1: one step per
@@ -184,7 +185,8 @@ trtr_status trtr_step(trtr_ctx* ctx, long n);
 trtr_status trtr_set_steps_per_launch(trtr_ctx* ctx, int k);
 
 /* The steps one launch of trtr_step advances where it can on this context: 2 when the two-step
- * kernel applies (FP32, periodic, src_mode NONE or PULSE, not disabled), else 1. */
+ * kernel applies (FP32, or FP16 / BF16 with even nx; periodic; src_mode NONE or PULSE; not
+ * disabled), else 1. */
 trtr_status trtr_get_steps_per_launch(const trtr_ctx* ctx, int* k);
 
 /* phi(x, t_n) = sum_i g_i(x, t_n) of the pre-collision populations (B_0^neq = 0, Sec. 2.2),

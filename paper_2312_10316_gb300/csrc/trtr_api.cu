@@ -235,9 +235,13 @@ trtr_status trtr_create(const trtr_params* p, void* cuda_stream, trtr_ctx** out)
     ctx->lf = lf;
     ctx->S_cur = ctx->S_prev = -1;
     ctx->steps_per_launch = 2;
-    // the two-step kernel's packed fields (FP32 storage, periodic, no field source)
-    const bool two_step = p->precision == TRTR_F32 && p->bc_mode == TRTR_BC_PERIODIC &&
-                          p->src_mode != TRTR_SRC_FIELD && p->nx >= 2 && p->ny >= 2;
+    // the two-step kernel's packed fields (FP32 or 2-byte storage, periodic, no field source; the
+    // 2-byte kernel rounds the one-step kernel's node pairs, so nx is even there)
+    const bool two_step_storage =
+        p->precision == TRTR_F32 ||
+        ((p->precision == TRTR_F16_OFS || p->precision == TRTR_BF16_OFS) && p->nx % 2 == 0);
+    const bool two_step = two_step_storage && p->bc_mode == TRTR_BC_PERIODIC && p->src_mode != TRTR_SRC_FIELD &&
+                          p->nx >= 2 && p->ny >= 2;
     ctx->lt = trtr::make_layout(p->nx, p->ny, 4, trtr::kGhostP);
 
     cudaError_t e = cudaGetDevice(&ctx->device);

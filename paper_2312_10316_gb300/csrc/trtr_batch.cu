@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(G::kThreads, G::kCtas)
         const InstanceDesc2* d = desc + t.x;
         uint64_t* bar = &full[s];
         mbar_expect_tx(bar, T::TX);
-        step2_issue<T>(smem + s * T::Stage, bar, &d->mp[parity], &d->mf, t.y, t.z, t.w);
+        step2_issue<T>(smem + s * T::Stage, bar, &d->mp[parity], &d->mf, t.y, t.z, t.w, t.w);
         constexpr int kStatic = (int)(sizeof(StepArgs<float>) - sizeof(TimeFields<float>));
         cp_async_16(&sargs[s], &d->base[parity], kStatic);
         if (SRC == TRTR_SRC_PULSE) {
@@ -346,9 +346,9 @@ __global__ void __launch_bounds__(G::kThreads, G::kCtas)
         if (!ok) s_abort = 1;
         float* sp = reinterpret_cast<float*>(smem + s * T::Stage);
         const float* sf = reinterpret_cast<const float*>(smem + s * T::Stage + T::PopBytes);
-        if (ok) step2_first<SRC, T, NT>(sp, sf, t.y, t.z, sargs[s], sargs[s].tf, tid);
+        if (ok) step2_first<float, SRC, T, NT>(sp, sf, t.y, t.z, sargs[s], sargs[s].tf, tid);
         __syncthreads();  // step 1 complete (and s_abort visible)
-        if (ok && !s_abort) step2_second<SRC, T, NT>(sp, sf, t.y, t.z, sargs[s], stf2[s], tid);
+        if (ok && !s_abort) step2_second<float, SRC, T, NT>(sp, sf, t.y, t.z, sargs[s], stf2[s], tid);
         __syncthreads();  // stage s and its argument slot fully read
         if (s_abort) {
             if (tid == 0) {

@@ -1,30 +1,34 @@
 // trtr_step2.cu -- two time steps of the evolution equation (14) per launch (temporal blocking
-// of the fused TRT-R step), for FP32 storage, periodic boundaries and no source or the
-// manufactured pulse source.  The node update is the one-step kernel's (collide_node, the
-// same source and acceleration arithmetic), so two steps here give the bits of two one-step
+// of the fused TRT-R step), for FP32 storage or FP16 / BF16 offset storage (FP32 arithmetic),
+// periodic boundaries and no source or the manufactured pulse source.  The node update is the
+// one-step kernel's (collide_node, the same source and acceleration arithmetic, the same
+// rounding of the stored 2-byte values), so two steps here give the bits of two one-step
 // launches; what changes is the data movement: the populations are read and written once per
 // two steps.
 //
 // Tile: BX x BY output nodes (i0.., j0..).  One TMA box of depth 9 brings P (the previous
-// step's post-collision values) over columns [i0 - 4, i0 + BX + 4) and rows [j0 - 2, j0 + BY + 2),
-// one box of depth 5 the packed fields (uhat, a = uhat . grad uhat, Dh) over the rows
+// step's post-collision values) over columns [i0 - HX, i0 + BX + HX) (HX = 16 bytes of columns:
+// 4 FP32, 8 2-byte values) and rows [j0 - 2, j0 + BY + 2), one box of depth 5 the packed fields
+// (uhat, a = uhat . grad uhat, Dh) over the columns [i0 - 4, i0 + BX + 4) and the rows
 // [j0 - 1, j0 + BY + 1).  The population planes keep a two-wide ghost frame of periodic copies,
 // so the two-node halo is a plain tile read at the edges too.
 //   Step 1 runs on the halo region R1 = columns [i0 - 2, i0 + BX + 2) x rows [j0 - 1, j0 + BY + 1)
 //   (its outermost columns are computed and not used).  Node (r, c) of R1 pulls
-//   g_q = P_q(x - e_q) from the stage at (row r + 1 - ey_q, column c + 2 - ex_q); that slot is
-//   pulled by this node alone, so the node writes its post-collision value P1_q back into the
-//   same slot (in place, no second buffer).
+//   g_q = P_q(x - e_q) from the stage at (row r + 1 - ey_q, column c + HX - 2 - ex_q); that slot
+//   is pulled by this node alone, so the node writes its post-collision value P1_q back into
+//   the same slot (in place, no second buffer; 2-byte storages round it to the storage format
+//   as a one-step launch would store it).
 //   Step 2 runs on the output nodes: node (r2, c2) = R1 node (r2 + 1, c2 + 2) pulls
-//   P1_q(x - e_q) from (row r2 + 2 - 2 ey_q, column c2 + 4 - 2 ex_q) and stores P2 to global
+//   P1_q(x - e_q) from (row r2 + 2 - 2 ey_q, column c2 + HX - 2 ex_q) and stores P2 to global
 //   memory with its ghost copies (nodes within two of an edge).
 // Geometry (Geom2For): narrow tiles (32 columns; 8 rows with the pulse source, 16 without) and
 // several CTAs per SM with two stages each, so that while one CTA waits at the barrier between
 // its two steps the others compute (the kernel is latency-bound, not HBM-bound).
 // R1 nodes outside the grid are periodic images: their populations come from the ghost frame,
 // their fields from the packed fields' ghost frame (copies of the wrapped node, the acceleration
-// included, whatever the gradient mode), and their source from the wrapped node's coordinates,
-// so they compute exactly what the wrapped node computes.
+// included, whatever the gradient mode), their source from the wrapped node's coordinates and
+// their rounding bits from the wrapped node pair, so they compute exactly what the wrapped node
+// computes.
 #include "trtr_step2_core.cuh"
 
 namespace trtr {
@@ -32,7 +36,7 @@ namespace {
 
 using namespace core;
 
-template <int SRC, class G, bool P1>
+template <typename S, int SRC, class G, bool P1, bool SR>
 __global__ void __launch_bounds__(G::kThreads, G::kCtas)
     step2_kernel(const __grid_constant__ CUtensorMap mp, const __grid_constant__ CUtensorMap mf, const Step2Args args) {
     constexpr int STAGES = G::kStages, NT = G::kThreads;
@@ -111,7 +115,7 @@ __global__ void __launch_bounds__(G::kThreads, G::kCtas)
         s_org[s] = o;
         if (o.x >= 0) {
             mbar_expect_tx(&full[s], T::TX);
-            step2_issue<T>(smem + s * T::Stage, &full[s], &mp, &mf, o.x, o.y, a.lp.gx);
+            step2_issue<T>(smem + s * T::Stage, &full[s], &mp, &mf, o.x, o.y, a.lp.gx, a.lf.gx);
         }
     };
 
@@ -136,11 +140,12 @@ __global__ void __launch_bounds__(G::kThreads, G::kCtas)
         const int i0 = o.x, j0 = o.y;
         const bool ok = mbar_wait_bounded(&full[s], (k / STAGES) & 1);
         if (!ok) s_abort = 1;
-        float* sp = reinterpret_cast<float*>(smem + s * T::Stage);
-        const float* sf = reinterpret_cast<const float*>(smem + s * T::Stage + T::PopBytes);
-        if (ok) step2_first<SRC, T, NT>(sp, sf, i0, j0, a, a.tf, tid);
+        S* sp = reinterpret_cast<S*>(smem + s * T::Stage);
+        const float* sf = reinterpret_cast<const float*>(smem + s * T::Stage + T::FldOff);
+        if (ok) step2_first<S, SRC, T, NT, SR>(sp, sf, i0, j0, a, a.tf, tid);
         __syncthreads();  // P1 complete (and s_abort visible)
-        if (ok && !s_abort) step2_second<SRC, T, NT, P1>(sp, sf, i0, j0, a, args.tf2, tid, static_cast<float*>(args.dst1));
+        if (ok && !s_abort)
+            step2_second<S, SRC, T, NT, P1, SR>(sp, sf, i0, j0, a, args.tf2, tid, static_cast<S*>(args.dst1), args.rkey2);
         __syncthreads();  // stage s fully read
         if (s_abort) {
             if (tid == 0) {
@@ -187,7 +192,8 @@ __global__ void pack_fields2_kernel(float* f2, const float* uv, const float* Dh,
 // The ghost cells at distance 2 of every plane (the outer ring of the two-wide frame) from the
 // interior node they repeat.  The distance-1 ring already holds its images: every step
 // kernel writes it.  Reads touch the interior only, writes the ring only.
-__global__ void refresh_ghosts2_kernel(float* P, PlaneLayout L) {
+template <typename E>
+__global__ void refresh_ghosts2_kernel(E* P, PlaneLayout L) {
     const int gw = L.nx + 2 * kGhostP, gh = L.ny + 2 * kGhostP;
     const int n = 2 * gw + 2 * (gh - 2);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < kQ * n; k += gridDim.x * blockDim.x) {
@@ -201,7 +207,7 @@ __global__ void refresh_ghosts2_kernel(float* P, PlaneLayout L) {
             j = u % (gh - 2) - kGhostP + 1;
             i = u < gh - 2 ? -kGhostP : L.nx + kGhostP - 1;
         }
-        float* plane = P + (size_t)q * L.plane;
+        E* plane = P + (size_t)q * L.plane;
         plane[L.at_g<kGhostP>(i, j)] = plane[L.at_g<kGhostP>(wrap_clamp(i, L.nx), wrap_clamp(j, L.ny))];
     }
 }
@@ -212,9 +218,9 @@ __global__ void refresh_ghosts2_kernel(float* P, PlaneLayout L) {
 
 // One launch: two steps from the buffer described by src_map into dst (dst1: the intermediate
 // state too, or null), as steps `step` and `step + 1` (the pulse source's time levels).
-template <int SRC, class G, bool P1>
+template <typename S, int SRC, class G, bool P1, bool SR>
 cudaError_t launch2_typed(trtr_ctx* ctx, const CUtensorMap& src_map, void* dst, void* dst1, long step) {
-    auto kernel = step2_kernel<SRC, G, P1>;
+    auto kernel = step2_kernel<S, SRC, G, P1, SR>;
     const size_t smem = (size_t)G::kStages * G::T::Stage + 128 + G::kStages * sizeof(uint64_t);
     static int configured_device = -1;
     static int ctas_per_sm = 1;
@@ -245,6 +251,8 @@ cudaError_t launch2_typed(trtr_ctx* ctx, const CUtensorMap& src_map, void* dst, 
     a.y0 = (float)ctx->p.y0;
     a.dx = (float)ctx->p.dx;
     a.dt = (float)ctx->p.dt;
+    a.rkey = sr_step_key(step);
+    args.rkey2 = sr_step_key(step + 1);
     if (SRC == TRTR_SRC_PULSE) {
         a.dD_amp = (float)(ctx->pulse.D0 * ctx->pulse.D_amp);
         a.tf = pulse_time_fields<float>(ctx->pulse, ctx->p.dt, step);
@@ -274,27 +282,48 @@ bool two_step_applies(const trtr_ctx* ctx) {
            (ctx->p.src_mode == TRTR_SRC_NONE || ctx->p.src_mode == TRTR_SRC_PULSE);
 }
 
-template <class G>
+template <typename S, class G>
 cudaError_t encode_pop2_typed(trtr_ctx* ctx, void* buffer, CUtensorMap* out) {
     using T = typename G::T;
-    return encode(out, tma_type<float>(), 4, buffer, ctx->lp, kQ, T::W, T::PR, kQ) ? cudaSuccess
-                                                                                  : cudaErrorInvalidValue;
+    return encode(out, tma_type<S>(), (int)sizeof(S), buffer, ctx->lp, kQ, T::W, T::PR, kQ) ? cudaSuccess
+                                                                                          : cudaErrorInvalidValue;
 }
 
-template <class G>
+template <typename S, class G>
 cudaError_t encode2_typed(trtr_ctx* ctx) {
     using T = typename G::T;
     bool ok = true;
     for (int b = 0; b < 2; ++b)
-        ok = ok && encode(&ctx->maps2[b], tma_type<float>(), 4, ctx->pop[b], ctx->lp, kQ, T::W, T::PR, kQ);
-    ok = ok && encode(&ctx->maps2[2], tma_type<float>(), 4, ctx->fld2, ctx->lt, kT2NF, T::W, T::FR, kT2NF);
+        ok = ok && encode(&ctx->maps2[b], tma_type<S>(), (int)sizeof(S), ctx->pop[b], ctx->lp, kQ, T::W, T::PR, kQ);
+    ok = ok && encode(&ctx->maps2[2], tma_type<float>(), 4, ctx->fld2, ctx->lt, kT2NF, T::WF, T::FR, kT2NF);
     return ok ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Calls f((S*)nullptr, Geom2Of<SRC, sizeof(S)>-typed tag, SRC) for the context's storage and
+// source mode (FP32, FP16 or BF16 populations; no source or the pulse source).
+template <typename S, class F>
+cudaError_t by_source(const trtr_ctx* ctx, F&& f) {
+    return ctx->p.src_mode == TRTR_SRC_PULSE
+               ? f((S*)nullptr, (Geom2Of<TRTR_SRC_PULSE, (int)sizeof(S)>*)nullptr, std::integral_constant<int, TRTR_SRC_PULSE>())
+               : f((S*)nullptr, (Geom2Of<TRTR_SRC_NONE, (int)sizeof(S)>*)nullptr, std::integral_constant<int, TRTR_SRC_NONE>());
+}
+template <class F>
+cudaError_t by_storage(const trtr_ctx* ctx, F&& f) {
+    switch (ctx->p.precision) {
+        case TRTR_F32: return by_source<float>(ctx, f);
+        case TRTR_F16_OFS: return by_source<__half>(ctx, f);
+        case TRTR_BF16_OFS: return by_source<__nv_bfloat16>(ctx, f);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t encode_maps2(trtr_ctx* ctx) {
     if (!ctx->fld2) return cudaSuccess;
-    return ctx->p.src_mode == TRTR_SRC_PULSE ? encode2_typed<Geom2Of<TRTR_SRC_PULSE>>(ctx)
-                                             : encode2_typed<Geom2Of<TRTR_SRC_NONE>>(ctx);
+    return by_storage(ctx, [&](auto* sp, auto* gp, auto) {
+        using S = std::remove_pointer_t<decltype(sp)>;
+        using G = std::remove_pointer_t<decltype(gp)>;
+        return encode2_typed<S, G>(ctx);
+    });
 }
 
 cudaError_t launch_pack_fields2(trtr_ctx* ctx) {
@@ -311,26 +340,39 @@ cudaError_t launch_refresh_ghosts2_buffer(trtr_ctx* ctx, void* P) {
     const int n = 2 * (ctx->p.nx + 2 * kGhostP) + 2 * (ctx->p.ny + 2 * kGhostP - 2);
     const int want = (kQ * n + 255) / 256, cap = ctx->num_sms * 4;
     ctx->launches += 1;
-    refresh_ghosts2_kernel<<<want < cap ? want : cap, 256, 0, ctx->stream>>>(static_cast<float*>(P), ctx->lp);
+    if (ctx->esize == 4)
+        refresh_ghosts2_kernel<<<want < cap ? want : cap, 256, 0, ctx->stream>>>(static_cast<float*>(P), ctx->lp);
+    else if (ctx->esize == 2)
+        refresh_ghosts2_kernel<<<want < cap ? want : cap, 256, 0, ctx->stream>>>(static_cast<unsigned short*>(P), ctx->lp);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
 cudaError_t launch_refresh_ghosts2(trtr_ctx* ctx) { return launch_refresh_ghosts2_buffer(ctx, ctx->pop[ctx->cur]); }
 
 cudaError_t encode_pop_map2(trtr_ctx* ctx, void* buffer, CUtensorMap* out) {
-    return ctx->p.src_mode == TRTR_SRC_PULSE ? encode_pop2_typed<Geom2Of<TRTR_SRC_PULSE>>(ctx, buffer, out)
-                                             : encode_pop2_typed<Geom2Of<TRTR_SRC_NONE>>(ctx, buffer, out);
-}
-
-template <bool P1>
-cudaError_t launch2_src(trtr_ctx* ctx, const CUtensorMap* src_map, void* dst, void* dst1, long step) {
-    return ctx->p.src_mode == TRTR_SRC_PULSE
-               ? launch2_typed<TRTR_SRC_PULSE, Geom2Of<TRTR_SRC_PULSE>, P1>(ctx, *src_map, dst, dst1, step)
-               : launch2_typed<TRTR_SRC_NONE, Geom2Of<TRTR_SRC_NONE>, P1>(ctx, *src_map, dst, dst1, step);
+    return by_storage(ctx, [&](auto* sp, auto* gp, auto) {
+        using S = std::remove_pointer_t<decltype(sp)>;
+        using G = std::remove_pointer_t<decltype(gp)>;
+        return encode_pop2_typed<S, G>(ctx, buffer, out);
+    });
 }
 
 cudaError_t launch_step2_from(trtr_ctx* ctx, const CUtensorMap* src_map, void* dst, void* dst1, long step) {
-    return dst1 ? launch2_src<true>(ctx, src_map, dst, dst1, step) : launch2_src<false>(ctx, src_map, dst, dst1, step);
+    const bool sr = ctx->esize == 2 && ctx->p.rounding == TRTR_ROUND_STOCHASTIC;
+    return by_storage(ctx, [&](auto* sp, auto* gp, auto src) {
+        using S = std::remove_pointer_t<decltype(sp)>;
+        using G = std::remove_pointer_t<decltype(gp)>;
+        constexpr int SRC = decltype(src)::value;
+        if constexpr (sizeof(S) == 2) {
+            if (sr)
+                return dst1 ? launch2_typed<S, SRC, G, true, true>(ctx, *src_map, dst, dst1, step)
+                            : launch2_typed<S, SRC, G, false, true>(ctx, *src_map, dst, dst1, step);
+        }
+        return dst1 ? launch2_typed<S, SRC, G, true, false>(ctx, *src_map, dst, dst1, step)
+                    : launch2_typed<S, SRC, G, false, false>(ctx, *src_map, dst, dst1, step);
+    });
 }
 
 cudaError_t launch_step2(trtr_ctx* ctx) {

@@ -11,57 +11,92 @@ namespace core {
 
 constexpr int kT2NF = 5;  // packed fields: uhat_x, uhat_y, a_x, a_y, Dh
 
-// Stage of one BX x BY output tile: the population box (9 planes) and the field box (5 planes).
-template <int BX, int BY>
+// Stage of one BX x BY output tile: the population box (9 planes of ES-byte values) and the
+// field box (5 planes of floats).  Both boxes start on a 16-byte column boundary left of the
+// two-node halo: HX = 16 / ES population columns, 4 field columns.
+template <int BX, int BY, int ES = 4>
 struct Tile2 {
     static constexpr int X = BX, Y = BY;
-    static constexpr int W = BX + 8;                     // staged columns [i0 - 4, i0 + BX + 4)
+    static constexpr int HX = 16 / ES;                   // staged population columns [i0 - HX, i0 + BX + HX)
+    static constexpr int W = BX + 2 * HX;
+    static constexpr int WF = BX + 8;                    // staged field columns [i0 - 4, i0 + BX + 4)
     static constexpr int PR = BY + 4;                    // staged population rows
     static constexpr int FR = BY + 2;                    // staged field rows
     static constexpr int R1 = (BY + 2) * (BX + 4) / 2;  // node pairs of step 1
     static constexpr int R2 = BY * BX / 2;               // node pairs of step 2
-    static constexpr int PopPlane = PR * W;              // floats
-    static constexpr int FldPlane = FR * W;
-    static constexpr int PopBytes = kQ * PopPlane * 4;
+    static constexpr int PopPlane = PR * W;              // values
+    static constexpr int FldPlane = FR * WF;             // floats
+    static constexpr int PopBytes = kQ * PopPlane * ES;
+    static constexpr int FldOff = (PopBytes + 127) / 128 * 128;  // the field box, 128-byte aligned
     static constexpr int FldBytes = kT2NF * FldPlane * 4;
     static constexpr int TX = PopBytes + FldBytes;       // bytes per tile (boxes include any fill)
-    static constexpr int Stage = (TX + 127) / 128 * 128;
-    static_assert(BX % 4 == 0, "tile origins on 16-byte boundaries");
-    static_assert(PopBytes % 128 == 0, "the field box must start on a 128-byte boundary");
-    static_assert(W <= 256 && PR <= 256, "TMA box dimensions are at most 256");
+    static constexpr int Stage = (FldOff + FldBytes + 127) / 128 * 128;
+    static_assert(ES == 4 || ES == 2, "FP32 or 2-byte populations");
+    static_assert(BX % 8 == 0, "tile origins on 16-byte boundaries");
+    static_assert(ES != 4 || FldOff == PopBytes, "FP32: the field box follows the population box");
+    static_assert(W <= 256 && WF <= 256 && PR <= 256, "TMA box dimensions are at most 256");
 };
 
-template <int STAGES, int CTAS, int THREADS, int BX, int BY>
+template <int STAGES, int CTAS, int THREADS, int BX, int BY, int ES = 4>
 struct Geom2 {
     static constexpr int kStages = STAGES, kCtas = CTAS, kThreads = THREADS;
-    using T = Tile2<BX, BY>;
+    using T = Tile2<BX, BY, ES>;
     static_assert(STAGES * T::Stage + 256 <= 227 * 1024, "the stages must fit in shared memory");
 };
-// Geometry per source mode (stages, CTAs per SM, threads, tile width, tile height), from the
-// sweeps of rebuilds with -DTRTR_STEP2_STAGES=S -DTRTR_STEP2_CTAS=C -DTRTR_STEP2_THREADS=T
-// -DTRTR_STEP2_BX=X -DTRTR_STEP2_BY=Y (all five; they set it for both modes): a few
-// independent CTAs per SM hide each one's barrier between the two steps, the pulse source's
-// arithmetic favours more of them.
-template <int SRC>
-struct Geom2For {  // in-kernel pulse source
-    using type = Geom2<2, 3, 128, 32, 8>;
+// Geometry per source mode and population size (stages, CTAs per SM, threads, tile width, tile
+// height), from the sweeps of rebuilds with -DTRTR_STEP2_STAGES=S -DTRTR_STEP2_CTAS=C
+// -DTRTR_STEP2_THREADS=T -DTRTR_STEP2_BX=X -DTRTR_STEP2_BY=Y (all five; they set it for both
+// modes of the FP32 kernel; TRTR_STEP2H_* the same for the 2-byte one): a few independent CTAs
+// per SM hide each one's barrier between the two steps, the pulse source's arithmetic favours
+// more of them.
+template <int SRC, int ES>
+struct Geom2For {  // FP32, in-kernel pulse source
+    using type = Geom2<2, 3, 128, 32, 8, ES>;
 };
 template <>
-struct Geom2For<TRTR_SRC_NONE> {
-    using type = Geom2<2, 2, 256, 32, 16>;
+struct Geom2For<TRTR_SRC_NONE, 4> {
+    using type = Geom2<2, 2, 256, 32, 16, 4>;
 };
+// 2-byte storages: half the stage bytes, so wider tiles with less step-1 halo work fit two CTAs
+// per SM.  Measured (GB300, FP16 pulse, GLUPS at 4096^2 / 8192^2): 32 x 8 in 3 (4) 128-thread
+// CTAs 111.0 / 117.2 (112.2 / 118.4), 64 x 8 in 3 128-thread CTAs 114.9 / 123.5, 64 x 12 in 2
+// 256-thread CTAs 115.8 / 125.1, 64 x 16 in 2 256-thread CTAs 120.3 / 131.5, 64 x 32 or 128 x 16
+// in one 512-thread CTA 114.5 / 126.5 and 111.4 / 124.5.
+template <int SRC>
+struct Geom2For<SRC, 2> {
+    using type = Geom2<2, 2, 256, 64, 16, 2>;
+};
+#if defined(TRTR_STEP2_BX) || defined(TRTR_STEP2H_BX)
+template <int SRC, int ES>
+struct Geom2Sweep {
+    using type = typename Geom2For<SRC, ES>::type;
+};
+#endif
 #ifdef TRTR_STEP2_BX
 template <int SRC>
-using Geom2Of = Geom2<TRTR_STEP2_STAGES, TRTR_STEP2_CTAS, TRTR_STEP2_THREADS, TRTR_STEP2_BX, TRTR_STEP2_BY>;
-#else
+struct Geom2Sweep<SRC, 4> {
+    using type = Geom2<TRTR_STEP2_STAGES, TRTR_STEP2_CTAS, TRTR_STEP2_THREADS, TRTR_STEP2_BX, TRTR_STEP2_BY, 4>;
+};
+#endif
+#ifdef TRTR_STEP2H_BX
 template <int SRC>
-using Geom2Of = typename Geom2For<SRC>::type;
+struct Geom2Sweep<SRC, 2> {
+    using type = Geom2<TRTR_STEP2H_STAGES, TRTR_STEP2H_CTAS, TRTR_STEP2H_THREADS, TRTR_STEP2H_BX, TRTR_STEP2H_BY, 2>;
+};
+#endif
+#if defined(TRTR_STEP2_BX) || defined(TRTR_STEP2H_BX)
+template <int SRC, int ES = 4>
+using Geom2Of = typename Geom2Sweep<SRC, ES>::type;
+#else
+template <int SRC, int ES = 4>
+using Geom2Of = typename Geom2For<SRC, ES>::type;
 #endif
 
 struct alignas(16) Step2Args {
-    StepArgs<float> a;  // tf: the pulse uniforms of the first step
+    StepArgs<float> a;  // tf, rkey: the pulse uniforms and rounding key of the first step
     TimeFields<float> tf2;  // of the second step
     void* dst1;             // if not null: also store the first step's state here (one-wide ghosts)
+    uint32_t rkey2;         // the second step's rounding key (stochastic rounding of 2-byte storages)
 };
 
 // Wrapped index of a node of the halo region (v in [-2, n + 1] with n >= 2 maps onto its
@@ -92,8 +127,9 @@ __device__ __forceinline__ F2 pair_source(const StepArgs<float>& a, const TimeFi
 }
 
 // The TMA loads of one tile into `stage` (its barrier armed by the caller): the population box of
-// depth 9 and the packed-field box of depth 5, x origin i0 - 4 (16-byte aligned), rows from
-// j0 - 2 and j0 - 1.
+// depth 9 from column i0 - HX (gxp: the population layout's column of x = 0) and row j0 - 2, and
+// the packed-field box of depth 5 from column i0 - 4 (gxf: the field layout's) and row j0 - 1;
+// both x origins are 16-byte aligned.
 // TRTR_STEP2_L2HINT = 1 (the default): the tile loads ask L2 to keep their lines (the
 // neighbouring tiles read the halo again) and the result stores to evict theirs first; measured
 // on the 4096^2 pulse: DRAM reads -2.3 %, launch -0.7 %.
@@ -102,25 +138,59 @@ __device__ __forceinline__ F2 pair_source(const StepArgs<float>& a, const TimeFi
 #endif
 template <class T>
 __device__ __forceinline__ void step2_issue(unsigned char* stage, uint64_t* bar, const CUtensorMap* mp,
-                                            const CUtensorMap* mf, int i0, int j0, int gx) {
-    const int x = i0 + gx - 4;
+                                            const CUtensorMap* mf, int i0, int j0, int gxp, int gxf) {
+    constexpr int kES = 16 / T::HX;
+    const int xp = i0 + gxp - T::HX, xf = i0 + gxf - 4;
 #if TRTR_STEP2_L2HINT
     const uint64_t keep = l2_evict_last();
-    if (tma_ok(stage, x, j0 + kGhostP - 2, 4)) tma_load_3d_hint(stage, mp, bar, x, j0 + kGhostP - 2, 0, keep);
-    if (tma_ok(stage + T::PopBytes, x, j0 + kGhostP - 1, 4))
-        tma_load_3d_hint(stage + T::PopBytes, mf, bar, x, j0 + kGhostP - 1, 0, keep);
+    if (tma_ok(stage, xp, j0 + kGhostP - 2, kES)) tma_load_3d_hint(stage, mp, bar, xp, j0 + kGhostP - 2, 0, keep);
+    if (tma_ok(stage + T::FldOff, xf, j0 + kGhostP - 1, 4))
+        tma_load_3d_hint(stage + T::FldOff, mf, bar, xf, j0 + kGhostP - 1, 0, keep);
 #else
-    if (tma_ok(stage, x, j0 + kGhostP - 2, 4)) tma_load_3d(stage, mp, bar, x, j0 + kGhostP - 2, 0);
-    if (tma_ok(stage + T::PopBytes, x, j0 + kGhostP - 1, 4))
-        tma_load_3d(stage + T::PopBytes, mf, bar, x, j0 + kGhostP - 1, 0);
+    if (tma_ok(stage, xp, j0 + kGhostP - 2, kES)) tma_load_3d(stage, mp, bar, xp, j0 + kGhostP - 2, 0);
+    if (tma_ok(stage + T::FldOff, xf, j0 + kGhostP - 1, 4))
+        tma_load_3d(stage + T::FldOff, mf, bar, xf, j0 + kGhostP - 1, 0);
 #endif
 }
 
-// Step 1 over the tile's halo region R1, in place in the stage (thread tid of NT).
-template <int SRC, class T, int NT>
-__device__ __forceinline__ void step2_first(float* sp, const float* sf, int i0, int j0, const StepArgs<float>& a,
+// A node pair of a staged population plane (S values; aligned: the pair starts on an even
+// column), read as offsets or written from a stored pair.
+template <typename S>
+__device__ __forceinline__ F2 stage_ld2(const S* v, bool aligned) {
+    using P = Pair<S>;
+    return aligned ? P::raw(*reinterpret_cast<const typename P::type*>(v)) : P::raw(v[0], v[1]);
+}
+template <typename S, typename S2>
+__device__ __forceinline__ void stage_st2(S* d, S2 v, bool aligned) {
+    if (aligned) {
+        *reinterpret_cast<S2*>(d) = v;
+    } else {
+        d[0] = reinterpret_cast<const S*>(&v)[0];
+        d[1] = reinterpret_cast<const S*>(&v)[1];
+    }
+}
+
+// The stored form of population q of a node pair: FP32 as it is; 2-byte offsets rounded to
+// nearest, or stochastically (SR) with the bits of the pair's key rk, as the one-step kernel
+// stores them.
+template <typename S, bool SR>
+__device__ __forceinline__ typename Pair<S>::type encode2(F2 v, uint32_t rk, int q) {
+    if constexpr (SR)
+        return Pair<S>::encode_sr(v, sr_bits(rk, q));
+    else
+        return Pair<S>::encode_raw(v);
+}
+
+// Step 1 over the tile's halo region R1, in place in the stage (thread tid of NT).  2-byte
+// storages: the step-1 values are rounded to the storage format with the first step's key, as
+// a one-step launch stores them (halo nodes with the key of the wrapped node; nx is even, so
+// the wrapped pairs are the one-step kernel's pairs).
+template <typename S, int SRC, class T, int NT, bool SR = false>
+__device__ __forceinline__ void step2_first(S* sp, const float* sf, int i0, int j0, const StepArgs<float>& a,
                                             const TimeFields<float>& tf, int tid) {
-    constexpr int kT2W = T::W, kT2PopPlane = T::PopPlane, kT2FldPlane = T::FldPlane;
+    constexpr int kT2W = T::W, kT2WF = T::WF, kT2PopPlane = T::PopPlane, kT2FldPlane = T::FldPlane;
+    constexpr bool kOfs = sizeof(S) == 2;  // offsets folded into the moments, as in the one-step kernel
+    constexpr int kC = T::HX - 2;          // stage column of R1 column 0
     // Node pairs (c, c + 1) of a halo row.  R1SHIFT = 1: c odd, the columns 1 .. X + 2 that step
     // 2 reads (the planes with e_x != 0 then sit on even offsets); 0: c even from 0, including
     // the two outermost columns (the planes with e_x = 0 and the fields on even offsets).
@@ -128,6 +198,7 @@ __device__ __forceinline__ void step2_first(float* sp, const float* sf, int i0, 
 #define TRTR_STEP2_R1SHIFT 0
 #endif
     constexpr int kShift = TRTR_STEP2_R1SHIFT;
+    static_assert(!kOfs || kShift == 0, "2-byte storages round the one-step kernel's pairs");
     constexpr int kRowPairs = (T::X + 4 - 2 * kShift) / 2;
     constexpr int kPairs = (T::Y + 2) * kRowPairs;
     const int nx = a.lp.nx, ny = a.lp.ny;
@@ -140,10 +211,10 @@ __device__ __forceinline__ void step2_first(float* sp, const float* sf, int i0, 
         F2 g[kQ];
 #pragma unroll
         for (int q = 0; q < kQ; ++q) {
-            const float* src = sp + q * kT2PopPlane + (r + 1 - lattice_ey(q)) * kT2W + c + 2 - lattice_ex(q);
-            g[q] = ld2(src, (lattice_ex(q) != 0) == (kShift == 1));
+            const S* src = sp + q * kT2PopPlane + (r + 1 - lattice_ey(q)) * kT2W + c + kC - lattice_ex(q);
+            g[q] = stage_ld2(src, (lattice_ex(q) != 0) == (kShift == 1));
         }
-        const float* f = sf + r * kT2W + c + 2;
+        const float* f = sf + r * kT2WF + c + 2;
         const bool fa = kShift == 0;
         const F2 ux = ld2(f, fa);
         const F2 uy = ld2(f + kT2FldPlane, fa);
@@ -151,18 +222,15 @@ __device__ __forceinline__ void step2_first(float* sp, const float* sf, int i0, 
         const F2 ay = ld2(f + 3 * kT2FldPlane, fa);
         const F2 Dh = ld2(f + 4 * kT2FldPlane, fa);
         const int x = i0 - 2 + c, y = j0 - 1 + r;
-        const F2 src = pair_source<SRC>(a, tf, wrap_clamp(x, nx), wrap_clamp(x + 1, nx), wrap_clamp(y, ny));
+        const int wx = wrap_clamp(x, nx), wy = wrap_clamp(y, ny);
+        const F2 src = pair_source<SRC>(a, tf, wx, wrap_clamp(x + 1, nx), wy);
         F2 out[kQ];
-        collide_node<F2>(g, ux, uy, ax, ay, Dh, src, magic, w2f, a.tau2_fixed, out);
+        collide_node<F2, kOfs>(g, ux, uy, ax, ay, Dh, src, magic, w2f, a.tau2_fixed, out, F2(a.phi_ref));
+        const uint32_t rk = SR ? sr_pair_key(wx, wy, nx, a.rkey) : 0u;
 #pragma unroll
         for (int q = 0; q < kQ; ++q) {
-            float* d = sp + q * kT2PopPlane + (r + 1 - lattice_ey(q)) * kT2W + c + 2 - lattice_ex(q);
-            if ((lattice_ex(q) != 0) == (kShift == 1)) {
-                *reinterpret_cast<float2*>(d) = out[q].v;
-            } else {
-                d[0] = out[q].v.x;
-                d[1] = out[q].v.y;
-            }
+            S* d = sp + q * kT2PopPlane + (r + 1 - lattice_ey(q)) * kT2W + c + kC - lattice_ex(q);
+            stage_st2(d, encode2<S, SR>(out[q], rk, q), (lattice_ex(q) != 0) == (kShift == 1));
         }
     }
 }
@@ -170,14 +238,17 @@ __device__ __forceinline__ void step2_first(float* sp, const float* sf, int i0, 
 // Step 2 on the tile's output nodes from the step-1 values in the stage, stored to a.dst with
 // the ghost copies of nodes within two of an edge.  P1: the step-1 state of the output nodes is
 // stored to dst1 too, with the one-wide ghost frame that one-step kernels read.
-template <int SRC, class T, int NT, bool P1 = false>
-__device__ __forceinline__ void step2_second(const float* sp, const float* sf, int i0, int j0,
+template <typename S, int SRC, class T, int NT, bool P1 = false, bool SR = false>
+__device__ __forceinline__ void step2_second(const S* sp, const float* sf, int i0, int j0,
                                              const StepArgs<float>& a, const TimeFields<float>& tf2, int tid,
-                                             float* dst1 = nullptr) {
-    constexpr int kT2X = T::X, kT2W = T::W, kT2R2 = T::R2, kT2PopPlane = T::PopPlane, kT2FldPlane = T::FldPlane;
+                                             S* dst1 = nullptr, uint32_t rkey2 = 0u) {
+    constexpr int kT2X = T::X, kT2W = T::W, kT2WF = T::WF, kT2R2 = T::R2, kT2PopPlane = T::PopPlane,
+                  kT2FldPlane = T::FldPlane;
+    constexpr bool kOfs = sizeof(S) == 2;
+    using S2 = typename Pair<S>::type;
     const int nx = a.lp.nx, ny = a.lp.ny;
     const F2 magic(a.magic), w2f(a.omega2_fixed);
-    float* dst = static_cast<float*>(a.dst);
+    S* dst = static_cast<S*>(a.dst);
     const size_t pl = a.lp.plane;
     for (int p = tid; p < kT2R2; p += NT) {
         const int r2 = p / (kT2X / 2), c2 = 2 * (p - r2 * (kT2X / 2));
@@ -186,7 +257,7 @@ __device__ __forceinline__ void step2_second(const float* sp, const float* sf, i
         if constexpr (P1) {  // the step-1 value of node (r2, c2) = R1 node (r2 + 1, c2 + 2), plane by plane
 #pragma unroll
             for (int q = 0; q < kQ; ++q) {
-                const float* v = sp + q * kT2PopPlane + (r2 + 2 - lattice_ey(q)) * kT2W + c2 + 4 - lattice_ex(q);
+                const S* v = sp + q * kT2PopPlane + (r2 + 2 - lattice_ey(q)) * kT2W + c2 + T::HX - lattice_ex(q);
                 store_with_ghosts<1, kGhostP>(dst1 + q * pl, a.lp, i, j, v[0]);
                 if (i + 1 < nx) store_with_ghosts<1, kGhostP>(dst1 + q * pl, a.lp, i + 1, j, v[1]);
             }
@@ -194,9 +265,9 @@ __device__ __forceinline__ void step2_second(const float* sp, const float* sf, i
         F2 g[kQ];
 #pragma unroll
         for (int q = 0; q < kQ; ++q)
-            g[q] = F2(*reinterpret_cast<const float2*>(sp + q * kT2PopPlane + (r2 + 2 - 2 * lattice_ey(q)) * kT2W +
-                                                      c2 + 4 - 2 * lattice_ex(q)));
-        const float* f = sf + (r2 + 1) * kT2W + c2 + 4;
+            g[q] = stage_ld2(sp + q * kT2PopPlane + (r2 + 2 - 2 * lattice_ey(q)) * kT2W + c2 + T::HX - 2 * lattice_ex(q),
+                             true);
+        const float* f = sf + (r2 + 1) * kT2WF + c2 + 4;
         const F2 ux(*reinterpret_cast<const float2*>(f));
         const F2 uy(*reinterpret_cast<const float2*>(f + kT2FldPlane));
         const F2 ax(*reinterpret_cast<const float2*>(f + 2 * kT2FldPlane));
@@ -204,12 +275,13 @@ __device__ __forceinline__ void step2_second(const float* sp, const float* sf, i
         const F2 Dh(*reinterpret_cast<const float2*>(f + 4 * kT2FldPlane));
         const F2 src = pair_source<SRC>(a, tf2, i, i + 1 < nx ? i + 1 : nx - 1, j);
         F2 out[kQ];
-        collide_node<F2>(g, ux, uy, ax, ay, Dh, src, magic, w2f, a.tau2_fixed, out);
+        collide_node<F2, kOfs>(g, ux, uy, ax, ay, Dh, src, magic, w2f, a.tau2_fixed, out, F2(a.phi_ref));
+        const uint32_t rk = SR ? sr_pair_key(i, j, nx, rkey2) : 0u;
         const bool edge = j < kGhostP || j >= ny - kGhostP || i < kGhostP || i + 1 >= nx - kGhostP;
         if (!edge) {
-            float* d0 = dst + a.lp.at_g<kGhostP>(i, j);
+            S* d0 = dst + a.lp.at_g<kGhostP>(i, j);
 #if TRTR_BOUNDS_CHECK
-            if ((reinterpret_cast<uintptr_t>(d0) & 7u) != 0u) {
+            if ((reinterpret_cast<uintptr_t>(d0) % sizeof(S2)) != 0u) {
                 TRTR_BOUNDS_FAULT(kBoundsPair, i, j);
                 continue;
             }
@@ -217,16 +289,23 @@ __device__ __forceinline__ void step2_second(const float* sp, const float* sf, i
 #if TRTR_STEP2_L2HINT
             const uint64_t leave = l2_evict_first();
 #pragma unroll
-            for (int q = 0; q < kQ; ++q) st_global_f2_hint(d0 + q * pl, out[q].v, leave);
+            for (int q = 0; q < kQ; ++q) {
+                if constexpr (sizeof(S) == 4)
+                    st_global_f2_hint(reinterpret_cast<float*>(d0 + q * pl), out[q].v, leave);
+                else
+                    st_global_b32_hint(reinterpret_cast<S2*>(d0 + q * pl), encode2<S, SR>(out[q], rk, q), leave);
+            }
 #else
 #pragma unroll
-            for (int q = 0; q < kQ; ++q) *reinterpret_cast<float2*>(d0 + q * pl) = out[q].v;
+            for (int q = 0; q < kQ; ++q) *reinterpret_cast<S2*>(d0 + q * pl) = encode2<S, SR>(out[q], rk, q);
 #endif
         } else {
 #pragma unroll
             for (int q = 0; q < kQ; ++q) {
-                store_with_ghosts<kGhostP, kGhostP>(dst + q * pl, a.lp, i, j, out[q].v.x);
-                if (i + 1 < nx) store_with_ghosts<kGhostP, kGhostP>(dst + q * pl, a.lp, i + 1, j, out[q].v.y);
+                const S2 v = encode2<S, SR>(out[q], rk, q);
+                store_with_ghosts<kGhostP, kGhostP>(dst + q * pl, a.lp, i, j, reinterpret_cast<const S*>(&v)[0]);
+                if (i + 1 < nx)
+                    store_with_ghosts<kGhostP, kGhostP>(dst + q * pl, a.lp, i + 1, j, reinterpret_cast<const S*>(&v)[1]);
             }
         }
     }

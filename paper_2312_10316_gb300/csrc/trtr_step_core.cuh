@@ -116,6 +116,14 @@ __device__ __forceinline__ void st_global_f2_hint(float* p, float2 v, uint64_t p
     asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(v.x), "f"(v.y), "l"(policy)
                  : "memory");
 }
+// the same for a pair of 2-byte values (one 32-bit word)
+template <typename S2>
+__device__ __forceinline__ void st_global_b32_hint(S2* p, S2 v, uint64_t policy) {
+    static_assert(sizeof(S2) == 4, "a 32-bit pair");
+    uint32_t w;
+    memcpy(&w, &v, sizeof(w));
+    asm volatile("st.global.L2::cache_hint.b32 [%0], %1, %2;" ::"l"(p), "r"(w), "l"(policy) : "memory");
+}
 
 // Bulk copy of `bytes` (a multiple of 16) from shared to global memory, both addresses 16-byte
 // aligned; the async proxy reads the source, completion is tracked per thread in bulk
@@ -352,6 +360,21 @@ __device__ __forceinline__ constexpr int plane_offset(int q) {
 }
 
 // Pair (2-element) storage vectors and their conversion to / from packed FP32.
+// Random bits of the stochastic rounding of node pair (i, i + 1) of row j (i even): the pair's
+// key, and the 32 bits of its population q.
+__device__ __forceinline__ uint32_t sr_pair_key(int i, int j, int nx, uint32_t rkey) {
+    return sr_hash(((uint32_t)j * (uint32_t)nx + (uint32_t)i) ^ rkey);
+}
+#ifndef TRTR_SR_WORDS
+#define TRTR_SR_WORDS 9
+#endif
+__device__ __forceinline__ uint32_t sr_bits(uint32_t rk, int q) {
+    // 9 words (the key rotated by 7 q), or 3 or 1 words shared by groups of populations (sweeps)
+    if (TRTR_SR_WORDS == 9) return __funnelshift_l(rk, rk, 7 * q);
+    if (TRTR_SR_WORDS == 3) return q < 3 ? rk : (q < 6 ? rk * 0x85EBCA6Bu : rk * 0xC2B2AE35u);
+    return rk;
+}
+
 template <typename S>
 struct Pair;
 template <>
@@ -530,22 +553,12 @@ __device__ __forceinline__ void tile_row_pairs(const unsigned char* st, int r, i
         F2 out[kQ];
         // 2-byte storages: g and out stay offsets (the offset is folded into the moments)
         collide_node<F2, kOfs>(g, ux, uy, ax, ay, Dh, src, magic, w2f, a.tau2_fixed, out, F2(phi_ref));
-        uint32_t rk = 0;
-        if constexpr (SR) rk = sr_hash(((uint32_t)j * (uint32_t)nx + (uint32_t)i) ^ a.rkey);
-#ifndef TRTR_SR_WORDS
-#define TRTR_SR_WORDS 9
-#endif
+        const uint32_t rk = SR ? sr_pair_key(i, j, nx, a.rkey) : 0u;
         auto enc = [&](int q) -> S2 {
-            if constexpr (SR) {
-                // random bits of population q: 9 words (the key rotated by 7 q), or 3 or 1 words shared
-                // by groups of populations (sweeps)
-                if (TRTR_SR_WORDS == 9) return P::encode_sr(out[q], __funnelshift_l(rk, rk, 7 * q));
-                if (TRTR_SR_WORDS == 3)
-                    return P::encode_sr(out[q], q < 3 ? rk : (q < 6 ? rk * 0x85EBCA6Bu : rk * 0xC2B2AE35u));
-                return P::encode_sr(out[q], rk);
-            } else {
+            if constexpr (SR)
+                return P::encode_sr(out[q], sr_bits(rk, q));
+            else
                 return P::encode_raw(out[q]);
-            }
         };
 
         // a8: store P_i(x); edge nodes also write their periodic ghost copies (the one-wide frame

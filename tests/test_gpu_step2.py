@@ -1,9 +1,11 @@
-"""The two-step kernel (two time steps of Eq. (14) per launch; FP32 storage, periodic
-boundaries, no source or the pulse source).
+"""The two-step kernel (two time steps of Eq. (14) per launch; FP32 storage, or FP16 / BF16
+offset storage on grids of even nx; periodic boundaries, no source or the pulse source).
 
-Its node update is the one-step kernel's, so the populations after any number of steps must
-equal those of one launch per step bit for bit; the one-step path is checked against the FP64
-oracle elsewhere, and one case here checks the two-step path against the oracle directly.
+Its node update is the one-step kernel's, and the 2-byte storages round the intermediate state
+exactly as a one-step launch stores it (the same stochastic-rounding bits), so the populations
+after any number of steps must equal those of one launch per step bit for bit; the one-step path
+is checked against the FP64 oracle elsewhere, and cases here check the two-step path against the
+oracle directly.
 """
 import math
 
@@ -26,10 +28,10 @@ from paper_2312_10316_gb300 import trtr as T  # noqa: E402
 GRIDS = [(2, 3), (3, 5), (5, 3), (37, 23), (130, 9), (128, 8), (257, 19), (300, 130)]
 
 
-def _random_solver(nx, ny, grad_mode, k):
+def _random_solver(nx, ny, grad_mode, k, precision=T.TRTR_F32, **kw):
     case = random_case(900 + 13 * nx + ny, nx, ny)
-    p = T.Params(nx=nx, ny=ny, dx=case["dx"], dt=case["dt"], precision=T.TRTR_F32, grad_mode=grad_mode,
-                 src_mode=T.TRTR_SRC_NONE)
+    p = T.Params(nx=nx, ny=ny, dx=case["dx"], dt=case["dt"], precision=precision, grad_mode=grad_mode,
+                 src_mode=T.TRTR_SRC_NONE, **kw)
     s = T.Solver(p)
     s.set_steps_per_launch(k)
     s.set_fields(case["ux"], case["uy"], case["D"])
@@ -37,10 +39,10 @@ def _random_solver(nx, ny, grad_mode, k):
     return s
 
 
-def _pulse_solver(nx, ny, grad_mode, k, D_amp=0.5):
+def _pulse_solver(nx, ny, grad_mode, k, D_amp=0.5, precision=T.TRTR_F32, **kw):
     pulse = W.Pulse(n=max(nx, ny), D_amp=D_amp, courant=0.4)
-    p = T.Params(nx=nx, ny=ny, dx=pulse.dx, dt=pulse.dt, x0=pulse.x0, y0=pulse.y0, precision=T.TRTR_F32,
-                 grad_mode=grad_mode, src_mode=T.TRTR_SRC_PULSE)
+    p = T.Params(nx=nx, ny=ny, dx=pulse.dx, dt=pulse.dt, x0=pulse.x0, y0=pulse.y0, precision=precision,
+                 grad_mode=grad_mode, src_mode=T.TRTR_SRC_PULSE, **kw)
     s = T.Solver(p)
     s.set_steps_per_launch(k)
     s.set_pulse(pulse.omega, pulse.xc, pulse.yc, pulse.sigma0, pulse.D0, pulse.D_amp)
@@ -62,6 +64,62 @@ def test_two_steps_per_launch_equal_one_step_launches_bitwise(nx, ny, grad_mode,
     assert np.array_equal(out[1][0], out[2][0], equal_nan=True)
     if min(nx, ny) >= 8:
         assert np.isfinite(out[2][0]).all()
+
+
+HALF = {"f16": T.TRTR_F16_OFS, "bf16": T.TRTR_BF16_OFS}
+ROUND = {"sr": T.TRTR_ROUND_STOCHASTIC, "rn": T.TRTR_ROUND_NEAREST}
+HALF_GRIDS = [(2, 3), (4, 5), (6, 2), (38, 23), (130, 9), (128, 8), (258, 19), (300, 130)]
+
+
+@pytest.mark.parametrize("nx,ny", HALF_GRIDS)
+@pytest.mark.parametrize("prec", ["f16", "bf16"])
+@pytest.mark.parametrize("rounding", ["sr", "rn"])
+@pytest.mark.parametrize("kind", ["none", "pulse"])
+def test_two_byte_two_step_launches_equal_one_step_launches_bitwise(nx, ny, prec, rounding, kind):
+    """The 2-byte storages: the same bits as one launch per step, for both roundings (the
+    stochastic bits of the intermediate state, halo nodes included, are the one-step kernel's)
+    and an offset phi_ref away from zero on the random states."""
+    make = _random_solver if kind == "none" else _pulse_solver
+    kw = dict(precision=HALF[prec], rounding=ROUND[rounding])
+    if kind == "none":
+        kw["phi_ref"] = 0.75
+    out = {}
+    for k in (1, 2):
+        with make(nx, ny, T.TRTR_GRAD_ONESIDED_EDGE, k, **kw) as s:
+            assert s.steps_per_launch == k
+            s.step(5)
+            s.step(3)
+            out[k] = s.get_populations()
+    assert np.array_equal(out[1], out[2], equal_nan=True)
+    if min(nx, ny) >= 8:
+        assert np.isfinite(out[2]).all()
+
+
+@pytest.mark.parametrize("prec", ["f16", "bf16"])
+def test_two_byte_odd_nx_runs_one_step_per_launch(prec):
+    with _random_solver(37, 12, T.TRTR_GRAD_PERIODIC, 2, precision=HALF[prec]) as s:
+        assert s.steps_per_launch == 1
+        l0 = s.launches
+        s.step(4)
+        assert s.launches - l0 == 4
+
+
+@pytest.mark.parametrize("prec", ["f16", "bf16"])
+def test_two_byte_two_step_path_against_the_oracle(prec):
+    """200^2 pulse, 8 steps (four two-step launches) against the FP64 oracle, per element."""
+    pulse = W.Pulse(n=200, D_amp=0.5, courant=0.4)
+    with T.pulse_solver(pulse, precision=HALF[prec]) as s:
+        assert s.steps_per_launch == 2
+        l0 = s.launches
+        s.step(8)
+        launches = s.launches - l0
+        phi = s.moments()
+    o = oracle_for_pulse(pulse)
+    o.step(8)
+    tol = {"f16": 1e-3, "bf16": 8e-3}[prec]
+    assert rel_l2(phi, o.phi()) <= tol
+    assert_elementwise(phi, o.phi(), 4 * tol, "phi", tile=(32, 8))
+    assert launches == 1 + 4  # field packing, four two-step launches
 
 
 def test_launch_counts_and_the_stability_check_cadence():
@@ -118,7 +176,7 @@ def test_two_step_path_against_the_oracle():
     assert launches == 1 + 4  # field packing, four two-step launches
 
 
-def _sampled_two_step_check(pulse, warm, nsamples, tol, seed=1):
+def _sampled_two_step_check(pulse, warm, nsamples, tol, seed=1, precision=T.TRTR_F32):
     """Full-size check of one two-step launch in the bench's launch configuration: after `warm`
     steps (two per launch), the populations that one more launch writes at sampled nodes equal
     two applications of the oracle's single-node update (Eq. (14)) to the GPU's own state: the
@@ -140,7 +198,7 @@ def _sampled_two_step_check(pulse, warm, nsamples, tol, seed=1):
     osim = oracle.Sim(oracle.SimParams(nx=1, ny=1, dx=pulse.dx, dt=pulse.dt, src_mode=2, omega=pulse.omega,
                                        xc=pulse.xc, yc=pulse.yc, sigma0=pulse.sigma0, D0=pulse.D0,
                                        D_amp=pulse.D_amp))
-    with T.pulse_solver(pulse, precision=T.TRTR_F32) as s:
+    with T.pulse_solver(pulse, precision=precision) as s:
         assert s.steps_per_launch == 2 and warm % 2 == 0
         s.step(warm)
         g_n = s.sample(bnodes)
@@ -172,6 +230,16 @@ def _sampled_two_step_check(pulse, warm, nsamples, tol, seed=1):
 @pytest.mark.parametrize("pulse", [W.C2A_F32_1024, W.C2B_F32_4096], ids=lambda p: p.name)
 def test_fullsize_sampled_two_step_launch(pulse):
     _sampled_two_step_check(pulse, 100, 1500, 2e-6)
+
+
+@pytest.mark.parametrize("prec", ["f16", "bf16"])
+@pytest.mark.parametrize("pulse", [W.C2B_F32_4096, W.C3_HALF_8192], ids=lambda p: p.name)
+def test_fullsize_sampled_two_byte_two_step_launch(pulse, prec):
+    """The 2-byte storages at the bench's sizes: the GPU rounds the intermediate state and the
+    result to the format (stochastically), the oracle does not, so the bound is a few units of
+    the format (2^-11 FP16, 2^-8 BF16) of the largest population."""
+    unit = {"f16": 2.0**-11, "bf16": 2.0**-8}[prec]
+    _sampled_two_step_check(pulse, 100, 1500, 8 * unit, precision=HALF[prec])
 
 
 def test_save_load_and_recorded_runs_keep_the_two_step_path_exact():
