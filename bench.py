@@ -534,6 +534,7 @@ def run_batch(args):
     value = nodes * args.steps * world / (ms * 1e-3) / 1e9
     step_ms = ms / args.steps
     solves_per_s = len(pulses) * world * args.steps / pulses[0].steps / (ms * 1e-3)
+    spl = batch.steps_per_launch
     batch.close()
 
     # one launch per instance per step, same instances, same stream
@@ -581,14 +582,16 @@ def run_batch(args):
 
             dist.destroy_process_group()
         return None
-    # FP32 batches run pairs of steps through the two-step kernel (92 B per node and launch)
-    spl = 2 if prec == T.TRTR_F32 else 1
+    # pairs of steps through the two-step kernel where it applies (92 B per node and launch in
+    # FP32, 56 B for the 2-byte storages)
     if spl == 2:
         bpn, kernel = two_step_bytes_per_node(pop_bytes), "batch2_kernel"
     else:
         bpn, kernel = algorithmic_bytes_per_node(pop_bytes), "batch_kernel"
     peak, peak_kind = measured_hbm_peak()
     achieved = bpn * nodes / (spl * step_ms * 1e-3) / 1e9
+    per_update_bpn = algorithmic_bytes_per_node(pop_bytes)
+    per_update = per_update_bpn * nodes / (step_ms * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(step_ms, 5), "higher_is_better": True, "scaling": "weak",
@@ -598,7 +601,9 @@ def run_batch(args):
                    "launch": T.trtr_batch_config_name(best), "parallelism": f"replicas{world}",
                    "l2_flush": f"inputs larger than L2: {2 * 9 * pop_bytes * nodes / 1e9:.2f} GB of populations"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": f"{peak_kind} copy bandwidth",
+                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "frac_per_node_update": round(per_update / peak, 4), "bytes_per_node_update": per_update_bpn,
+                     "peak_kind": f"{peak_kind} copy bandwidth",
                      "bytes_per_node": bpn, "kernel": kernel, "steps_per_launch": spl},
         "gpu_launches": args.steps // spl + args.steps % spl,
         "clocks": clk,

@@ -266,7 +266,8 @@ trtr_status trtr_adjoint(trtr_ctx* ctx, const double* dJ_dphi, int on_device, do
  * Many independent problems of uneven sizes advanced together, each by the same step of
  * Eq. (14).  The paper solves one problem at a time; this is a throughput mode of its step.
  * Persistent kernel launches walk a work-list of (instance, tile) pairs spanning every
- * instance: one time step per launch, or two for FP32 instances (the two-step kernel);
+ * instance: one time step per launch, or two (the two-step kernel) where every instance has
+ * FP32 storage, or 2-byte storage with even nx;
  * trtr_batch_step replays two-launch CUDA graphs of them.
  * Each instance is an ordinary context (trtr_batch_instance gives it out for queries). */
 typedef struct {
@@ -304,17 +305,23 @@ trtr_status trtr_batch_tune(trtr_batch* b, int trial_steps, int* config_out, flo
 /* Selects a configuration explicitly. */
 trtr_status trtr_batch_set_config(trtr_batch* b, int config);
 
-/* Advances every instance by n >= 0 steps (asynchronous on the batch's stream).  With FP32
- * instances, pairs of steps run as launches of the two-step kernel over a work-list of its
- * tiles (the same results bit for bit; see trtr_batch_set_steps_per_launch), the other steps
+/* Advances every instance by n >= 0 steps (asynchronous on the batch's stream).  Where the
+ * two-step kernel applies (every instance FP32, or 2-byte with even nx), pairs of steps run as
+ * launches of it over a work-list of its tiles (the same results bit for bit; see
+ * trtr_batch_set_steps_per_launch), the other steps
  * with the configured one-step kernel.  Instances must not be stepped through their own
  * contexts in between (TRTR_ESTATE). */
 trtr_status trtr_batch_step(trtr_batch* b, long n);
 
 /* k = 2 (the default): trtr_batch_step runs pairs of steps with the two-step kernel where it
- * applies (FP32 instances); k = 1: every step with the configured one-step kernel.
+ * applies (FP32 instances, or 2-byte instances of even nx); k = 1: every step with the
+ * configured one-step kernel.
  * TRTR_EINVAL for other k. */
 trtr_status trtr_batch_set_steps_per_launch(trtr_batch* b, int k);
+
+/* The steps one launch of trtr_batch_step advances where it can: 2 when the two-step kernel
+ * applies to the batch and is not disabled, else 1.  TRTR_EINVAL for NULL arguments. */
+trtr_status trtr_batch_get_steps_per_launch(const trtr_batch* b, int* k);
 
 /* Waits for the batch's stream; TRTR_ETIMEOUT if a step kernel gave up a bounded wait
  * (TRTR_EBOUNDS in the bounds-checked build if a kernel access out of bounds was caught). */

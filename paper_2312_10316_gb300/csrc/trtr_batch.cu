@@ -47,7 +47,7 @@ struct alignas(64) InstanceDesc {
     Pulse pulse;
     double dt;
 };
-// Two-step launches (FP32): the two-step kernel's maps and arguments per instance.
+// Two-step launches (FP32 or 2-byte instances): the two-step kernel's maps and arguments per instance.
 struct alignas(64) InstanceDesc2 {
     CUtensorMap mp[2];        // populations, source buffer 0 / 1, the two-step tile's box
     CUtensorMap mf;           // packed fields
@@ -268,17 +268,20 @@ __global__ void __launch_bounds__(32 * BY, min_blocks<BY>())
     }
 }
 
-// Two time steps per launch over the work-list of two-step tiles (FP32): per tile the producer
-// issues the instance's two TMA boxes and copies its arguments and the time uniforms of both
-// steps into the stage's slot (the barrier's second arrival), then the block runs the two-step
-// kernel's two steps on the staged tile.  The last CTA advances the clock by two steps and both
-// time tables.
-template <int SRC, class G>
+// Two time steps per launch over the work-list of two-step tiles (FP32 or 2-byte instances):
+// per tile the producer issues the instance's two TMA boxes and copies its arguments and the
+// time uniforms of both steps into the stage's slot (the barrier's second arrival), then the
+// block runs the two-step kernel's two steps on the staged tile (SR: the 2-byte values rounded
+// stochastically with both steps' keys, from the clock).  The last CTA advances the clock by two
+// steps and both time tables.
+template <typename S, int SRC, class G, bool SR>
 __global__ void __launch_bounds__(G::kThreads, G::kCtas)
     batch2_kernel(const InstanceDesc2* __restrict__ desc, const int4* __restrict__ tiles, int ntiles,
                   TimeFields<float>* tu, TimeFields2* tu2, BatchClock* clk, int count, int parity) {
     constexpr int STAGES = G::kStages, NT = G::kThreads;
     using T = typename G::T;
+    const long long n0 = *reinterpret_cast<volatile long long*>(&clk->n);
+    const uint32_t rkey1 = SR ? sr_step_key((long)n0) : 0u, rkey2 = SR ? sr_step_key((long)n0 + 1) : 0u;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(16) StepArgs<float> sargs[STAGES];
     __shared__ __align__(16) TimeFields<float> stf2[STAGES];
@@ -313,12 +316,12 @@ __global__ void __launch_bounds__(G::kThreads, G::kCtas)
             s_t[s] = make_int4(-1, 0, 0, 0);
             return;
         }
-        const int4 t = tiles[idx];  // (instance, i0, j0, gx_p)
+        const int4 t = tiles[idx];  // (instance, i0, j0, gx_p | gx_f << 16)
         s_t[s] = t;
         const InstanceDesc2* d = desc + t.x;
         uint64_t* bar = &full[s];
         mbar_expect_tx(bar, T::TX);
-        step2_issue<T>(smem + s * T::Stage, bar, &d->mp[parity], &d->mf, t.y, t.z, t.w, t.w);
+        step2_issue<T>(smem + s * T::Stage, bar, &d->mp[parity], &d->mf, t.y, t.z, t.w & 0xffff, t.w >> 16);
         constexpr int kStatic = (int)(sizeof(StepArgs<float>) - sizeof(TimeFields<float>));
         cp_async_16(&sargs[s], &d->base[parity], kStatic);
         if (SRC == TRTR_SRC_PULSE) {
@@ -344,11 +347,12 @@ __global__ void __launch_bounds__(G::kThreads, G::kCtas)
         if (t.x < 0) break;
         const bool ok = mbar_wait_bounded(&full[s], (k / STAGES) & 1);
         if (!ok) s_abort = 1;
-        float* sp = reinterpret_cast<float*>(smem + s * T::Stage);
-        const float* sf = reinterpret_cast<const float*>(smem + s * T::Stage + T::PopBytes);
-        if (ok) step2_first<float, SRC, T, NT>(sp, sf, t.y, t.z, sargs[s], sargs[s].tf, tid);
+        S* sp = reinterpret_cast<S*>(smem + s * T::Stage);
+        const float* sf = reinterpret_cast<const float*>(smem + s * T::Stage + T::FldOff);
+        if (ok) step2_first<S, SRC, T, NT, SR>(sp, sf, t.y, t.z, sargs[s], sargs[s].tf, tid, rkey1);
         __syncthreads();  // step 1 complete (and s_abort visible)
-        if (ok && !s_abort) step2_second<float, SRC, T, NT>(sp, sf, t.y, t.z, sargs[s], stf2[s], tid);
+        if (ok && !s_abort)
+            step2_second<S, SRC, T, NT, false, SR>(sp, sf, t.y, t.z, sargs[s], stf2[s], tid, nullptr, rkey2);
         __syncthreads();  // stage s and its argument slot fully read
         if (s_abort) {
             if (tid == 0) {
@@ -553,14 +557,15 @@ cudaError_t dispatch(trtr_batch* b, int geom, int what, int parity = 0, int mode
     }
 }
 
-// The two-step kernel over the batch (FP32 instances; geometry of the batch's source mode).
-template <int SRC>
+// The two-step kernel over the batch (storage S, geometry of the storage and the batch's source
+// mode, SR: stochastic rounding of 2-byte instances).
+template <typename S, int SRC, bool SR>
 struct Batch2Launch {
-    using G = Geom2Of<SRC>;
+    using G = Geom2Of<SRC, (int)sizeof(S)>;
     using T = typename G::T;
     static size_t smem() { return (size_t)G::kStages * T::Stage + 128 + G::kStages * sizeof(uint64_t); }
     static cudaError_t configure(trtr_batch* b) {
-        auto kernel = batch2_kernel<SRC, G>;
+        auto kernel = batch2_kernel<S, SRC, G, SR>;
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem());
         if (e != cudaSuccess) return e;
         int per_sm = 0;
@@ -571,7 +576,7 @@ struct Batch2Launch {
         return cudaSuccess;
     }
     static cudaError_t launch(trtr_batch* b, int parity) {
-        batch2_kernel<SRC, G><<<b->grid2, G::kThreads, smem(), b->stream>>>(
+        batch2_kernel<S, SRC, G, SR><<<b->grid2, G::kThreads, smem(), b->stream>>>(
             static_cast<const InstanceDesc2*>(b->d_desc2), b->d_tiles2, b->ntiles2, b->d_tu, b->d_tu2, b->d_clk,
             b->count, parity);
         return cudaGetLastError();
@@ -582,8 +587,8 @@ struct Batch2Launch {
             InstanceDesc2& d = h[k];
             bool ok = true;
             for (int p = 0; p < 2; ++p)
-                ok = ok && encode(&d.mp[p], tma_type<float>(), 4, c->pop[p], c->lp, kQ, T::W, T::PR, kQ);
-            ok = ok && encode(&d.mf, tma_type<float>(), 4, c->fld2, c->lt, kT2NF, T::W, T::FR, kT2NF);
+                ok = ok && encode(&d.mp[p], tma_type<S>(), (int)sizeof(S), c->pop[p], c->lp, kQ, T::W, T::PR, kQ);
+            ok = ok && encode(&d.mf, tma_type<float>(), 4, c->fld2, c->lt, kT2NF, T::WF, T::FR, kT2NF);
             if (!ok) return false;
             StepArgs<float>& a = d.base[0];
             memset(static_cast<void*>(&a), 0, sizeof(a));
@@ -618,7 +623,8 @@ struct Batch2Launch {
         for (int k = 0; k < b->count; ++k) {
             const int nx = b->ctx[k]->p.nx, ny = b->ctx[k]->p.ny;
             for (int j0 = 0; j0 < ny; j0 += T::Y)
-                for (int i0 = 0; i0 < nx; i0 += T::X) t.push_back(make_int4(k, i0, j0, b->ctx[k]->lp.gx));
+                for (int i0 = 0; i0 < nx; i0 += T::X)
+                    t.push_back(make_int4(k, i0, j0, b->ctx[k]->lp.gx | (b->ctx[k]->lt.gx << 16)));
         }
         if (cudaMalloc(&b->d_tiles2, t.size() * sizeof(int4)) != cudaSuccess) return TRTR_ENOMEM;
         if (cudaMemcpyAsync(b->d_desc2, h.data(), sizeof(InstanceDesc2) * b->count, cudaMemcpyHostToDevice,
@@ -633,13 +639,28 @@ struct Batch2Launch {
     }
 };
 
+// Calls f with a Batch2Launch<S, SRC, SR> of the batch's storage, source mode and rounding.
+template <class F>
+auto with_batch2(const trtr_batch* b, F&& f) {
+    auto by_src = [&](auto* sp, auto sr) {
+        using S = std::remove_pointer_t<decltype(sp)>;
+        constexpr bool SR = decltype(sr)::value;
+        return b->src == TRTR_SRC_PULSE ? f(Batch2Launch<S, TRTR_SRC_PULSE, SR>()) : f(Batch2Launch<S, TRTR_SRC_NONE, SR>());
+    };
+    using TrueT = std::integral_constant<bool, true>;
+    using FalseT = std::integral_constant<bool, false>;
+    if (b->precision == TRTR_F16_OFS) return b->sr ? by_src((__half*)nullptr, TrueT()) : by_src((__half*)nullptr, FalseT());
+    if (b->precision == TRTR_BF16_OFS)
+        return b->sr ? by_src((__nv_bfloat16*)nullptr, TrueT()) : by_src((__nv_bfloat16*)nullptr, FalseT());
+    return by_src((float*)nullptr, FalseT());
+}
+
 cudaError_t launch_two(trtr_batch* b, int parity) {
-    return b->src == TRTR_SRC_PULSE ? Batch2Launch<TRTR_SRC_PULSE>::launch(b, parity)
-                                    : Batch2Launch<TRTR_SRC_NONE>::launch(b, parity);
+    return with_batch2(b, [&](auto l) { return decltype(l)::launch(b, parity); });
 }
 
 trtr_status setup_two_step(trtr_batch* b) {
-    return b->src == TRTR_SRC_PULSE ? Batch2Launch<TRTR_SRC_PULSE>::setup(b) : Batch2Launch<TRTR_SRC_NONE>::setup(b);
+    return with_batch2(b, [&](auto l) { return decltype(l)::setup(b); });
 }
 
 size_t desc_size(int precision) {
@@ -884,7 +905,7 @@ trtr_status trtr_batch_create(const trtr_instance* inst, int count, void* cuda_s
     if (s == TRTR_OK) s = trtr::apply_config(b, b->config);
     // two steps per launch where every instance has the two-step kernel's packed fields
     b->steps_per_launch = 2;
-    b->two_step = s == TRTR_OK && prec == TRTR_F32;
+    b->two_step = s == TRTR_OK;  // where every instance has the two-step fields (FP32, or 2-byte with even nx)
     for (int k = 0; k < count && b->two_step; ++k) b->two_step = b->ctx[k]->fld2 != nullptr;
     if (s == TRTR_OK && b->two_step &&
         (cudaMalloc(&b->d_desc2, sizeof(trtr::InstanceDesc2) * count) != cudaSuccess ||
@@ -940,6 +961,12 @@ trtr_status trtr_batch_set_config(trtr_batch* b, int config) {
 trtr_status trtr_batch_set_steps_per_launch(trtr_batch* b, int k) {
     if (!b || (k != 1 && k != 2)) return TRTR_EINVAL;
     b->steps_per_launch = k;
+    return TRTR_OK;
+}
+
+trtr_status trtr_batch_get_steps_per_launch(const trtr_batch* b, int* k) {
+    if (!b || !k) return TRTR_EINVAL;
+    *k = b->two_step && b->steps_per_launch == 2 ? 2 : 1;
     return TRTR_OK;
 }
 

@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(G::kThreads, G::kCtas)
         if (!ok) s_abort = 1;
         S* sp = reinterpret_cast<S*>(smem + s * T::Stage);
         const float* sf = reinterpret_cast<const float*>(smem + s * T::Stage + T::FldOff);
-        if (ok) step2_first<S, SRC, T, NT, SR>(sp, sf, i0, j0, a, a.tf, tid);
+        if (ok) step2_first<S, SRC, T, NT, SR>(sp, sf, i0, j0, a, a.tf, tid, a.rkey);
         __syncthreads();  // P1 complete (and s_abort visible)
         if (ok && !s_abort)
             step2_second<S, SRC, T, NT, P1, SR>(sp, sf, i0, j0, a, args.tf2, tid, static_cast<S*>(args.dst1), args.rkey2);

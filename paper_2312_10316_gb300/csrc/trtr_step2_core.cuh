@@ -182,12 +182,12 @@ __device__ __forceinline__ typename Pair<S>::type encode2(F2 v, uint32_t rk, int
 }
 
 // Step 1 over the tile's halo region R1, in place in the stage (thread tid of NT).  2-byte
-// storages: the step-1 values are rounded to the storage format with the first step's key, as
+// storages: the step-1 values are rounded to the storage format with the first step's key rkey1, as
 // a one-step launch stores them (halo nodes with the key of the wrapped node; nx is even, so
 // the wrapped pairs are the one-step kernel's pairs).
 template <typename S, int SRC, class T, int NT, bool SR = false>
 __device__ __forceinline__ void step2_first(S* sp, const float* sf, int i0, int j0, const StepArgs<float>& a,
-                                            const TimeFields<float>& tf, int tid) {
+                                            const TimeFields<float>& tf, int tid, uint32_t rkey1 = 0u) {
     constexpr int kT2W = T::W, kT2WF = T::WF, kT2PopPlane = T::PopPlane, kT2FldPlane = T::FldPlane;
     constexpr bool kOfs = sizeof(S) == 2;  // offsets folded into the moments, as in the one-step kernel
     constexpr int kC = T::HX - 2;          // stage column of R1 column 0
@@ -226,7 +226,7 @@ __device__ __forceinline__ void step2_first(S* sp, const float* sf, int i0, int 
         const F2 src = pair_source<SRC>(a, tf, wx, wrap_clamp(x + 1, nx), wy);
         F2 out[kQ];
         collide_node<F2, kOfs>(g, ux, uy, ax, ay, Dh, src, magic, w2f, a.tau2_fixed, out, F2(a.phi_ref));
-        const uint32_t rk = SR ? sr_pair_key(wx, wy, nx, a.rkey) : 0u;
+        const uint32_t rk = SR ? sr_pair_key(wx, wy, nx, rkey1) : 0u;
 #pragma unroll
         for (int q = 0; q < kQ; ++q) {
             S* d = sp + q * kT2PopPlane + (r + 1 - lattice_ey(q)) * kT2W + c + kC - lattice_ex(q);

@@ -106,6 +106,7 @@ _SIGNATURES = {
     "trtr_check_bounds_path": (_st, [_vp]),
     "trtr_set_steps_per_launch": (_st, [_vp, ctypes.c_int]),
     "trtr_batch_set_steps_per_launch": (_st, [_vp, ctypes.c_int]),
+    "trtr_batch_get_steps_per_launch": (_st, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "trtr_get_steps_per_launch": (_st, [_vp, ctypes.POINTER(ctypes.c_int)]),
 }
 
@@ -583,6 +584,12 @@ def trtr_batch_set_steps_per_launch(b, k: int):
     _bcheck(lib.trtr_batch_set_steps_per_launch(b, int(k)), "trtr_batch_set_steps_per_launch")
 
 
+def trtr_batch_get_steps_per_launch(b) -> int:
+    k = ctypes.c_int()
+    _bcheck(lib.trtr_batch_get_steps_per_launch(b, ctypes.byref(k)), "trtr_batch_get_steps_per_launch")
+    return k.value
+
+
 def trtr_batch_sync(b):
     _bcheck(lib.trtr_batch_sync(b), "trtr_batch_sync")
 
@@ -659,6 +666,10 @@ class Batch:
 
     def set_steps_per_launch(self, k: int):
         trtr_batch_set_steps_per_launch(self.b, k)
+
+    @property
+    def steps_per_launch(self) -> int:
+        return trtr_batch_get_steps_per_launch(self.b)
 
     def step(self, n: int = 1):
         trtr_batch_step(self.b, n)

@@ -30,8 +30,8 @@ def _uneven_pulses(seed=3, sizes=(48, 64, 100, 130, 200, 37), D_amp=0.0):
     return out
 
 
-def _single_solution(pulse, precision, steps):
-    with T.pulse_solver(pulse, precision=precision) as s:
+def _single_solution(pulse, precision, steps, **kw):
+    with T.pulse_solver(pulse, precision=precision, **kw) as s:
         s.step(steps)
         return s.get_populations().copy()
 
@@ -138,6 +138,39 @@ def test_two_steps_per_launch_batch_is_bitwise_the_single_solve(steps, D_amp):
         assert b.info()["step"] == total
         for k, p in enumerate(pulses):
             assert np.array_equal(b.instance(k).get_populations(), ref[k]), (k, p.n)
+
+
+@pytest.mark.parametrize("precision", [T.TRTR_F16_OFS, T.TRTR_BF16_OFS])
+@pytest.mark.parametrize("rounding", [T.TRTR_ROUND_STOCHASTIC, T.TRTR_ROUND_NEAREST])
+@pytest.mark.parametrize("D_amp", [0.0, 0.5])
+def test_two_byte_two_step_batch_is_bitwise_the_single_solve(precision, rounding, D_amp):
+    """2-byte batches of even-sized instances run pairs of steps through the two-step kernel,
+    whose intermediate state is rounded with the one-step kernel's bits; step counts split over
+    several calls interleave it with the one-step batch kernel."""
+    pulses = _uneven_pulses(D_amp=D_amp, sizes=(48, 64, 100, 130, 200, 38))
+    steps = [3, 5, 2, 7, 1, 9]
+    total = sum(steps)
+    ref = [_single_solution(p, precision, total, rounding=rounding) for p in pulses]
+    with T.Batch([T.pulse_instance(p, precision, rounding=rounding) for p in pulses]) as b:
+        assert b.steps_per_launch == 2
+        for n in steps:
+            b.step(n)
+        b.sync()
+        for k, p in enumerate(pulses):
+            assert np.array_equal(b.instance(k).get_populations(), ref[k]), (k, p.n)
+
+
+def test_steps_per_launch_of_batches():
+    even = _uneven_pulses(sizes=(48, 64))
+    odd = _uneven_pulses(sizes=(48, 37))
+    with T.Batch([T.pulse_instance(p, T.TRTR_F16_OFS) for p in even]) as b:
+        assert b.steps_per_launch == 2
+        b.set_steps_per_launch(1)
+        assert b.steps_per_launch == 1
+    with T.Batch([T.pulse_instance(p, T.TRTR_F16_OFS) for p in odd]) as b:
+        assert b.steps_per_launch == 1  # an instance of odd nx: one step per launch
+    with T.Batch([T.pulse_instance(p, T.TRTR_F32) for p in odd]) as b:
+        assert b.steps_per_launch == 2
 
 
 def test_batch_steps_per_launch_is_validated():
