@@ -48,6 +48,8 @@ WORKLOADS = {
 }
 DEFAULT_WORKLOAD = "pulse4096_f32_varD_mms"
 # batched workloads: 256 seeded pulses, square grids drawn from {64 ... 1024}, one launch per step
+# FP32 workloads whose bench line also times the same grid and physics with 2-byte storage
+COMPANIONS = {"pulse4096_f32_varD_mms": "pulse4096_f16_varD_mms", "pulse8192_f32_varD_mms": "pulse8192_f16_varD_mms"}
 BATCH_WORKLOADS = {"batch256_f32": ("f32", 4), "batch256_f16": ("f16", 2)}
 # gradient of the L2 misfit w.r.t. D through 2000 steps of a 512^2 pulse (discrete adjoint)
 # (and the same at 2048^2, whose 151 MB per state do not fit in L2)
@@ -77,6 +79,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample length")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-companion", action="store_true",
+                    help="skip the 2-byte-storage companion measurement of FP32 pulse workloads")
     ap.add_argument("--parity-steps", type=int, default=-1,
                     help="steps of the FP64 GPU comparison run that states the L2 error, independent of "
                          "--steps (-1: the workload's configured length, 10000 steps; 0: skip)")
@@ -269,31 +273,14 @@ def cpu_baseline(pulse, seconds: float):
 # ------------------------------------------------------------------------------ ours
 
 
-def run_ours(args):
-    import numpy as np
+def timed_steps(args, pulse, prec, pop_bytes, workload, rnd, src_override, world, stream, sh, local):
+    """W warm-up steps, then K steps of `workload` timed with one CUDA event per launch on the
+    library's stream, clocks sampled meanwhile: (GLUPS, ms per step, roofline, launches, clocks)."""
     import torch
 
     from paper_2312_10316_gb300 import trtr as T
 
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    pulse, prec_key, pop_bytes = WORKLOADS[args.workload]
-    prec = T.PRECISIONS[prec_key]
-    stream = torch.cuda.Stream()
-    sh = stream.cuda_stream
     n_nodes = pulse.nx * pulse.ny
-
-    # ---- device-resident throughput
-    src_override = {"auto": None, "none": T.TRTR_SRC_NONE, "field": T.TRTR_SRC_FIELD,
-                    "pulse": T.TRTR_SRC_PULSE}[args.src]
-    if src_override is not None:
-        args.parity_steps, args.no_e2e = 0, True
-    rounding = "stochastic" if args.rounding == "auto" else args.rounding
-    rnd = T.TRTR_ROUND_STOCHASTIC if rounding == "stochastic" else T.TRTR_ROUND_NEAREST
     solver = T.pulse_solver(pulse, precision=prec, stream=sh, src_mode=src_override, rounding=rnd)
     if src_override == T.TRTR_SRC_FIELD:
         solver.set_source(W.source(pulse, 0.0))  # the manufactured source as a stationary field
@@ -342,7 +329,7 @@ def run_ours(args):
     bpn += extra
     peak, peak_kind = measured_hbm_peak()
     achieved = bpn * n_nodes / (avg_launch_ms * 1e-3) / 1e9
-    traffic = ncu_traffic(args.workload, kernel) if src_override is None else None
+    traffic = ncu_traffic(workload, kernel) if src_override is None else None
     # the same launches against the method's bytes per node-update (one step's populations and
     # fields, whatever the kernel moves), and the DRAM bytes the committed counters measured
     per_update_bpn = algorithmic_bytes_per_node(pop_bytes) + extra
@@ -355,23 +342,76 @@ def run_ours(args):
                 "peak_kind": f"{peak_kind} copy bandwidth", "bytes_per_node": bpn,
                 "kernel": kernel, "steps_per_launch": spl,
                 "median_launch_ms": round(statistics.median(per_launch), 5)}
-    phi_gpu = solver.moments() if args.parity_steps else None
     solver.close()
+    return value, ms_per_step, roofline, gpu_launches, clk
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2312_10316_gb300 import trtr as T
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    pulse, prec_key, pop_bytes = WORKLOADS[args.workload]
+    prec = T.PRECISIONS[prec_key]
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+    n_nodes = pulse.nx * pulse.ny
+
+    # ---- device-resident throughput
+    src_override = {"auto": None, "none": T.TRTR_SRC_NONE, "field": T.TRTR_SRC_FIELD,
+                    "pulse": T.TRTR_SRC_PULSE}[args.src]
+    if src_override is not None:
+        args.parity_steps, args.no_e2e = 0, True
+    rounding = "stochastic" if args.rounding == "auto" else args.rounding
+    rnd = T.TRTR_ROUND_STOCHASTIC if rounding == "stochastic" else T.TRTR_ROUND_NEAREST
+    value, ms_per_step, roofline, gpu_launches, clk = timed_steps(
+        args, pulse, prec, pop_bytes, args.workload, rnd, src_override, world, stream, sh, local)
+    # the same grid and physics with 2-byte storage (FP32 workloads that have one): its own timed
+    # region after this one, its parity in the shared parity leg below
+    companion = COMPANIONS.get(args.workload) if (src_override is None and not args.no_companion) else None
+    comp = None
+    if companion:
+        cpulse, ckey, cbytes = WORKLOADS[companion]
+        cv, cms, croof, cl, cclk = timed_steps(args, cpulse, T.PRECISIONS[ckey], cbytes, companion,
+                                               T.TRTR_ROUND_STOCHASTIC, None, world, stream, sh, local)
+        comp = {"workload": companion, "dtype": ckey, "rounding": "stochastic", "value": round(cv, 3),
+                "unit": UNIT, "ms_per_step": round(cms, 5), "steps": args.steps, "roofline": croof,
+                "gpu_launches": cl, "clocks": cclk, "parity": None,
+                "note": "timed after the headline region, same grid and physics, 2-byte offset storage"}
 
     # ---- stated L2 error against the FP64 path (outside the timed region)
     parity = None
     if args.parity_steps and rank == 0:
         ks = pulse.steps if args.parity_steps < 0 else args.parity_steps
-        at = {}
+        at, cat = {}, {}
         with T.pulse_solver(pulse, precision=prec, stream=sh, rounding=rnd) as a, \
                 T.pulse_solver(pulse, precision=T.TRTR_F64, stream=sh) as b:
+            c16 = (T.pulse_solver(WORKLOADS[companion][0], precision=T.PRECISIONS[WORKLOADS[companion][1]], stream=sh)
+                   if comp else None)
             done = 0
             for c in sorted({c for c in (100, 1000, ks) if c <= ks}):
                 a.step(c - done)
                 b.step(c - done)
+                if c16:
+                    c16.step(c - done)
                 done = c
                 pa, pb = a.moments(), b.moments()
                 at[c] = float(np.linalg.norm(pa - pb) / np.linalg.norm(pb))
+                if c16:
+                    pc = c16.moments()
+                    cat[c] = float(np.linalg.norm(pc - pb) / np.linalg.norm(pb))
+            if c16:
+                comp["parity"] = {"rel_l2_vs_f64_gpu": cat[ks], "steps": ks, "rel_l2_at_steps": cat,
+                                  "mass_rel_diff": float(abs(pc.sum() - pb.sum()) / abs(pb.sum())),
+                                  "reference": "the same GPU FP64 solve as the headline's parity"}
+                c16.close()
         parity = {"rel_l2_vs_f64_gpu": at[ks], "steps": ks, "rel_l2_at_steps": at,
                   "mass_rel_diff": float(abs(pa.sum() - pb.sum()) / abs(pb.sum())),
                   "reference": "GPU FP64 path (matches the FP64 oracle to 1e-12)",
@@ -438,6 +478,8 @@ def run_ours(args):
         "e2e": e2e,
         "parity": parity,
     }
+    if comp:
+        line["fp16_storage"] = comp
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(pulse, args.cpu_seconds)
     if world > 1:
