@@ -32,8 +32,7 @@ struct Tile2 {
     static constexpr int TX = PopBytes + FldBytes;       // bytes per tile (boxes include any fill)
     static constexpr int Stage = (FldOff + FldBytes + 127) / 128 * 128;
     static_assert(ES == 4 || ES == 2, "FP32 or 2-byte populations");
-    static_assert(BX % 8 == 0, "tile origins on 16-byte boundaries");
-    static_assert(ES != 4 || FldOff == PopBytes, "FP32: the field box follows the population box");
+    static_assert((BX * ES) % 16 == 0 && BX % 4 == 0, "tile origins on 16-byte boundaries");
     static_assert(W <= 256 && WF <= 256 && PR <= 256, "TMA box dimensions are at most 256");
 };
 
@@ -49,8 +48,13 @@ struct Geom2 {
 // modes of the FP32 kernel; TRTR_STEP2H_* the same for the 2-byte one): a few independent CTAs
 // per SM hide each one's barrier between the two steps, the pulse source's arithmetic favours
 // more of them.
+// FP32 with the pulse: 32 x 8 tiles in three 128-thread CTAs (GB300, GLUPS at 4096^2 / 8192^2:
+// 114.1 / 121.8); wider or taller tiles leave fewer CTAs or one stage (64 x 8 in two 256-thread
+// CTAs 108.6 / 115.5, 64 x 16 in one 512-thread CTA 100.2 / 106.6, 60 x 6 104.1 / 111.7), and
+// 28-column tiles, whose step-1 pairs fill the block evenly, measured slower (28 x 14: 102.2 /
+// 108.7).
 template <int SRC, int ES>
-struct Geom2For {  // FP32, in-kernel pulse source
+struct Geom2For {
     using type = Geom2<2, 3, 128, 32, 8, ES>;
 };
 template <>

@@ -97,6 +97,21 @@ def test_recorded_run_with_two_steps_per_launch_gives_the_same_gradient():
         assert np.array_equal(one[1], two[1]), (steps, iv)
 
 
+@pytest.mark.parametrize("precision", [T.TRTR_F16_OFS, T.TRTR_BF16_OFS])
+def test_two_byte_recorded_run_and_recomputation_with_two_steps_per_launch(precision):
+    """2-byte storages on an even-nx grid: the recorded run and the segment recomputation (which
+    also stores the intermediate state) take pairs of steps through the two-step kernel; phi and
+    the gradient are the one-step run's bits."""
+    pulse, ux, uy, D, phi0 = _setup(40, nx=38, ny=23)
+    lamN = np.random.default_rng(6).uniform(-1, 1, size=(23, 38))
+    for steps, iv in ((30, 7), (31, 0), (40, 8)):
+        one = _gpu_grad(pulse, ux, uy, D, phi0, lamN, steps, precision, iv, nx=38, ny=23, spl=1)
+        two = _gpu_grad(pulse, ux, uy, D, phi0, lamN, steps, precision, iv, nx=38, ny=23, spl=2)
+        assert np.array_equal(one[0], two[0]), (steps, iv)
+        assert np.array_equal(one[1], two[1]), (steps, iv)
+        assert np.isfinite(two[1]).all()
+
+
 def test_adjoint_f32_against_the_oracle_adjoint_64():
     """FP32 forward states and FP32 adjoint arithmetic (FP64 accumulation of dJ/dD)."""
     pulse, ux, uy, D, phi0 = _setup(64)

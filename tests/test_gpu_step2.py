@@ -122,8 +122,9 @@ def test_two_byte_two_step_path_against_the_oracle(prec):
     assert launches == 1 + 4  # field packing, four two-step launches
 
 
-def test_launch_counts_and_the_stability_check_cadence():
-    with _pulse_solver(64, 48, T.TRTR_GRAD_ONESIDED_EDGE, 2) as s:
+@pytest.mark.parametrize("precision", [T.TRTR_F32, T.TRTR_F16_OFS])
+def test_launch_counts_and_the_stability_check_cadence(precision):
+    with _pulse_solver(64, 48, T.TRTR_GRAD_ONESIDED_EDGE, 2, precision=precision) as s:
         l0 = s.launches
         s.step(6)
         assert s.launches - l0 == 1 + 3  # field packing, then three two-step launches
@@ -136,7 +137,7 @@ def test_launch_counts_and_the_stability_check_cadence():
     ref = None
     for k in (1, 2):
         pulse = W.Pulse(n=64, D_amp=0.5, courant=0.4)
-        p = T.Params(nx=64, ny=48, dx=pulse.dx, dt=pulse.dt, x0=pulse.x0, y0=pulse.y0, precision=T.TRTR_F32,
+        p = T.Params(nx=64, ny=48, dx=pulse.dx, dt=pulse.dt, x0=pulse.x0, y0=pulse.y0, precision=precision,
                      grad_mode=T.TRTR_GRAD_ONESIDED_EDGE, src_mode=T.TRTR_SRC_PULSE, check_every=3)
         with T.Solver(p) as s:
             s.set_steps_per_launch(k)
@@ -242,11 +243,12 @@ def test_fullsize_sampled_two_byte_two_step_launch(pulse, prec):
     _sampled_two_step_check(pulse, 100, 1500, 8 * unit, precision=HALF[prec])
 
 
-def test_save_load_and_recorded_runs_keep_the_two_step_path_exact():
+@pytest.mark.parametrize("precision", [T.TRTR_F32, T.TRTR_F16_OFS, T.TRTR_BF16_OFS])
+def test_save_load_and_recorded_runs_keep_the_two_step_path_exact(precision):
     nx, ny = 70, 33
     res = {}
     for k in (1, 2):
-        with _pulse_solver(nx, ny, T.TRTR_GRAD_ONESIDED_EDGE, k) as s:
+        with _pulse_solver(nx, ny, T.TRTR_GRAD_ONESIDED_EDGE, k, precision=precision) as s:
             s.step(3)
             blob = s.save()
             s.step(2)
