@@ -75,7 +75,10 @@ constexpr int kNumGeoms = 5;
 constexpr int kNumSchedules = 4;
 constexpr int kNumConfigs = kNumGeoms * kNumSchedules;
 constexpr int kDefaultConfig = 3 * kNumSchedules + 3;  // 128 x 16 tiles, dynamic
-constexpr int kBatch2Run = 4;  // work-list entries per take of the two-step batch kernel
+#ifndef TRTR_BATCH2_RUN
+#define TRTR_BATCH2_RUN 4
+#endif
+constexpr int kBatch2Run = TRTR_BATCH2_RUN;  // work-list entries per take of the two-step batch kernel
 // kernel mode of a schedule: 0 chunked, 1 interleaved, 2 dynamic
 constexpr int schedule_mode(int schedule) { return schedule == 0 ? 1 : (schedule == 3 ? 2 : 0); }
 
@@ -557,11 +560,30 @@ cudaError_t dispatch(trtr_batch* b, int geom, int what, int parity = 0, int mode
     }
 }
 
-// The two-step kernel over the batch (storage S, geometry of the storage and the batch's source
+// Geometry of the two-step batch kernel: 32 x 8 tiles in 128-thread CTAs for every storage and
+// source mode, where the single grid takes 32 x 16 (FP32 without a source) or 64 x 16 (2-byte):
+// the batch's many small instances favour small tiles.  Measured on the 256 uneven instances
+// (GLUPS): FP32 32 x 16 in two 256-thread CTAs 102.6, 32 x 8 in three or four CTAs 110.4; FP16
+// 64 x 16 110.6, 64 x 8 in three CTAs 96.1, 32 x 16 in two 256-thread CTAs 124.1, 32 x 12 in
+// three 117.1, 32 x 8 in three or four 125.9 (three stages 108.8).  The
+// TRTR_BATCH2_{STAGES,CTAS,THREADS,BX,BY} macros set it for both storages (sweeps).
+template <int SRC, int ES>
+struct BatchGeom2 {
+    using type = Geom2<2, ES == 2 ? 4 : 3, 128, 32, 8, ES>;
+};
+#ifdef TRTR_BATCH2_BX
+template <int SRC, int ES>
+using BatchGeom2Of = Geom2<TRTR_BATCH2_STAGES, TRTR_BATCH2_CTAS, TRTR_BATCH2_THREADS, TRTR_BATCH2_BX, TRTR_BATCH2_BY, ES>;
+#else
+template <int SRC, int ES>
+using BatchGeom2Of = typename BatchGeom2<SRC, ES>::type;
+#endif
+
+// The two-step kernel over the batch (storage S, the batch geometry of the storage and source
 // mode, SR: stochastic rounding of 2-byte instances).
 template <typename S, int SRC, bool SR>
 struct Batch2Launch {
-    using G = Geom2Of<SRC, (int)sizeof(S)>;
+    using G = BatchGeom2Of<SRC, (int)sizeof(S)>;
     using T = typename G::T;
     static size_t smem() { return (size_t)G::kStages * T::Stage + 128 + G::kStages * sizeof(uint64_t); }
     static cudaError_t configure(trtr_batch* b) {
