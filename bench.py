@@ -2,8 +2,11 @@
 """Throughput of the fused TRT-R step (GLUPS) on the rotating-pulse workloads.
 
 One bench step is one TRT-R time step (pull-stream, phi, TRT-R relaxation, auxiliary term,
-source, store) over every node of the workload's grid, i.e. one launch of the fused step
-kernel.  Prints ONE JSON line on rank 0.
+source, store) over every node of the workload's grid; where the two-step kernel applies, one
+launch advances two of them.  Prints ONE JSON line on rank 0: the workload's throughput with
+its roofline, the relative L2 error of a full-length solve against the GPU FP64 path, an
+end-to-end run from host buffers and, for the FP32 pulse workloads, the same grid with FP16
+storage (`fp16_storage`).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
 
