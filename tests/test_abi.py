@@ -124,6 +124,9 @@ def test_null_arguments(T):
     assert lib.trtr_set_source_prev(None, None, 0) == T.TRTR_EINVAL
     assert lib.trtr_check_timeout_path(None, 1000) == T.TRTR_EINVAL
     assert lib.trtr_bounds_report(None) == T.TRTR_EINVAL
+    assert lib.trtr_batch_set_steps_per_launch(None, 2) == T.TRTR_EINVAL
+    assert lib.trtr_batch_get_steps_per_launch(None, None) == T.TRTR_EINVAL
+    assert lib.trtr_get_steps_per_launch(None, None) == T.TRTR_EINVAL
 
 
 def test_batch_rejects_bad_instances_before_touching_cuda(T):
