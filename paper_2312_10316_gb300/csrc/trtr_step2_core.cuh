@@ -48,18 +48,15 @@ struct Geom2 {
 // modes of the FP32 kernel; TRTR_STEP2H_* the same for the 2-byte one): a few independent CTAs
 // per SM hide each one's barrier between the two steps, the pulse source's arithmetic favours
 // more of them.
-// FP32 with the pulse: 32 x 8 tiles in three 128-thread CTAs (GB300, GLUPS at 4096^2 / 8192^2:
-// 114.1 / 121.8); wider or taller tiles leave fewer CTAs or one stage (64 x 8 in two 256-thread
-// CTAs 108.6 / 115.5, 64 x 16 in one 512-thread CTA 100.2 / 106.6, 60 x 6 104.1 / 111.7), and
-// 28-column tiles, whose step-1 pairs fill the block evenly, measured slower (28 x 14: 102.2 /
-// 108.7).
+// FP32: 32 x 8 tiles in three 128-thread CTAs (GB300, GLUPS at 4096^2 / 8192^2 with the pulse:
+// 114.1 / 121.8; without a source 131.6 / 141.0, against 123.2 / 131.4 for 32 x 16 tiles in two
+// 256-thread CTAs); wider or taller tiles leave fewer CTAs or one stage (64 x 8 in two
+// 256-thread CTAs 108.6 / 115.5, 64 x 16 in one 512-thread CTA 100.2 / 106.6, 60 x 6 104.1 /
+// 111.7), and 28-column tiles, whose step-1 pairs fill the block evenly, measured slower
+// (28 x 14: 102.2 / 108.7).
 template <int SRC, int ES>
 struct Geom2For {
     using type = Geom2<2, 3, 128, 32, 8, ES>;
-};
-template <>
-struct Geom2For<TRTR_SRC_NONE, 4> {
-    using type = Geom2<2, 2, 256, 32, 16, 4>;
 };
 // 2-byte storages: half the stage bytes, so wider tiles with less step-1 halo work fit two CTAs
 // per SM.  Measured (GB300, FP16 pulse, GLUPS at 4096^2 / 8192^2): 32 x 8 in 3 (4) 128-thread
